@@ -1,0 +1,138 @@
+"""Seeded synthetic inputs for three-quarter sampling reconstruction.
+
+This module only *draws* test inputs: high-resolution images, L-pixel
+opaque-quadrant masks, and the sensor measurement that turns one into
+low-resolution L-pixel values (Sec. II, Eq. 1: each L-pixel integrates the
+three transparent high-resolution sub-pixels of its 2x2 footprint).  It holds
+none of the reconstruction arithmetic and imports nothing else from this
+package, so both the CPU oracle and the CUDA path can take their inputs from
+here.
+
+The paper evaluates on 100 natural 1200x1200 images (Sec. V-A), which are not
+available; the images drawn here stand in for them:
+
+* ``S`` 2-D sinusoids with per-axis frequency ~ U(-0.5, 0.5) cycles per HR
+  pixel (up to HR Nyquist), phase ~ U(0, 2 pi), amplitude ~ U(0, 1);
+* ``E`` straight step edges through a uniform point with direction
+  ~ U(0, pi) and height ~ U(-1, 1) * mean sinusoid amplitude;
+* min-max normalisation to [0, 1], optional Gaussian noise ``sigma``,
+  clipping to [0, 1].
+
+Masks hold one code per LR pixel, the index of its opaque quadrant:
+0 = top-left, 1 = top-right, 2 = bottom-left, 3 = bottom-right.  A recurrent
+mask tiles a ``T x T`` LR tile drawn uniformly from {0..3} (Sec. V-A uses a
+random pattern repeating every 32 HR pixels, i.e. T = 16); a non-recurrent
+mask draws every LR pixel independently.
+
+All randomness comes from numpy's PCG64 generator, whose streams are the same
+on every platform.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "image", "recurrent_mask", "random_mask", "measure", "workload",
+    "batch_sizes", "OPAQUE_OFFSETS",
+]
+
+# (row, col) offset of the opaque sub-pixel inside the 2x2 footprint, by code.
+OPAQUE_OFFSETS = ((0, 0), (0, 1), (1, 0), (1, 1))
+
+
+def image(h: int, w: int, n_sin: int, n_edges: int, seed: int,
+          sigma: float = 0.0) -> np.ndarray:
+    """Return an ``h x w`` float64 image in [0, 1] drawn from ``seed``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fy = rng.uniform(-0.5, 0.5, n_sin)
+    fx = rng.uniform(-0.5, 0.5, n_sin)
+    ph = rng.uniform(0.0, 2.0 * np.pi, n_sin)
+    amp = rng.uniform(0.0, 1.0, n_sin)
+    yy = np.arange(h, dtype=np.float64)
+    xx = np.arange(w, dtype=np.float64)
+    # sin(2pi fy y + 2pi fx x + ph) = sin(a_y) cos(b_x) + cos(a_y) sin(b_x)
+    ay = 2.0 * np.pi * np.outer(yy, fy) + ph[None, :]          # h x S
+    bx = 2.0 * np.pi * np.outer(fx, xx)                         # S x w
+    left = np.concatenate([np.sin(ay) * amp, np.cos(ay) * amp], axis=1)
+    right = np.concatenate([np.cos(bx), np.sin(bx)], axis=0)
+    img = left @ right
+    mean_amp = float(amp.mean()) if n_sin else 1.0
+    py = rng.uniform(0.0, h, n_edges)
+    px = rng.uniform(0.0, w, n_edges)
+    th = rng.uniform(0.0, np.pi, n_edges)
+    hgt = rng.uniform(-1.0, 1.0, n_edges) * mean_amp
+    for e in range(n_edges):
+        ny, nx = np.sin(th[e]), np.cos(th[e])
+        side = (yy[:, None] - py[e]) * ny + (xx[None, :] - px[e]) * nx > 0.0
+        img += hgt[e] * side
+    lo, hi = img.min(), img.max()
+    img = (img - lo) / (hi - lo) if hi > lo else np.zeros_like(img)
+    if sigma > 0.0:
+        img = img + rng.normal(0.0, sigma, img.shape)
+    return np.clip(img, 0.0, 1.0)
+
+
+def recurrent_mask(lr_h: int, lr_w: int, tile: int, seed: int) -> np.ndarray:
+    """Opaque-quadrant codes of a ``tile x tile`` LR tile repeated periodically."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = rng.integers(0, 4, (tile, tile), dtype=np.uint8)
+    reps = (-(-lr_h // tile), -(-lr_w // tile))
+    return np.ascontiguousarray(np.tile(t, reps)[:lr_h, :lr_w])
+
+
+def random_mask(lr_h: int, lr_w: int, seed: int) -> np.ndarray:
+    """Independent opaque-quadrant code per LR pixel (a non-recurrent sensor)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(0, 4, (lr_h, lr_w), dtype=np.uint8)
+
+
+def measure(f: np.ndarray, mask: np.ndarray) -> np.ndarray:
+    """Simulate the three-quarter sensor of Eq. 1 (coefficients 1, a sum).
+
+    ``y[p, q]`` is the sum of the three transparent HR sub-pixels of the
+    footprint ``f[2p:2p+2, 2q:2q+2]``; ``mask[p, q]`` names the opaque one.
+    """
+    lr_h, lr_w = mask.shape
+    f = np.asarray(f, dtype=np.float64)[: 2 * lr_h, : 2 * lr_w]
+    quad = f.reshape(lr_h, 2, lr_w, 2).transpose(0, 2, 1, 3).reshape(lr_h, lr_w, 4)
+    total = quad.sum(axis=2)
+    opaque = np.take_along_axis(quad, mask[..., None].astype(np.int64), axis=2)[..., 0]
+    return total - opaque
+
+
+def batch_sizes(n: int, seed: int, lo=(256, 256), hi=(1536, 2048), mult: int = 8):
+    """Uneven image sizes (h, w), multiples of ``mult``, drawn by ``seed``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hs = rng.integers(lo[0] // mult, hi[0] // mult + 1, n) * mult
+    ws = rng.integers(lo[1] // mult, hi[1] // mult + 1, n) * mult
+    return [(int(a), int(b)) for a, b in zip(hs, ws)]
+
+
+# Workloads shaped like the paper's (Sec. V) at the sizes this library is
+# measured on.  Each entry: HR size (h, w), sinusoids, edges, noise sigma,
+# LR tile of the recurrent mask, image seed, mask seed.
+_WORKLOADS = {
+    "rljsde_64x64":      dict(h=64,   w=64,   n_sin=32,   n_edges=4,   sigma=0.0,   tile=4, seed=1000, mseed=8),
+    "rljsde_1024x1024":  dict(h=1024, w=1024, n_sin=256,  n_edges=32,  sigma=0.005, tile=4, seed=2000, mseed=9),
+    "rljsde_4096x3072":  dict(h=3072, w=4096, n_sin=2048, n_edges=256, sigma=0.0,   tile=8, seed=3000, mseed=10),
+    "rljsde_1200x1200":  dict(h=1200, w=1200, n_sin=256,  n_edges=32,  sigma=0.005, tile=16, seed=6000, mseed=13),
+}
+
+
+def workload(name: str, index: int = 0, random: bool = False):
+    """Return ``(f, mask, y)`` for a named workload.
+
+    ``f`` is the HR image (float64), ``mask`` the LR code array (uint8), and
+    ``y`` the float32 L-pixel measurements.  ``random=True`` swaps the
+    recurrent mask for a non-recurrent one of the same size.
+    """
+    cfg = _WORKLOADS[name]
+    f = image(cfg["h"], cfg["w"], cfg["n_sin"], cfg["n_edges"],
+              cfg["seed"] + index, cfg["sigma"])
+    lr_h, lr_w = cfg["h"] // 2, cfg["w"] // 2
+    if random:
+        mask = random_mask(lr_h, lr_w, cfg["mseed"] + 100)
+    else:
+        mask = recurrent_mask(lr_h, lr_w, cfg["tile"], cfg["mseed"])
+    y = measure(f, mask).astype(np.float32)
+    return f, mask, y
