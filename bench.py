@@ -1,0 +1,303 @@
+"""Benchmark: HR megapixels per second reconstructed by RL-JSDE on GB300.
+
+One step = one call of the C-ABI reconstruction on one synthetic image of the
+workload (default: 1024x1024 HR from 512x512 L-pixel measurements, recurrent
+4x4-LR mask tile, nu_max = 100): the whole hot path (gather, initial
+projection, greedy loop, synthesis) in one persistent kernel launch.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+(the reference arm of this project) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HR megapixels/s reconstructed on 1 GB300 vs oracle (Δ≤1e-4) and % roofline"
+UNIT = "MP/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def flops_per_block(nu: int) -> int:
+    """Arithmetic of the factored RL-JSDE path per 4x4 block (FMA = 2 flops,
+    multiplications by structural zeros not counted)."""
+    dft = 256 * 16 * 4 + 4 * 256 * 8 * 8 + 4 * 256 * 2      # row DFTs, column DFTs (even/odd), combine
+    first = 256 * 64                                          # transform + scores, no update
+    per_iter = 256 * 96                                       # update 32 + transform 48 + scores 16 per kappa
+    scalar = 64                                               # delta, h_t(uv), g_t, synthesis
+    return dft + first + (nu - 1) * per_iter + nu * scalar
+
+
+def fp32_peak_tflops() -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_traffic(workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2205_02646_gb300", "csrc", "kernels.cu")
+    try:
+        rec = json.load(open(path))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        ent = rec.get(workload)
+        if ent and ent.get("kernels_cu_sha256") == digest:
+            return ent.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def cpu_oracle_sample(y, mask, nu, budget_s=15.0, seed=0):
+    """Time the FP64 direct oracle on a bounded random sample of blocks."""
+    import oracle
+    nb = (mask.shape[0] // 2) * (mask.shape[1] // 2)
+    rng = np.random.default_rng(seed)
+    params = oracle.Params(nu_max=nu)
+    threads = os.cpu_count() or 1
+    y64 = np.asarray(y, np.float64)
+    probe = rng.choice(nb, min(nb, 2 * threads), replace=False)
+    t0 = time.perf_counter()
+    oracle.reconstruct(y64, mask, params, blocks=probe, n_threads=threads)
+    t_probe = time.perf_counter() - t0
+    per_block = t_probe / len(probe)
+    n = int(min(nb, max(len(probe), (budget_s - t_probe) / max(per_block, 1e-9))))
+    blocks = rng.choice(nb, n, replace=False)
+    t0 = time.perf_counter()
+    oracle.reconstruct(y64, mask, params, blocks=blocks, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n * 16 / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d random 4x4 blocks of the workload (%.1f s, FP64 direct L-JSDE, %d threads)"
+                      % (n, dt, threads)}, n, dt
+
+
+def run_reference(args, rank, world):
+    from paper_2205_02646_gb300 import synth
+    if rank != 0:
+        return
+    import oracle
+    oracle.load()
+    f, mask, y = synth.workload(args.workload)
+    nu = args.nu_max
+    nb = (mask.shape[0] // 2) * (mask.shape[1] // 2)
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(1)
+    params = oracle.Params(nu_max=nu)
+    y64 = y.astype(np.float64)
+    per_step = max(threads, args.ref_blocks)
+    for _ in range(args.warmup):
+        oracle.reconstruct(y64, mask, params, blocks=rng.choice(nb, threads, replace=False), n_threads=threads)
+    total = 0.0
+    for _ in range(args.steps):
+        bl = rng.choice(nb, per_step, replace=False)
+        t0 = time.perf_counter()
+        oracle.reconstruct(y64, mask, params, blocks=bl, n_threads=threads)
+        total += time.perf_counter() - t0
+    mp = args.steps * per_step * 16 / 1e6
+    val = mp / total
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "nu_max": nu,
+                                            "blocks_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d random 4x4 blocks per step, FP64 direct L-JSDE" % per_step},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rljsde_1024x1024")
+    ap.add_argument("--nu-max", type=int, default=100)
+    ap.add_argument("--ref-blocks", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2205_02646_gb300 import build, rljsde, synth
+    build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    # Each rank reconstructs its own image (independent problems, no exchange).
+    f, mask, y = synth.workload(args.workload, index=rank)
+    lr_h, lr_w = mask.shape
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base, _, _ = cpu_oracle_sample(y, mask, args.nu_max)
+
+    params = rljsde.default_params(nu_max=args.nu_max)
+    plan = rljsde.Plan(mask, params)
+    info = plan.info()
+    stream = torch.cuda.current_stream()
+    lr = torch.from_numpy(y).to(dev)
+    hr = torch.empty((2 * lr_h, 2 * lr_w), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)       # > 129 MB L2
+    mp_per_step = 4 * lr_h * lr_w / 1e6
+
+    for _ in range(args.warmup):
+        plan.reconstruct(lr, hr, stream)
+    plan.check(stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clocks = Clocks(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))                       # evict L2 between timed steps
+        ev[i][0].record(stream)
+        plan.reconstruct(lr, hr, stream)            # one kernel launch
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    plan.check(stream)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * mp_per_step * args.steps / (total_ms / 1e3)
+
+    # End to end through the public API with host buffers: H2D of the
+    # measurements from pinned memory, reconstruction, D2H of the HR image.
+    lr_host = torch.from_numpy(y).pin_memory()
+    hr_host = torch.empty((2 * lr_h, 2 * lr_w)).pin_memory()
+    for _ in range(2):
+        lr.copy_(lr_host, non_blocking=True)
+        plan.reconstruct(lr, hr, stream)
+        hr_host.copy_(hr, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lr.copy_(lr_host, non_blocking=True)
+        plan.reconstruct(lr, hr, stream)
+        hr_host.copy_(hr, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = world * mp_per_step * args.steps / (e2e_ms / 1e3)
+
+    n_blocks = info["n_blocks"]
+    flops = flops_per_block(args.nu_max) * n_blocks
+    mean_s = total_ms / args.steps / 1e3
+    achieved = flops / mean_s / 1e12
+    peak = fp32_peak_tflops()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "hr": [2 * lr_h, 2 * lr_w], "nu_max": args.nu_max,
+                   "gamma_odc": params.gamma_odc, "rho_decay": params.rho_decay, "q": "default",
+                   "mask_tile_lr": 4, "tables": info["n_tables"], "blocks": n_blocks,
+                   "launch": [info["grid"], info["warps_per_cta"]], "l2": "flushed between steps",
+                   "parallelism": "independent images per GPU"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(lr_host.numel() * 4),
+                "d2h_bytes_per_step": int(hr_host.numel() * 4)},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": kernel_traffic(args.workload),
+                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (derived)",
+                     "flops_per_block": flops_per_block(args.nu_max)},
+        "clocks": clk,
+    }
+    if cpu_base is not None:
+        line["cpu_baseline"] = cpu_base
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * rljsde.h -- C ABI of the GB300 (sm_103a) RL-JSDE library.
+ *
+ * Reconstructs a 2x-resolution image from three-quarter sampling
+ * measurements with recurrent local joint sparse deconvolution and
+ * extrapolation (RL-JSDE; Grosche, Regensky, Sinn, Seiler, Kaup, TCAS-II
+ * 2022).  The calls follow the paper's statement of the problem:
+ *
+ *   - Sec. II, Eq. 1: each L-pixel value y is the SUM of the three
+ *     transparent HR sub-pixels of its 2x2 footprint; mask[p][q] in 0..3 names
+ *     the opaque one (0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right).
+ *     lr_h x lr_w measurements give a (2 lr_h) x (2 lr_w) HR image.
+ *   - Sec. III: every B x B = 4 x 4 HR target block is rebuilt from a
+ *     W x W = 32 x 32 model window of DFT atoms centred on it; only the
+ *     central block is kept.
+ *   - Sec. IV, Eqs. 11-17: per block, nu_max greedy iterations over the
+ *     W^2 = 1024 candidates on the projected residual R, using tables
+ *     precomputed once per distinct local measurement matrix (a "plan
+ *     entry"); Eq. 18: the model is transformed back.
+ *
+ * Pointer conventions: "host" pointers are read during the call only;
+ * "device" pointers must be CUDA device (or managed) memory on the current
+ * device and stay valid until the work on `stream` has finished.  A NULL
+ * stream is the legacy default stream.  Pitches are in ELEMENTS.
+ *
+ * Errors: every function returns an rljsde_status.  Asynchronous problems a
+ * kernel detects (non-finite input, a table load that did not arrive) are
+ * recorded in a device status word of the plan and reported by
+ * rljsde_check(); no kernel traps.
+ */
+#ifndef RLJSDE_H
+#define RLJSDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RLJSDE_OK = 0,
+    RLJSDE_ERR_INVALID_ARG = 1,     /* NULL pointer, bad parameter value        */
+    RLJSDE_ERR_BAD_SHAPE = 2,       /* lr_h / lr_w not even, or too large        */
+    RLJSDE_ERR_BAD_MASK = 3,        /* a mask code outside 0..3                  */
+    RLJSDE_ERR_OUT_OF_MEMORY = 4,   /* host or device allocation failed          */
+    RLJSDE_ERR_CUDA = 5,            /* a CUDA runtime call failed                */
+    RLJSDE_ERR_TIMEOUT = 6,         /* a bounded device wait gave up             */
+    RLJSDE_ERR_NONFINITE_INPUT = 7, /* NaN/Inf measurement (treated as absent)   */
+    RLJSDE_ERR_UNSUPPORTED = 8      /* valid request this build does not offer   */
+} rljsde_status;
+
+/* Reconstruction parameters.  The paper fixes B and W (Sec. III); it names
+ * nu_max, gamma_odc, the spatial weight w_m and the frequency weight q but
+ * gives no values: the defaults below are this library's readings. */
+typedef struct {
+    int block;            /* B: must be 4 (Sec. III)                                */
+    int window;           /* W: must be 32 (Sec. III)                               */
+    int nu_max;           /* iterations per block, 1..4096 (Sec. IV); default 100   */
+    double gamma_odc;     /* orthogonality deficiency compensation, Eq. 15; 0.5     */
+    double rho_decay;     /* w_m = rho^d_m, d_m the HR-pixel distance from the
+                             L-pixel's 2x2 centre to the block centre (Eq. 8); 0.7  */
+    int q_mode;           /* Eq. 11 frequency weight: 0 = (1 - |kt| / (W/sqrt2))^2
+                             with signed frequency kt; 1 = all ones; 2 = q_table    */
+    const double *q_table;/* host, W*W entries row-major over (sigma, rho), q_mode 2 */
+    int precision;        /* 0 = FP32 loop (tables built in FP64, stored FP32);
+                             1 = FP64 loop                                           */
+    int path;             /* 0 = recurrent (one table set per distinct local
+                             measurement matrix, Eqs. 11-17); 2 = direct L-JSDE
+                             (Eqs. 4-10: residual r kept, O(W^4) projection every
+                             iteration, no tables)                                   */
+} rljsde_params;
+
+/* Fill *p with the defaults above.  Returns RLJSDE_ERR_INVALID_ARG on NULL. */
+int rljsde_default_params(rljsde_params *p);
+
+typedef struct rljsde_plan rljsde_plan_t;   /* opaque; owns all its device memory */
+
+/*
+ * Build a plan for one image size and sensor mask (Sec. IV: "pre-computed and
+ * re-used for all model windows with the same measurement matrix").
+ *   mask: host, lr_h x lr_w codes 0..3, row-major, contiguous.
+ *   lr_h, lr_w: even, 4 .. 32768.
+ * Every target block's local measurement matrix (the window's codes, with
+ * positions outside the image absent) is classified; tables are built in FP64
+ * on the host per distinct one and uploaded.  Synchronous; allocates device
+ * memory on the current device.  *out is NULL on failure.
+ */
+int rljsde_plan_create(rljsde_plan_t **out, const uint8_t *mask, int lr_h, int lr_w,
+                       const rljsde_params *p);
+
+/*
+ * The same for a batch of n_images images of possibly different sizes
+ * (masks[i]: host, lr_h[i] x lr_w[i]).  Blocks of all images go into one
+ * work list; table sets are shared across images.
+ */
+int rljsde_plan_create_batch(rljsde_plan_t **out, int n_images, const uint8_t *const *masks,
+                             const int *lr_h, const int *lr_w, const rljsde_params *p);
+
+/*
+ * Reconstruct one image: lr (device, lr_h x lr_w floats, pitch lr_pitch >= lr_w)
+ * -> hr (device, 2lr_h x 2lr_w floats, pitch hr_pitch >= 2 lr_w).  Every HR
+ * pixel is written.  Only for single-image plans.  Asynchronous on `stream`,
+ * allocates nothing, one kernel launch.
+ */
+int rljsde_reconstruct(const rljsde_plan_t *plan, const float *lr, size_t lr_pitch,
+                       float *hr, size_t hr_pitch, void *stream);
+
+/*
+ * As rljsde_reconstruct, and also records every block's greedy trace:
+ *   sel: device, n_blocks * nu_max uint16 selected linear indices sigma*W+rho;
+ *   dc:  device, n_blocks * nu_max * 2 floats, gamma_odc * delta (re, im);
+ * block b = bi * (2 lr_w / 4) + bj (row-major over target blocks).
+ */
+int rljsde_reconstruct_trace(const rljsde_plan_t *plan, const float *lr, size_t lr_pitch,
+                             float *hr, size_t hr_pitch, uint16_t *sel, float *dc,
+                             void *stream);
+
+/* Device-side description of one image of a batch (device pointers). */
+typedef struct {
+    const float *lr;      /* lr_h x lr_w, pitch lr_pitch  */
+    float *hr;            /* 2lr_h x 2lr_w, pitch hr_pitch */
+    int64_t lr_pitch;
+    int64_t hr_pitch;
+} rljsde_image;
+
+/*
+ * Copy the batch's image pointers (host array of n_images entries, in the
+ * order given at plan creation) into plan-owned device memory.  Synchronous.
+ * Call again whenever buffers change; not needed for single-image plans.
+ */
+int rljsde_set_images(rljsde_plan_t *plan, const rljsde_image *images);
+
+/*
+ * Reconstruct every image of a batch plan in ONE persistent kernel launch.
+ * Reads the pointers stored by rljsde_set_images.  Asynchronous, allocates
+ * nothing, launches exactly one kernel: safe to capture in a CUDA graph.
+ */
+int rljsde_reconstruct_batch(const rljsde_plan_t *plan, void *stream);
+
+/* Launch shape of the persistent kernel: warps per CTA (4 or 8) and resident
+ * CTAs per SM to launch (1..4; clamped to what fits).  0 restores defaults. */
+int rljsde_set_launch(rljsde_plan_t *plan, int warps_per_cta, int ctas_per_sm);
+
+typedef struct {
+    int n_images;
+    int n_blocks;           /* target blocks over all images                  */
+    int n_tables;           /* distinct local measurement matrices (plans)    */
+    int n_interior_tables;  /* of which windows lie wholly inside the image   */
+    int n_work_entries;     /* blocks after padding each table's run          */
+    int warps_per_cta, ctas_per_sm, grid;   /* launch shape in effect         */
+    int64_t device_table_bytes;   /* factored tables actually stored (device) */
+    int64_t paper_B_bytes;        /* Table I equivalent: n_tables x 256 x 1024 x 8 B */
+    int64_t paper_C_bytes;        /* n_tables x 1024^2 x 8 B                  */
+    int64_t paper_D_bytes;        /* n_tables x 1024 x 8 B                    */
+} rljsde_plan_info_t;
+
+int rljsde_plan_info(const rljsde_plan_t *plan, rljsde_plan_info_t *out);
+
+/* Synchronise `stream`, read and clear the plan's device status word.
+ * Returns RLJSDE_OK or the first asynchronous error recorded. */
+int rljsde_check(const rljsde_plan_t *plan, void *stream);
+
+void rljsde_plan_destroy(rljsde_plan_t *plan);
+
+const char *rljsde_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLJSDE_H */

@@ -1,0 +1,100 @@
+// Internal layout shared by the host plan builder (plan.cpp) and the CUDA
+// kernels (kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "rljsde.h"
+
+namespace rljsde {
+
+constexpr int kW = 32;          // model window edge, HR pixels (Sec. III)
+constexpr int kB = 4;           // target block edge, HR pixels (Sec. III)
+constexpr int kL = kW / 2;      // window edge in L-pixels
+constexpr int kK = kW * kW;     // candidate atoms
+constexpr int kOff = (kW - kB) / 2;   // block offset inside the window (14)
+constexpr int kChunk = 8;       // work entries per chunk; one table per chunk
+
+// One image of the work list (device copy for batches).
+struct ImageDesc {
+    const float *lr;
+    float *hr;
+    int lr_h, lr_w;
+    long long lr_pitch, hr_pitch;
+};
+
+// One target block to reconstruct; img < 0 marks padding.
+struct WorkEntry {
+    int img, bi, bj, ord;
+};
+
+// Plan-independent constants: spatial weights w(p, q) of the window's
+// L-pixels and exp(2 pi i n / 32), each in FP32 and FP64.
+struct Consts {
+    float w32[256];
+    float om32[64];     // (re, im) for n = 0..31
+    double w64[256];
+    double om64[64];
+};
+
+template <typename T>
+struct alignas(16) Vec4 {
+    T x, y, z, w;
+};
+
+// Tables of one local measurement matrix in the factored form.
+//
+// With t(m) the opaque quadrant of L-pixel m at window LR position (p, q),
+// the integrated atom of Eq. 4 factors as
+//     a_m(k) = w32^(2 p k1 + 2 q k2) h_t(k),
+//     h_t(k) = sum over the three transparent offsets (e, g) of w32^(e k1 + g k2),
+// so the Gram matrix of Eq. 14 is
+//     C_{k,l} = sum_t conj(h_t(k)) h_t(l) G_t((l - k) mod 16),
+//     G_t(d) = sum_{m: t(m) = t} w_m w16^(p d1 + q d2),
+// and D_k = C_{k,k} (Eq. 13) = sum_t |h_t(k)|^2 G_t(0).
+template <typename T>
+struct Record {
+    Vec4<T> G01[256];     // (G_0(d), G_1(d)) as (re, im, re, im), d = d1 * 16 + d2
+    Vec4<T> G23[256];     // (G_2(d), G_3(d))
+    Vec4<T> qD[256];      // q_k / D_k at k = (kap1 + 16a, kap2 + 16b), entry 2a + b
+    T invD[kK];           // 1 / D_k, k = k1 * 32 + k2
+    uint8_t types[256];   // opaque code per window L-pixel (p * 16 + q), 255 = absent
+};
+static_assert(sizeof(Record<float>) % 16 == 0, "record size must allow bulk copies");
+static_assert(sizeof(Record<double>) % 16 == 0, "record size must allow bulk copies");
+
+}  // namespace rljsde
+
+// The opaque plan object of the C ABI.
+struct rljsde_plan {
+    rljsde_params params{};
+    std::vector<double> q;            // W*W frequency weights (FP64)
+    int n_images = 0;
+    std::vector<int> lr_h, lr_w;
+    int n_blocks = 0, n_tables = 0, n_interior = 0;
+    int n_entries = 0, n_chunks = 0;
+    int direct = 0;                   // path == 2
+    int device = 0, sm_count = 0;
+    int warps = 8, ctas_per_sm = 0, grid = 0;
+    // device memory, all owned by the plan
+    void *d_records = nullptr;        // n_tables records (float or double)
+    size_t record_bytes = 0;
+    rljsde::WorkEntry *d_entries = nullptr;
+    uint32_t *d_chunk_table = nullptr;
+    rljsde::Consts *d_consts = nullptr;
+    float *d_qD = nullptr;            // direct path: W*W q values (float)
+    uint8_t *d_masks = nullptr;       // direct path: all masks, concatenated
+    std::vector<long long> mask_offset;
+    long long *d_mask_offset = nullptr;
+    int *d_status = nullptr;
+    rljsde::ImageDesc *d_images = nullptr;
+    std::vector<int> ord_base;        // first block ordinal of each image
+};
+
+namespace rljsde {
+// Implemented in kernels.cu.
+int choose_launch(rljsde_plan *plan, int warps, int ctas_per_sm);
+const char *last_cuda_error();
+}  // namespace rljsde

@@ -1,0 +1,219 @@
+"""Python binding of the C ABI in ``include/rljsde.h`` (argument marshalling only).
+
+Every step of the reconstruction runs in the CUDA library ``librljsde.so``;
+this module converts numpy masks and torch CUDA tensors into the pointers and
+sizes the ABI takes.  It raises if the library has not been built: there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librljsde.so")
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_SHAPE", 3: "BAD_MASK", 4: "OUT_OF_MEMORY", 5: "CUDA",
+          6: "TIMEOUT", 7: "NONFINITE_INPUT", 8: "UNSUPPORTED"}
+
+
+class RljsdeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (what, _lib().rljsde_status_string(status).decode(),
+                                          STATUS.get(status, status)))
+
+
+class Params(ctypes.Structure):
+    """``rljsde_params``: B, W, nu_max, gamma_odc, rho_decay, q_mode, q_table,
+    precision, path (see the header for meanings and defaults)."""
+    _fields_ = [("block", ctypes.c_int), ("window", ctypes.c_int), ("nu_max", ctypes.c_int),
+                ("gamma_odc", ctypes.c_double), ("rho_decay", ctypes.c_double),
+                ("q_mode", ctypes.c_int), ("q_table", ctypes.POINTER(ctypes.c_double)),
+                ("precision", ctypes.c_int), ("path", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_images", ctypes.c_int), ("n_blocks", ctypes.c_int), ("n_tables", ctypes.c_int),
+                ("n_interior_tables", ctypes.c_int), ("n_work_entries", ctypes.c_int),
+                ("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("grid", ctypes.c_int),
+                ("device_table_bytes", ctypes.c_int64), ("paper_B_bytes", ctypes.c_int64),
+                ("paper_C_bytes", ctypes.c_int64), ("paper_D_bytes", ctypes.c_int64)]
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_void_p), ("hr", ctypes.c_void_p), ("lr_pitch", ctypes.c_int64),
+                ("hr_pitch", ctypes.c_int64)]
+
+
+EXPORTS = ["rljsde_default_params", "rljsde_plan_create", "rljsde_plan_create_batch",
+           "rljsde_reconstruct", "rljsde_reconstruct_trace", "rljsde_set_images",
+           "rljsde_reconstruct_batch", "rljsde_set_launch", "rljsde_plan_info", "rljsde_check",
+           "rljsde_plan_destroy", "rljsde_status_string"]
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librljsde.so is not built (run __graft_entry__.build() or "
+                              "python -m paper_2205_02646_gb300.build); there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        lib.rljsde_default_params.argtypes = [ctypes.POINTER(Params)]
+        lib.rljsde_plan_create.argtypes = [ctypes.POINTER(vp), vp, i, i, ctypes.POINTER(Params)]
+        lib.rljsde_plan_create_batch.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp),
+                                                 ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(Params)]
+        lib.rljsde_reconstruct.argtypes = [vp, vp, sz, vp, sz, vp]
+        lib.rljsde_reconstruct_trace.argtypes = [vp, vp, sz, vp, sz, vp, vp, vp]
+        lib.rljsde_set_images.argtypes = [vp, ctypes.POINTER(Image)]
+        lib.rljsde_reconstruct_batch.argtypes = [vp, vp]
+        lib.rljsde_set_launch.argtypes = [vp, i, i]
+        lib.rljsde_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        lib.rljsde_check.argtypes = [vp, vp]
+        lib.rljsde_plan_destroy.argtypes = [vp]
+        lib.rljsde_plan_destroy.restype = None
+        lib.rljsde_status_string.argtypes = [i]
+        lib.rljsde_status_string.restype = ctypes.c_char_p
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load the shared library (raises ImportError if it is not built)."""
+    return _lib()
+
+
+def _ok(st, what):
+    if st != 0:
+        raise RljsdeError(st, what)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _ok(_lib().rljsde_default_params(ctypes.byref(p)), "rljsde_default_params")
+    q_table = kw.pop("q_table", None)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    if q_table is not None:
+        arr = np.ascontiguousarray(q_table, dtype=np.float64).ravel()
+        p._q_keep = arr
+        p.q_table = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.q_mode = 2
+    return p
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check_tensor(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError("%s must be a float32 CUDA tensor" % name)
+    if t.dim() != 2 or tuple(t.shape) != tuple(shape) or t.stride(1) != 1:
+        raise ValueError("%s must be %s with unit column stride, got %s" % (name, shape, tuple(t.shape)))
+
+
+class Plan:
+    """Owns an ``rljsde_plan_t`` (tables and work list in device memory)."""
+
+    def __init__(self, masks, params: Params | None = None):
+        lib = _lib()
+        self.params = params if params is not None else default_params()
+        single = isinstance(masks, np.ndarray)
+        ms = [np.ascontiguousarray(masks if single else m, dtype=np.uint8)
+              for m in ([masks] if single else masks)]
+        self.shapes = [m.shape for m in ms]
+        self.single = single
+        h = ctypes.c_void_p()
+        if single:
+            st = lib.rljsde_plan_create(ctypes.byref(h), ms[0].ctypes.data, ms[0].shape[0], ms[0].shape[1],
+                                        ctypes.byref(self.params))
+        else:
+            n = len(ms)
+            ptrs = (ctypes.c_void_p * n)(*[m.ctypes.data for m in ms])
+            hs = (ctypes.c_int * n)(*[m.shape[0] for m in ms])
+            ws = (ctypes.c_int * n)(*[m.shape[1] for m in ms])
+            st = lib.rljsde_plan_create_batch(ctypes.byref(h), n, ptrs, hs, ws, ctypes.byref(self.params))
+        _ok(st, "rljsde_plan_create")
+        self._h = h
+        self._images = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        out = PlanInfo()
+        _ok(_lib().rljsde_plan_info(self._h, ctypes.byref(out)), "rljsde_plan_info")
+        return {f: getattr(out, f) for f, _ in PlanInfo._fields_}
+
+    def set_launch(self, warps_per_cta=0, ctas_per_sm=0):
+        _ok(_lib().rljsde_set_launch(self._h, warps_per_cta, ctas_per_sm), "rljsde_set_launch")
+
+    def reconstruct(self, lr, hr, stream=None):
+        lr_h, lr_w = self.shapes[0]
+        _check_tensor(lr, (lr_h, lr_w), "lr")
+        _check_tensor(hr, (2 * lr_h, 2 * lr_w), "hr")
+        _ok(_lib().rljsde_reconstruct(self._h, lr.data_ptr(), lr.stride(0), hr.data_ptr(), hr.stride(0),
+                                      _stream_ptr(stream)), "rljsde_reconstruct")
+
+    def reconstruct_trace(self, lr, hr, sel, dc, stream=None):
+        import torch
+        lr_h, lr_w = self.shapes[0]
+        _check_tensor(lr, (lr_h, lr_w), "lr")
+        _check_tensor(hr, (2 * lr_h, 2 * lr_w), "hr")
+        nb = (lr_h // 2) * (lr_w // 2)
+        nu = self.params.nu_max
+        if sel.dtype != torch.int16 or sel.numel() != nb * nu or not sel.is_cuda:
+            raise ValueError("sel must be a CUDA int16 tensor of n_blocks * nu_max entries")
+        if dc.dtype != torch.float32 or dc.numel() != nb * nu * 2 or not dc.is_cuda:
+            raise ValueError("dc must be a CUDA float32 tensor of n_blocks * nu_max * 2 entries")
+        _ok(_lib().rljsde_reconstruct_trace(self._h, lr.data_ptr(), lr.stride(0), hr.data_ptr(), hr.stride(0),
+                                            sel.data_ptr(), dc.data_ptr(), _stream_ptr(stream)),
+            "rljsde_reconstruct_trace")
+
+    def set_images(self, lrs, hrs):
+        n = len(self.shapes)
+        if len(lrs) != n or len(hrs) != n:
+            raise ValueError("need one lr and one hr tensor per image")
+        arr = (Image * n)()
+        for i, ((lr_h, lr_w), lr, hr) in enumerate(zip(self.shapes, lrs, hrs)):
+            _check_tensor(lr, (lr_h, lr_w), "lr[%d]" % i)
+            _check_tensor(hr, (2 * lr_h, 2 * lr_w), "hr[%d]" % i)
+            arr[i] = Image(lr.data_ptr(), hr.data_ptr(), lr.stride(0), hr.stride(0))
+        _ok(_lib().rljsde_set_images(self._h, arr), "rljsde_set_images")
+        self._images = (list(lrs), list(hrs))       # keep the buffers alive
+
+    def reconstruct_batch(self, stream=None):
+        _ok(_lib().rljsde_reconstruct_batch(self._h, _stream_ptr(stream)), "rljsde_reconstruct_batch")
+
+    def check(self, stream=None):
+        _ok(_lib().rljsde_check(self._h, _stream_ptr(stream)), "rljsde_check")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().rljsde_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle,
+block by block, on seeded synthetic inputs (see ``parity.compare``)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_02646_gb300 import synth
+from parity import compare, mirror
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4          # max-abs on [0, 1] images, FP32 loop vs FP64 oracle
+TIE = 1e-4          # relative score gap below which a departure is a near-tie
+
+
+@pytest.fixture(scope="module")
+def rl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_02646_gb300 import build, rljsde
+    build.build()
+    rljsde.load()
+    return rljsde
+
+
+def gpu_run(rl, y, mask, trace=True, **kw):
+    import torch
+    lr_h, lr_w = mask.shape
+    plan = rl.Plan(mask, rl.default_params(**kw))
+    lr = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).cuda()
+    hr = torch.full((2 * lr_h, 2 * lr_w), float("nan"), device="cuda")
+    nb = (lr_h // 2) * (lr_w // 2)
+    nu = plan.params.nu_max
+    if trace:
+        sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
+        dc = torch.zeros(nb * nu * 2, dtype=torch.float32, device="cuda")
+        plan.reconstruct_trace(lr, hr, sel, dc)
+    else:
+        plan.reconstruct(lr, hr)
+    plan.check()
+    torch.cuda.synchronize()
+    out = dict(hr=hr.cpu().numpy(), plan=plan)
+    if trace:
+        out["sel"] = sel.cpu().numpy().reshape(nb, nu)
+        d = dc.cpu().numpy().reshape(nb, nu, 2)
+        out["dc"] = d[..., 0] + 1j * d[..., 1]
+    return out
+
+
+def oracle_run(y, mask, blocks=None, nu_max=100, **kw):
+    p = oracle.Params(nu_max=nu_max, **kw)
+    hr, tr = oracle.reconstruct(np.asarray(y, np.float64), mask, p, blocks=blocks, trace=True)
+    return hr, tr
+
+
+def check(res, max_tie_frac=0.03):
+    assert not res["fails"], res["fails"][:5]
+    assert res["near_ties"] <= max(1, max_tie_frac * res["n"]), res["tie_blocks"]
+
+
+@pytest.mark.parametrize("index", [0, 1, 2])
+def test_64x64_every_block_vs_oracle(rl, index):
+    f, mask, y = synth.workload("rljsde_64x64", index=index)
+    g = gpu_run(rl, y, mask)
+    hr, tr = oracle_run(y, mask)
+    nbw = mask.shape[1] // 2
+    blocks = np.arange(g["sel"].shape[0])
+    res = compare(g["hr"], g["sel"], hr, tr["sel"], tr["gap"], blocks, nbw, TOL, TIE,
+                  gpu_dc=g["dc"], orc_dc=tr["dc"])
+    check(res)
+    assert np.isfinite(g["hr"]).all()
+    print("64x64 #%d: matched %d / %d, near-ties %d, max err %.3g"
+          % (index, res["matched"], res["n"], res["near_ties"], res["max_err"]))
+
+
+def test_first_selection_ties_resolved_like_oracle(rl):
+    """Iteration 1 has exact conjugate ties; both sides keep the lower index."""
+    f, mask, y = synth.workload("rljsde_64x64", index=3)
+    g = gpu_run(rl, y, mask, nu_max=1)
+    hr, tr = oracle_run(y, mask, nu_max=1)
+    assert np.array_equal(g["sel"][:, 0].astype(np.int64) & 0xFFFF, tr["sel"][:, 0])
+
+
+@pytest.mark.parametrize("lr_shape,tile,seed", [((20, 36), 4, 1), ((4, 4), 2, 2), ((6, 10), 4, 3),
+                                                ((24, 24), 0, 4)])
+def test_ragged_small_and_random_masks(rl, lr_shape, tile, seed):
+    lr_h, lr_w = lr_shape
+    f = synth.image(2 * lr_h, 2 * lr_w, 24, 3, 5000 + seed)
+    mask = synth.random_mask(lr_h, lr_w, seed) if tile == 0 else synth.recurrent_mask(lr_h, lr_w, tile, seed)
+    y = synth.measure(f, mask).astype(np.float32)
+    g = gpu_run(rl, y, mask, nu_max=60)
+    hr, tr = oracle_run(y, mask, nu_max=60)
+    res = compare(g["hr"], g["sel"], hr, tr["sel"], tr["gap"], np.arange(g["sel"].shape[0]),
+                  lr_w // 2, TOL, TIE)
+    check(res)
+
+
+def test_q_modes_and_gamma(rl):
+    f, mask, y = synth.workload("rljsde_64x64", index=4)
+    qt = np.random.default_rng(3).uniform(0.1, 1.0, 1024)
+    for kw in (dict(q_mode=1, gamma_odc=1.0), dict(q_table=qt, gamma_odc=0.3), dict(rho_decay=0.5)):
+        okw = dict(kw)
+        if "q_table" in okw:
+            okw["q_mode"] = 2
+        g = gpu_run(rl, y, mask, nu_max=50, **kw)
+        hr, tr = oracle_run(y, mask, nu_max=50, **okw)
+        res = compare(g["hr"], g["sel"], hr, tr["sel"], tr["gap"], np.arange(g["sel"].shape[0]),
+                      mask.shape[1] // 2, TOL, TIE)
+        check(res)
+
+
+def test_1024_full_size_sampled_blocks(rl):
+    """Full 1024x1024 image in the launch configuration the benchmark uses;
+    the oracle recomputes a sample of blocks one by one (every border and
+    corner type plus random interior blocks)."""
+    f, mask, y = synth.workload("rljsde_1024x1024")
+    g = gpu_run(rl, y, mask, trace=True)
+    nbh, nbw = mask.shape[0] // 2, mask.shape[1] // 2
+    rng = np.random.default_rng(0)
+    edge = [bi * nbw + bj for bi in list(range(4)) + list(range(nbh - 4, nbh))
+            for bj in (0, 1, 2, 3, 100, nbw - 4, nbw - 3, nbw - 2, nbw - 1)]
+    blocks = np.unique(np.concatenate([edge, rng.choice(nbh * nbw, 96, replace=False)]))
+    hr, tr = oracle_run(y, mask, blocks=blocks)
+    res = compare(g["hr"], g["sel"][blocks], hr, tr["sel"], tr["gap"], blocks, nbw, TOL, TIE,
+                  gpu_dc=g["dc"][blocks], orc_dc=tr["dc"])
+    check(res)
+    assert np.isfinite(g["hr"]).all() and g["hr"].shape == (1024, 1024)
+
+
+def test_direct_path_vs_oracle(rl):
+    f, mask, y = synth.workload("rljsde_64x64", index=5)
+    g = gpu_run(rl, y, mask, nu_max=40, path=2)
+    hr, tr = oracle_run(y, mask, nu_max=40)
+    res = compare(g["hr"], g["sel"], hr, tr["sel"], tr["gap"], np.arange(g["sel"].shape[0]),
+                  mask.shape[1] // 2, TOL, TIE, gpu_dc=g["dc"], orc_dc=tr["dc"])
+    check(res)
+
+
+def test_fp64_loop_vs_oracle(rl):
+    f, mask, y = synth.workload("rljsde_64x64", index=6)
+    g = gpu_run(rl, y, mask, precision=1)
+    hr, tr = oracle_run(y, mask)
+    res = compare(g["hr"], g["sel"], hr, tr["sel"], tr["gap"], np.arange(g["sel"].shape[0]),
+                  mask.shape[1] // 2, tol=2e-7, tie=1e-6)      # FP64 loop, FP32 HR output
+    check(res, max_tie_frac=0.01)
+
+
+def test_batch_equals_single_launches(rl):
+    import torch
+    sizes = [(32, 48), (40, 40), (16, 72)]
+    masks, ys = [], []
+    for i, (h, w) in enumerate(sizes):
+        f = synth.image(2 * h, 2 * w, 16, 2, 7000 + i)
+        m = synth.recurrent_mask(h, w, 4, 77)
+        masks.append(m)
+        ys.append(synth.measure(f, m).astype(np.float32))
+    params = rl.default_params(nu_max=30)
+    bp = rl.Plan(masks, params)
+    lrs = [torch.from_numpy(y).cuda() for y in ys]
+    hrs = [torch.zeros((2 * h, 2 * w), device="cuda") for h, w in sizes]
+    bp.set_images(lrs, hrs)
+    bp.reconstruct_batch()
+    bp.check()
+    for m, lr, hrb in zip(masks, lrs, hrs):
+        sp = rl.Plan(m, params)
+        hr1 = torch.zeros_like(hrb)
+        sp.reconstruct(lr, hr1)
+        sp.check()
+        assert torch.equal(hr1, hrb)
+
+
+def test_nonfinite_input_reported(rl):
+    import torch
+    f, mask, y = synth.workload("rljsde_64x64")
+    y = y.copy()
+    y[10, 10] = np.nan
+    plan = rl.Plan(mask, rl.default_params(nu_max=5))
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.zeros((64, 64), device="cuda")
+    plan.reconstruct(lr, hr)
+    with pytest.raises(rl.RljsdeError) as e:
+        plan.check()
+    assert e.value.status == 7
+    plan.check()                        # the status word was cleared
+    assert torch.isfinite(hr).all()
+
+
+def test_plan_info_counts(rl):
+    mask = synth.recurrent_mask(128, 128, 16, 5)
+    plan = rl.Plan(mask)
+    info = plan.info()
+    assert info["n_interior_tables"] == 64                 # Table I: 32^2 / 4^2
+    assert info["paper_C_bytes"] == info["n_tables"] * 1024 * 1024 * 8
+    assert info["n_blocks"] == 64 * 64
