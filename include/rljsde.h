@@ -142,6 +142,26 @@ int rljsde_reconstruct_batch(const rljsde_plan_t *plan, void *stream);
  * CTAs per SM to launch (1..4; clamped to what fits).  0 restores defaults. */
 int rljsde_set_launch(rljsde_plan_t *plan, int warps_per_cta, int ctas_per_sm);
 
+/*
+ * Autotuner (this library's, not the paper's): times every launch shape of
+ * the persistent kernel that fits (warps per CTA x resident CTAs per SM) on
+ * the plan's own work, `reps` timed launches each after one warm-up, and
+ * keeps the fastest on the plan.  lr/hr as for rljsde_reconstruct (single-image
+ * plans), or both NULL to use the images stored by rljsde_set_images.
+ * Synchronous (events on `stream`); writes hr.  Outputs may be NULL.
+ */
+int rljsde_autotune(rljsde_plan_t *plan, const float *lr, size_t lr_pitch, float *hr, size_t hr_pitch,
+                    int reps, void *stream, int *warps_out, int *ctas_out, float *best_ms_out);
+
+/*
+ * Capture one rljsde_reconstruct_batch launch on `stream` (not the legacy
+ * NULL stream) into a CUDA graph owned by the plan, replacing any earlier
+ * one; rljsde_graph_launch replays it.  The graph reads the image pointers
+ * from plan memory, so rljsde_set_images may change them between replays.
+ */
+int rljsde_graph_capture(rljsde_plan_t *plan, void *stream);
+int rljsde_graph_launch(const rljsde_plan_t *plan, void *stream);
+
 typedef struct {
     int n_images;
     int n_blocks;           /* target blocks over all images                  */

@@ -141,29 +141,49 @@ struct Args {
     const float *q;
 };
 
+template <typename T> struct RecOf;
+template <> struct RecOf<float> { using type = RecordF32; };
+template <> struct RecOf<double> { using type = Record<double>; };
+
+// Pair tables of the FP32 loop: for kap1 pair j, (cos, cos, sin, sin) of
+// 2 pi kap1 / 32 for kap1 = 2j, 2j+1, and (-sin, -sin); the same for the
+// angle index n, n+1 of exp(-2 pi i (kap1 + kap2) / 32).
+struct PairTables {
+    float4 e2[8];
+    float2 e2n[8];
+    float4 e12[32];
+    float2 e12n[32];
+};
+
 // Shared memory of the recurrent kernel.
 template <typename T, int WARPS>
 struct SmemLayout {
-    static constexpr size_t rec = sizeof(Record<T>);
-    static constexpr size_t scratch = 256 * 4 * sizeof(C2<T>);   // per warp
+    static constexpr size_t rec = sizeof(typename RecOf<T>::type);
+    static constexpr size_t scratch = 256 * 2 * sizeof(C2<T>);   // per warp
     static constexpr size_t off_slots = 0;
     static constexpr size_t off_scratch = 2 * rec;
     static constexpr size_t off_om = off_scratch + WARPS * scratch;       // 32 x C2<T>
     static constexpr size_t off_omc = off_om + 32 * sizeof(C2<T>);        // 32 x C2<T>
-    static constexpr size_t off_w = off_omc + 32 * sizeof(C2<T>);         // 256 x T
+    static constexpr size_t off_pair = off_omc + 32 * sizeof(C2<T>);      // PairTables
+    static constexpr size_t off_w = off_pair + sizeof(PairTables);        // 256 x T
     static constexpr size_t off_bar = off_w + 256 * sizeof(T);            // 2 x u64
     static constexpr size_t bytes = off_bar + 2 * sizeof(uint64_t);
 };
 
-// ------------------------------------------------------ one target block --
-// Runs steps 1-4 for `we` with the tables in `rec`.  Whole warp.
-template <typename T>
-__device__ __forceinline__ void recurrent_block(const Args &a, const Record<T> &rec, C2<T> *scratch,
-                                                const C2<T> *om, const C2<T> *omc, const T *wt,
-                                                const WorkEntry we, const int lane)
+__device__ __forceinline__ const uint8_t *rec_types(const RecordF32 &r) { return r.types; }
+__device__ __forceinline__ const uint8_t *rec_types(const Record<double> &r) { return r.types; }
+
+// ------------------------------------------- initial projected residual --
+// Steps 1-2 for one block: gather the weighted window and run the 16x16 DFTs
+// per type; returns Y[i][t] for kap = (8h + i, lane & 15), h = lane >> 4.
+template <typename T, typename Rec>
+__device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec, C2<T> *scratch,
+                                                   const C2<T> *omc, const T *wt, const WorkEntry we,
+                                                   const int lane, C2<T> (&Y)[8][4])
 {
     const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
     const int p0 = 2 * we.bi - kOff / 2, q0 = 2 * we.bj - kOff / 2;
+    const uint8_t *types = rec_types(rec);
     __syncwarp();    // the previous block of this warp is done with the scratch
 
     // 1. gather: x(p, q) = w(p, q) y(p, q) into the plane of its type.
@@ -174,7 +194,7 @@ __device__ __forceinline__ void recurrent_block(const Args &a, const Record<T> &
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int q = (lane & 1) * 8 + j, Q = q0 + q;
-            const int code = rec.types[p * 16 + q];
+            const int code = types[p * 16 + q];
             T v = 0;
             if (code < 4 && P >= 0 && P < img.lr_h && Q >= 0 && Q < img.lr_w) {
                 const float y = img.lr[(long long)P * img.lr_pitch + Q];
@@ -208,65 +228,116 @@ __device__ __forceinline__ void recurrent_block(const Args &a, const Record<T> &
             acc[i][3].re += x.w * tw.re; acc[i][3].im += x.w * tw.im;
         }
     }
-    __syncwarp();
-    // Tbuf[p][k2] = 4 complex (t = 0..3), stored as two Vec4.
-    Vec4<T> *tb = reinterpret_cast<Vec4<T> *>(scratch);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int p = 8 * h + i;
-        st4(&tb[(p * 16 + k2) * 2 + 0], Vec4<T>{acc[i][0].re, acc[i][0].im, acc[i][1].re, acc[i][1].im});
-        st4(&tb[(p * 16 + k2) * 2 + 1], Vec4<T>{acc[i][2].re, acc[i][2].im, acc[i][3].re, acc[i][3].im});
-    }
-    __syncwarp();
 
-    // 2b. column DFTs, split by parity of p: half h sums p = 2j + h for
-    // kap1' in [0, 8); then Y(kap1') = E + O and Y(kap1' + 8) = E - O.
+    // 2b. column DFTs, two types at a time through the scratch, split by the
+    // parity of p: half h sums p = 2j + h for kap1' in [0, 8); then
+    // Y(kap1') = E + O and Y(kap1' + 8) = E - O.
+    Vec4<T> *tb = reinterpret_cast<Vec4<T> *>(scratch);     // [p][k2]: 2 complex
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int pass = 0; pass < 2; ++pass) {
+        const int t0 = 2 * pass;
+        __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 4; ++t) acc[i][t] = {0, 0};
+        for (int i = 0; i < 8; ++i)
+            st4(&tb[(8 * h + i) * 16 + k2],
+                Vec4<T>{acc[i][t0].re, acc[i][t0].im, acc[i][t0 + 1].re, acc[i][t0 + 1].im});
+        __syncwarp();
+        C2<T> cc[8][2];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cc[i][0] = cc[i][1] = {0, 0};
 #pragma unroll 2
-    for (int j = 0; j < 8; ++j) {
-        const int p = 2 * j + h;
-        const Vec4<T> t01 = ld4(&tb[(p * 16 + k2) * 2 + 0]);
-        const Vec4<T> t23 = ld4(&tb[(p * 16 + k2) * 2 + 1]);
-        const C2<T> tv[4] = {{t01.x, t01.y}, {t01.z, t01.w}, {t23.x, t23.y}, {t23.z, t23.w}};
+        for (int j = 0; j < 8; ++j) {
+            const int p = 2 * j + h;
+            const Vec4<T> tv = ld4(&tb[p * 16 + k2]);
+            const C2<T> tt[2] = {{tv.x, tv.y}, {tv.z, tv.w}};
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const C2<T> tw = omc[(2 * p * i) & 31];
+            for (int i = 0; i < 8; ++i) {
+                const C2<T> tw = omc[(2 * p * i) & 31];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                acc[i][t].re += tv[t].re * tw.re - tv[t].im * tw.im;
-                acc[i][t].im += tv[t].re * tw.im + tv[t].im * tw.re;
+                for (int u = 0; u < 2; ++u) {
+                    cc[i][u].re += tt[u].re * tw.re - tt[u].im * tw.im;
+                    cc[i][u].im += tt[u].re * tw.im + tt[u].im * tw.re;
+                }
             }
         }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const T ore = __shfl_xor_sync(0xffffffffu, cc[i][u].re, 16);
+                const T oim = __shfl_xor_sync(0xffffffffu, cc[i][u].im, 16);
+                // h = 0 holds E and receives O: Y = E + O; h = 1 holds O: Y = E - O
+                Y[i][t0 + u] = h == 0 ? C2<T>{cc[i][u].re + ore, cc[i][u].im + oim}
+                                      : C2<T>{ore - cc[i][u].re, oim - cc[i][u].im};
+            }
     }
-    C2<T> Y[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const T ore = __shfl_xor_sync(0xffffffffu, acc[i][t].re, 16);
-            const T oim = __shfl_xor_sync(0xffffffffu, acc[i][t].im, 16);
-            // h = 0 holds E and receives O: Y = E + O; h = 1 holds O: Y = E - O
-            Y[i][t] = h == 0 ? C2<T>{acc[i][t].re + ore, acc[i][t].im + oim}
-                             : C2<T>{ore - acc[i][t].re, oim - acc[i][t].im};
-        }
+}
 
-    // 3. greedy loop on the factored projected residual.
+// Keep the best (score, index, R) of one candidate; candidates arrive in
+// increasing index order, so a strict > keeps the lowest index on ties.
+template <typename T>
+__device__ __forceinline__ void keep_best(T s, int k, T re, T im, T &bs, int &bk, T &bre, T &bim)
+{
+    if (s > bs) { bs = s; bk = k; bre = re; bim = im; }
+}
+
+// Warp argmax over (score, index), ties to the lowest index.
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T &bs, int &bk)
+{
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const T os = __shfl_xor_sync(0xffffffffu, bs, m);
+        const int ok = __shfl_xor_sync(0xffffffffu, bk, m);
+        if (os > bs || (os == bs && ok < bk)) { bs = os; bk = ok; }
+    }
+}
+
+// Per-iteration bookkeeping shared by both loops: delta, the update
+// coefficients g_t = gamma delta h_t(uv) and the synthesis of Eq. 18.
+template <typename T>
+__device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, const T invD, const T gamma,
+                                            const int bk, const T Rre, const T Rim, const int eta, const int gam,
+                                            const int lane, const long long trow, const int it, int &u, int &v,
+                                            C2<T> (&g)[4], T &fpix)
+{
+    const C2<T> gd = {gamma * (Rre * invD), gamma * (Rim * invD)};   // gamma * delta (Eqs. 15, 16)
+    u = bk >> 5;
+    v = bk & 31;
+    // h_t(uv) = P - e_t with P = 1 + w^v + w^u + w^(u+v)
+    const C2<T> ev = om[v], eu = om[u], euv = om[(u + v) & 31];
+    const C2<T> P = cadd(cadd(cadd(C2<T>{1, 0}, ev), eu), euv);
+    g[0] = cmul(gd, csub(P, C2<T>{1, 0}));
+    g[1] = cmul(gd, csub(P, ev));
+    g[2] = cmul(gd, csub(P, eu));
+    g[3] = cmul(gd, csub(P, euv));
+    const C2<T> ph = om[(eta * u + gam * v) & 31];
+    fpix += gd.re * ph.re - gd.im * ph.im;
+    if (a.trace_sel != nullptr && lane == 0) {
+        a.trace_sel[trow + it] = (uint16_t)bk;
+        a.trace_dc[2 * (trow + it)] = (float)gd.re;
+        a.trace_dc[2 * (trow + it) + 1] = (float)gd.im;
+    }
+}
+
+// ------------------------------------------------------ FP64 (scalar) loop --
+template <typename T>
+__device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec, const C2<T> *om,
+                                            const C2<T> *omc, const WorkEntry we, const int lane,
+                                            C2<T> (&Y)[8][4])
+{
+    const int k2 = lane & 15, h = lane >> 4;
     const C2<T> e1 = omc[k2];                       // exp(-2 pi i kap2 / 32)
     const T gamma = (T)a.gamma;
     const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
     T fpix = 0;                                     // Eq. 18 accumulator
     int u = 0, v = 0;
     C2<T> g[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    const bool tracing = a.trace_sel != nullptr;
     const long long trow = (long long)we.ord * a.nu_max;
 
     for (int it = 0; it < a.nu_max; ++it) {
-        T bs0 = -1, bs1 = -1;
+        T bs0 = -1, bs1 = -1, b0re = 0, b0im = 0, b1re = 0, b1im = 0;
         int bk0 = 0, bk1 = 0;
-        C2<T> bR0 = {0, 0}, bR1 = {0, 0};
         const int d2 = (v - k2) & 15;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -288,78 +359,207 @@ __device__ __forceinline__ void recurrent_block(const Args &a, const Record<T> &
             const C2<T> pp = cadd(Z0, U), mm = csub(Z0, U), ss = cadd(V, X), dd = csub(V, X);
             const C2<T> R00 = cadd(pp, ss), R01 = cadd(mm, dd), R10 = csub(pp, ss), R11 = csub(mm, dd);
             const Vec4<T> qd = ld4(&rec.qD[k1 * 16 + k2]);
-            const T s00 = qd.x * (R00.re * R00.re + R00.im * R00.im);
-            const T s01 = qd.y * (R01.re * R01.re + R01.im * R01.im);
-            const T s10 = qd.z * (R10.re * R10.re + R10.im * R10.im);
-            const T s11 = qd.w * (R11.re * R11.re + R11.im * R11.im);
             const int k = k1 * kW + k2;
-            // visited in increasing k within each half a: strict > keeps the lowest index
-            if (s00 > bs0) { bs0 = s00; bk0 = k; bR0 = R00; }
-            if (s01 > bs0) { bs0 = s01; bk0 = k + 16; bR0 = R01; }
-            if (s10 > bs1) { bs1 = s10; bk1 = k + 512; bR1 = R10; }
-            if (s11 > bs1) { bs1 = s11; bk1 = k + 528; bR1 = R11; }
+            keep_best(qd.x * (R00.re * R00.re + R00.im * R00.im), k, R00.re, R00.im, bs0, bk0, b0re, b0im);
+            keep_best(qd.y * (R01.re * R01.re + R01.im * R01.im), k + 16, R01.re, R01.im, bs0, bk0, b0re, b0im);
+            keep_best(qd.z * (R10.re * R10.re + R10.im * R10.im), k + 512, R10.re, R10.im, bs1, bk1, b1re, b1im);
+            keep_best(qd.w * (R11.re * R11.re + R11.im * R11.im), k + 528, R11.re, R11.im, bs1, bk1, b1re, b1im);
         }
-        if (bs1 > bs0) { bs0 = bs1; bk0 = bk1; bR0 = bR1; }
-        // warp argmax, ties to the lowest index
+        if (bs1 > bs0) { bs0 = bs1; bk0 = bk1; b0re = b1re; b0im = b1im; }
         T bs = bs0;
         int bk = bk0;
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) {
-            const T os = __shfl_xor_sync(0xffffffffu, bs, m);
-            const int ok = __shfl_xor_sync(0xffffffffu, bk, m);
-            if (os > bs || (os == bs && ok < bk)) { bs = os; bk = ok; }
-        }
+        warp_argmax(bs, bk);
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;    // lane owning kap = (k1 & 15, k2 & 15)
-        const T Rre = __shfl_sync(0xffffffffu, bR0.re, wl);
-        const T Rim = __shfl_sync(0xffffffffu, bR0.im, wl);
-        const T invD = rec.invD[bk];
-        const C2<T> gd = {gamma * (Rre * invD), gamma * (Rim * invD)};   // gamma * delta
-        u = bk >> 5;
-        v = bk & 31;
-        // h_t(uv) = P - e_t with P = 1 + w^v + w^u + w^(u+v)
-        const C2<T> ev = om[v], eu = om[u], euv = om[(u + v) & 31];
-        const C2<T> P = cadd(cadd(cadd(C2<T>{1, 0}, ev), eu), euv);
-        g[0] = cmul(gd, csub(P, C2<T>{1, 0}));
-        g[1] = cmul(gd, csub(P, ev));
-        g[2] = cmul(gd, csub(P, eu));
-        g[3] = cmul(gd, csub(P, euv));
-        const C2<T> ph = om[(eta * u + gam * v) & 31];
-        fpix += gd.re * ph.re - gd.im * ph.im;
-        if (tracing && lane == 0) {
-            a.trace_sel[trow + it] = (uint16_t)bk;
-            a.trace_dc[2 * (trow + it)] = (float)gd.re;
-            a.trace_dc[2 * (trow + it) + 1] = (float)gd.im;
-        }
+        const T Rre = __shfl_sync(0xffffffffu, b0re, wl);
+        const T Rim = __shfl_sync(0xffffffffu, b0im, wl);
+        select_step<T>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
     }
-
-    // 4. central block -> HR image
     if (lane < 16) {
+        const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
         const int yy = 4 * we.bi + (lane >> 2), xx = 4 * we.bj + (lane & 3);
         img.hr[(long long)yy * img.hr_pitch + xx] = (float)fpix;
     }
 }
 
+// ------------------------------------------------- FP32 (f32x2) loop --
+// The same iteration with two frequencies kap1 = 8h + 2jj, 8h + 2jj + 1 in
+// the two halves of each packed register (Blackwell FFMA2 / FADD2 / FMUL2):
+// every element still sees exactly the scalar loop's IEEE operations.
+struct CP { float2 re, im; };     // two complex numbers, split re / im
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+// Shared-memory loads the compiler may not hoist out of the iteration loop:
+// the tables are loop-invariant, but keeping them in registers across
+// iterations would cost more registers (occupancy) than the loads cost.
+__device__ __forceinline__ float4 lds4(const void *p)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(smem_addr(p)));
+    return v;
+}
+__device__ __forceinline__ float2 lds2(const void *p)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(smem_addr(p)));
+    return v;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ CP addc(CP a, CP b) { return {add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ CP subc(CP a, CP b) { return {sub2(a.re, b.re), sub2(a.im, b.im)}; }
+// exp(-i theta) * z with c = cos theta, s = sin theta, ns = -s
+__device__ __forceinline__ CP rot(float2 c, float2 s, float2 ns, CP z)
+{
+    return {fma2(s, z.im, mul2(c, z.re)), fma2(ns, z.re, mul2(c, z.im))};
+}
+__device__ __forceinline__ float2 energy(float2 q, CP r) { return mul2(q, fma2(r.im, r.im, mul2(r.re, r.re))); }
+
+__device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &rec, const C2<float> *om,
+                                                const C2<float> *omc, const PairTables &pt, const WorkEntry we,
+                                                const int lane, C2<float> (&Y0)[8][4])
+{
+    const int k2 = lane & 15, h = lane >> 4;
+    CP Y[4][4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            Y[jj][t] = {f2(Y0[2 * jj][t].re, Y0[2 * jj + 1][t].re), f2(Y0[2 * jj][t].im, Y0[2 * jj + 1][t].im)};
+    const float c1 = om[k2].re, s1 = om[k2].im;     // exp(-2 pi i kap2 / 32) = c1 - i s1
+    const float2 e1c = f2(c1, c1), e1s = f2(s1, s1), e1n = f2(-s1, -s1);
+    const float gamma = (float)a.gamma;
+    const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
+    float fpix = 0.f;
+    int u = 0, v = 0;
+    C2<float> g[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    const long long trow = (long long)we.ord * a.nu_max;
+
+    for (int it = 0; it < a.nu_max; ++it) {
+        float bs0 = -1.f, bs1 = -1.f, b0re = 0.f, b0im = 0.f, b1re = 0.f, b1im = 0.f;
+        int bk0 = 0, bk1 = 0;
+        const int d2 = (v - k2) & 15;
+        float2 ngre[4], gim[4], ngim[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            ngre[t] = f2(-g[t].re, -g[t].re);
+            gim[t] = f2(g[t].im, g[t].im);
+            ngim[t] = f2(-g[t].im, -g[t].im);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int k1 = 8 * h + 2 * jj;               // first of the pair
+            if (it > 0) {
+                // Eq. 17 on the factored state: Y_t -= g_t G_t((uv - kap) mod 16)
+                const int d1 = (u - k1) & 15;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float4 G = *reinterpret_cast<const float4 *>(rec.GP[t][d1][d2]);
+                    const float2 Gre = f2(G.x, G.y), Gim = f2(G.z, G.w);
+                    Y[jj][t].re = fma2(Gim, gim[t], fma2(Gre, ngre[t], Y[jj][t].re));
+                    Y[jj][t].im = fma2(Gre, ngim[t], fma2(Gim, ngre[t], Y[jj][t].im));
+                }
+            }
+            const CP S = addc(addc(Y[jj][0], Y[jj][1]), addc(Y[jj][2], Y[jj][3]));
+            const CP Z0 = subc(S, Y[jj][0]);
+            const CP U = rot(e1c, e1s, e1n, subc(S, Y[jj][1]));
+            const float4 e2 = lds4(&pt.e2[4 * h + jj]);
+            const CP V = rot(f2(e2.x, e2.y), f2(e2.z, e2.w), lds2(&pt.e2n[4 * h + jj]), subc(S, Y[jj][2]));
+            const float4 e12 = lds4(&pt.e12[k1 + k2]);
+            const CP X = rot(f2(e12.x, e12.y), f2(e12.z, e12.w), lds2(&pt.e12n[k1 + k2]), subc(S, Y[jj][3]));
+            const CP pp = addc(Z0, U), mm = subc(Z0, U), ss = addc(V, X), dd = subc(V, X);
+            const CP R00 = addc(pp, ss), R01 = addc(mm, dd), R10 = subc(pp, ss), R11 = subc(mm, dd);
+            const float4 q0 = lds4(rec.qDP[4 * h + jj][0][k2]);
+            const float4 q1 = lds4(rec.qDP[4 * h + jj][1][k2]);
+            const float2 s00 = energy(f2(q0.x, q0.y), R00), s01 = energy(f2(q0.z, q0.w), R01);
+            const float2 s10 = energy(f2(q1.x, q1.y), R10), s11 = energy(f2(q1.z, q1.w), R11);
+            const int ka = k1 * kW + k2, kb = ka + kW;
+            keep_best(s00.x, ka, R00.re.x, R00.im.x, bs0, bk0, b0re, b0im);
+            keep_best(s01.x, ka + 16, R01.re.x, R01.im.x, bs0, bk0, b0re, b0im);
+            keep_best(s00.y, kb, R00.re.y, R00.im.y, bs0, bk0, b0re, b0im);
+            keep_best(s01.y, kb + 16, R01.re.y, R01.im.y, bs0, bk0, b0re, b0im);
+            keep_best(s10.x, ka + 512, R10.re.x, R10.im.x, bs1, bk1, b1re, b1im);
+            keep_best(s11.x, ka + 528, R11.re.x, R11.im.x, bs1, bk1, b1re, b1im);
+            keep_best(s10.y, kb + 512, R10.re.y, R10.im.y, bs1, bk1, b1re, b1im);
+            keep_best(s11.y, kb + 528, R11.re.y, R11.im.y, bs1, bk1, b1re, b1im);
+        }
+        if (bs1 > bs0) { bs0 = bs1; bk0 = bk1; b0re = b1re; b0im = b1im; }
+        float bs = bs0;
+        int bk = bk0;
+        warp_argmax(bs, bk);
+        const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;
+        const float Rre = __shfl_sync(0xffffffffu, b0re, wl);
+        const float Rim = __shfl_sync(0xffffffffu, b0im, wl);
+        select_step<float>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
+    }
+    if (lane < 16) {
+        const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
+        const int yy = 4 * we.bi + (lane >> 2), xx = 4 * we.bj + (lane & 3);
+        img.hr[(long long)yy * img.hr_pitch + xx] = fpix;
+    }
+}
+
+template <typename T> struct Loop;
+template <> struct Loop<float> {
+    static __device__ __forceinline__ void run(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+                                               const C2<float> *om, const C2<float> *omc, const PairTables &pt,
+                                               const float *wt, const WorkEntry we, const int lane)
+    {
+        C2<float> Y[8][4];
+        initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
+        greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
+    }
+};
+template <> struct Loop<double> {
+    static __device__ __forceinline__ void run(const Args &a, const Record<double> &rec, C2<double> *scratch,
+                                               const C2<double> *om, const C2<double> *omc, const PairTables &,
+                                               const double *wt, const WorkEntry we, const int lane)
+    {
+        C2<double> Y[8][4];
+        initial_projection<double>(a, rec, scratch, omc, wt, we, lane, Y);
+        greedy_loop<double>(a, rec, om, omc, we, lane, Y);
+    }
+};
+
 // --------------------------------------------------- persistent kernel --
-template <typename T, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, (sizeof(T) == 4 ? 16 / WARPS : 1)) recurrent_kernel(const Args a)
+template <typename T, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args a)
 {
     using L = SmemLayout<T, WARPS>;
+    using Rec = typename RecOf<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
-    auto slot = [&](int s) { return reinterpret_cast<Record<T> *>(smem + L::off_slots + s * L::rec); };
+    auto slot = [&](int s) { return reinterpret_cast<Rec *>(smem + L::off_slots + s * L::rec); };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     C2<T> *scratch = reinterpret_cast<C2<T> *>(smem + L::off_scratch + warp * L::scratch);
     C2<T> *om = reinterpret_cast<C2<T> *>(smem + L::off_om);
     C2<T> *omc = reinterpret_cast<C2<T> *>(smem + L::off_omc);
+    PairTables *pt = reinterpret_cast<PairTables *>(smem + L::off_pair);
     T *wt = reinterpret_cast<T *>(smem + L::off_w);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::off_bar);
 
-    for (int i = threadIdx.x; i < 256; i += WARPS * 32)
-        wt[i] = sizeof(T) == 8 ? (T)a.consts->w64[i] : (T)a.consts->w32[i];
+    for (int i = threadIdx.x; i < 256; i += WARPS * 32) {
+        if constexpr (sizeof(T) == 8) wt[i] = a.consts->w64[i];
+        else wt[i] = a.consts->w32[i];
+    }
     for (int i = threadIdx.x; i < 32; i += WARPS * 32) {
-        const T re = sizeof(T) == 8 ? (T)a.consts->om64[2 * i] : (T)a.consts->om32[2 * i];
-        const T im = sizeof(T) == 8 ? (T)a.consts->om64[2 * i + 1] : (T)a.consts->om32[2 * i + 1];
+        T re, im;
+        if constexpr (sizeof(T) == 8) { re = a.consts->om64[2 * i]; im = a.consts->om64[2 * i + 1]; }
+        else { re = a.consts->om32[2 * i]; im = a.consts->om32[2 * i + 1]; }
         om[i] = {re, im};
         omc[i] = {re, -im};
+        const float c0 = a.consts->om32[2 * i], s0 = a.consts->om32[2 * i + 1];
+        const int n1 = (i + 1) & 31;
+        const float c1 = a.consts->om32[2 * n1], s1 = a.consts->om32[2 * n1 + 1];
+        pt->e12[i] = make_float4(c0, c1, s0, s1);
+        pt->e12n[i] = make_float2(-s0, -s1);
+        if (i < 8) {
+            const float ca = a.consts->om32[4 * i], sa = a.consts->om32[4 * i + 1];
+            const float cb = a.consts->om32[4 * i + 2], sb = a.consts->om32[4 * i + 3];
+            pt->e2[i] = make_float4(ca, cb, sa, sb);
+            pt->e2n[i] = make_float2(-sa, -sb);
+        }
     }
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -395,7 +595,7 @@ __global__ void __launch_bounds__(WARPS * 32, (sizeof(T) == 4 ? 16 / WARPS : 1))
         }
         for (int e = warp; e < kChunk; e += WARPS) {
             const WorkEntry we = a.entries[(size_t)c * kChunk + e];
-            if (we.img >= 0) recurrent_block<T>(a, *slot(s), scratch, om, omc, wt, we, lane);
+            if (we.img >= 0) Loop<T>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane);
         }
         __syncthreads();                       // every warp is done with slot s
         const int c2 = blockIdx.x + (r + 2) * gridDim.x;
@@ -569,21 +769,27 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
 }
 
 // -------------------------------------------------------------- launch --
-template <typename T, int WARPS>
-cudaError_t set_smem_attr()
-{
-    return cudaFuncSetAttribute(recurrent_kernel<T, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SmemLayout<T, WARPS>::bytes);
-}
+// Instantiations of the persistent kernel: loop precision, warps per CTA and
+// the minimum resident CTAs per SM the register budget is sized for.
+struct Variant {
+    int fp64, warps, minb;
+    void (*fn)(Args);
+    size_t smem;
+};
+#define RLJSDE_VARIANT(T, W, M) {sizeof(T) == 8, W, M, recurrent_kernel<T, W, M>, SmemLayout<T, W>::bytes}
+const Variant kVariants[] = {
+    RLJSDE_VARIANT(float, 4, 3), RLJSDE_VARIANT(float, 4, 4), RLJSDE_VARIANT(float, 8, 2),
+    RLJSDE_VARIANT(float, 8, 1), RLJSDE_VARIANT(double, 4, 1), RLJSDE_VARIANT(double, 8, 1),
+};
+#undef RLJSDE_VARIANT
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-template <typename T, int WARPS>
-int occupancy()
+int occupancy(const Variant &v)
 {
     int n = 0;
-    if (set_smem_attr<T, WARPS>() != cudaSuccess) return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, recurrent_kernel<T, WARPS>, WARPS * 32,
-                                                      SmemLayout<T, WARPS>::bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem) != cudaSuccess)
         return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v.fn, v.warps * 32, v.smem) != cudaSuccess) return -1;
     return n;
 }
 
@@ -610,16 +816,9 @@ int launch(const rljsde_plan *p, const Args &a, cudaStream_t s)
 {
     if (p->direct) {
         direct_kernel<<<p->grid, kDirectWarps * 32, 0, s>>>(a, p->n_entries);
-    } else if (p->params.precision == 1) {
-        if (p->warps == 4)
-            recurrent_kernel<double, 4><<<p->grid, 128, SmemLayout<double, 4>::bytes, s>>>(a);
-        else
-            recurrent_kernel<double, 8><<<p->grid, 256, SmemLayout<double, 8>::bytes, s>>>(a);
     } else {
-        if (p->warps == 4)
-            recurrent_kernel<float, 4><<<p->grid, 128, SmemLayout<float, 4>::bytes, s>>>(a);
-        else
-            recurrent_kernel<float, 8><<<p->grid, 256, SmemLayout<float, 8>::bytes, s>>>(a);
+        const Variant &v = kVariants[p->variant];
+        v.fn<<<p->grid, v.warps * 32, v.smem, s>>>(a);
     }
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
@@ -640,13 +839,28 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
         p->grid = (int)(want < g ? (want > 0 ? want : 1) : g);
         return RLJSDE_OK;
     }
-    if (warps == 0) warps = 8;
-    int occ = p->params.precision ? (warps == 4 ? occupancy<double, 4>() : occupancy<double, 8>())
-                                  : (warps == 4 ? occupancy<float, 4>() : occupancy<float, 8>());
-    if (occ < 0) return RLJSDE_ERR_CUDA;
-    if (occ == 0) return RLJSDE_ERR_UNSUPPORTED;
+    // Default: 4 warps per CTA, as many CTAs as the 168-register variant fits.
+    if (warps == 0) { warps = 4; if (ctas_per_sm == 0) ctas_per_sm = 3; }
+    const int fp64 = p->params.precision == 1;
+    // The variant with this precision and warp count whose register budget
+    // admits the requested CTAs per SM (the largest one not above it).
+    int best = -1, best_occ = 0;
+    for (int pass = 0; pass < 2 && best < 0; ++pass)    // second pass: smallest budget above the request
+        for (int i = 0; i < kNumVariants; ++i) {
+            const Variant &v = kVariants[i];
+            if (v.fp64 != fp64 || v.warps != warps) continue;
+            if (pass == 0 && ctas_per_sm > 0 && v.minb > ctas_per_sm) continue;
+            const int occ = occupancy(v);
+            if (occ < 0) return RLJSDE_ERR_CUDA;
+            if (occ == 0) continue;
+            const bool better = best < 0 || (pass == 0 ? v.minb > kVariants[best].minb
+                                                       : v.minb < kVariants[best].minb);
+            if (better) { best = i; best_occ = occ; }
+        }
+    if (best < 0) return RLJSDE_ERR_UNSUPPORTED;
+    p->variant = best;
     p->warps = warps;
-    p->ctas_per_sm = ctas_per_sm > 0 ? (ctas_per_sm < occ ? ctas_per_sm : occ) : occ;
+    p->ctas_per_sm = ctas_per_sm > 0 ? (ctas_per_sm < best_occ ? ctas_per_sm : best_occ) : best_occ;
     long long g = (long long)p->sm_count * p->ctas_per_sm;
     p->grid = (int)(p->n_chunks < g ? (p->n_chunks > 0 ? p->n_chunks : 1) : g);
     return RLJSDE_OK;
@@ -684,6 +898,82 @@ int rljsde_reconstruct_batch(const rljsde_plan_t *plan, void *stream)
     Args a = make_args(plan);
     a.descs = plan->d_images;
     return launch(plan, a, (cudaStream_t)stream);
+}
+
+int rljsde_autotune(rljsde_plan_t *plan, const float *lr, size_t lr_pitch, float *hr, size_t hr_pitch, int reps,
+                    void *stream, int *warps_out, int *ctas_out, float *ms_out)
+{
+    if (!plan || reps < 1 || reps > 1000) return RLJSDE_ERR_INVALID_ARG;
+    if ((lr == nullptr) != (hr == nullptr)) return RLJSDE_ERR_INVALID_ARG;
+    if (lr && plan->n_images != 1) return RLJSDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Args a = make_args(plan);
+    if (lr) {
+        if (lr_pitch < (size_t)plan->lr_w[0] || hr_pitch < (size_t)(2 * plan->lr_w[0])) return RLJSDE_ERR_INVALID_ARG;
+        a.single = {lr, hr, plan->lr_h[0], plan->lr_w[0], (long long)lr_pitch, (long long)hr_pitch};
+    } else {
+        a.descs = plan->d_images;
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return RLJSDE_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return RLJSDE_ERR_CUDA; }
+    const int keep_w = plan->warps, keep_c = plan->ctas_per_sm;
+    float best_ms = 1e30f;
+    int best_w = keep_w, best_c = keep_c, st = RLJSDE_OK;
+    const int shapes[][2] = {{4, 1}, {4, 2}, {4, 3}, {4, 4}, {8, 1}, {8, 2}};
+    for (const auto &sh : shapes) {
+        if (plan->direct) break;
+        if (choose_launch(plan, sh[0], sh[1]) != RLJSDE_OK) continue;
+        if (plan->ctas_per_sm != sh[1]) continue;          // did not fit
+        if ((st = launch(plan, a, s)) != RLJSDE_OK) break; // warm-up
+        float ms = 1e30f;
+        for (int r = 0; r < reps && st == RLJSDE_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = launch(plan, a, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = RLJSDE_ERR_CUDA; break; }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t < ms) ms = t;
+        }
+        if (st != RLJSDE_OK) break;
+        if (ms < best_ms) { best_ms = ms; best_w = sh[0]; best_c = sh[1]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int st2 = choose_launch(plan, best_w, best_c);
+    if (st == RLJSDE_OK) st = st2;
+    if (warps_out) *warps_out = plan->warps;
+    if (ctas_out) *ctas_out = plan->ctas_per_sm;
+    if (ms_out) *ms_out = best_ms < 1e29f ? best_ms : 0.f;
+    (void)keep_w; (void)keep_c;
+    return st;
+}
+
+int rljsde_graph_capture(rljsde_plan_t *plan, void *stream)
+{
+    if (!plan) return RLJSDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s == nullptr) return RLJSDE_ERR_INVALID_ARG;      // the legacy stream cannot be captured
+    if (plan->graph_exec) { cudaGraphExecDestroy((cudaGraphExec_t)plan->graph_exec); plan->graph_exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RLJSDE_ERR_CUDA;
+    int st = rljsde_reconstruct_batch(plan, stream);
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (st != RLJSDE_OK || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return st ? st : RLJSDE_ERR_CUDA; }
+    cudaGraphExec_t ex = nullptr;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return RLJSDE_ERR_CUDA;
+    plan->graph_exec = ex;
+    return RLJSDE_OK;
+}
+
+int rljsde_graph_launch(const rljsde_plan_t *plan, void *stream)
+{
+    if (!plan || !plan->graph_exec) return RLJSDE_ERR_INVALID_ARG;
+    return cudaGraphLaunch((cudaGraphExec_t)plan->graph_exec, (cudaStream_t)stream) == cudaSuccess
+               ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -71,15 +71,19 @@ void window_key(const uint8_t *mask, int lr_h, int lr_w, int bi, int bj, uint8_t
     }
 }
 
-// FP64 factored tables of one local measurement matrix.
-template <typename T>
-void build_record(const uint8_t *key, const double *w, const Cd *r32, const std::vector<double> &q,
-                  Record<T> *rec)
+// FP64 factored tables of one local measurement matrix:
+//   G_t(d) = sum_{m: t(m) = t} w_m w16^(p d1 + q d2),  w16^n = w32^(2n),
+//   D_k    = sum_t |h_t(k)|^2 G_t(0)  (= C_{k,k}, Eq. 13),
+//   h_t(k) = sum over the three transparent offsets of w32^(e k1 + g k2).
+struct Tables {
+    double Gre[4][256], Gim[4][256];
+    double D[kK];
+};
+
+void build_tables(const uint8_t *key, const double *w, const Cd *r32, Tables &T)
 {
-    // G_t(d) = sum_{m: t(m) = t} w_m w16^(p d1 + q d2),  w16^n = w32^(2n)
-    static thread_local double Gre[4][256], Gim[4][256];
     for (int t = 0; t < 4; ++t)
-        for (int d = 0; d < 256; ++d) Gre[t][d] = Gim[t][d] = 0.0;
+        for (int d = 0; d < 256; ++d) T.Gre[t][d] = T.Gim[t][d] = 0.0;
     for (int p = 0; p < kL; ++p)
         for (int qq = 0; qq < kL; ++qq) {
             int t = key[p * kL + qq];
@@ -88,16 +92,10 @@ void build_record(const uint8_t *key, const double *w, const Cd *r32, const std:
             for (int d1 = 0; d1 < 16; ++d1)
                 for (int d2 = 0; d2 < 16; ++d2) {
                     const Cd &e = r32[(2 * (p * d1 + qq * d2)) & 31];
-                    Gre[t][d1 * 16 + d2] += wm * e.re;
-                    Gim[t][d1 * 16 + d2] += wm * e.im;
+                    T.Gre[t][d1 * 16 + d2] += wm * e.re;
+                    T.Gim[t][d1 * 16 + d2] += wm * e.im;
                 }
         }
-    for (int d = 0; d < 256; ++d) {
-        rec->G01[d] = {(T)Gre[0][d], (T)Gim[0][d], (T)Gre[1][d], (T)Gim[1][d]};
-        rec->G23[d] = {(T)Gre[2][d], (T)Gim[2][d], (T)Gre[3][d], (T)Gim[3][d]};
-    }
-    // D_k = sum_t |h_t(k)|^2 G_t(0), h_t(k) = sum of the three transparent phases
-    double D[kK];
     for (int k1 = 0; k1 < kW; ++k1)
         for (int k2 = 0; k2 < kW; ++k2) {
             double dk = 0.0;
@@ -110,27 +108,71 @@ void build_record(const uint8_t *key, const double *w, const Cd *r32, const std:
                         hre += z.re;
                         him += z.im;
                     }
-                dk += (hre * hre + him * him) * Gre[t][0];
+                dk += (hre * hre + him * him) * T.Gre[t][0];
             }
-            D[k1 * kW + k2] = dk;
+            T.D[k1 * kW + k2] = dk;
         }
-    for (int k = 0; k < kK; ++k) rec->invD[k] = D[k] > 1e-300 ? (T)(1.0 / D[k]) : (T)0;
+}
+
+inline double inv_or_zero(double num, double den) { return den > 1e-300 ? num / den : 0.0; }
+
+void build_record64(const uint8_t *key, const double *w, const Cd *r32, const std::vector<double> &q,
+                    Record<double> *rec)
+{
+    static thread_local Tables T;
+    build_tables(key, w, r32, T);
+    for (int d = 0; d < 256; ++d) {
+        rec->G01[d] = {T.Gre[0][d], T.Gim[0][d], T.Gre[1][d], T.Gim[1][d]};
+        rec->G23[d] = {T.Gre[2][d], T.Gim[2][d], T.Gre[3][d], T.Gim[3][d]};
+    }
+    for (int k = 0; k < kK; ++k) rec->invD[k] = inv_or_zero(1.0, T.D[k]);
     for (int k1 = 0; k1 < 16; ++k1)
         for (int k2 = 0; k2 < 16; ++k2) {
-            T v[4];
+            double v[4];
             for (int a = 0; a < 2; ++a)
                 for (int b = 0; b < 2; ++b) {
                     int k = (k1 + 16 * a) * kW + k2 + 16 * b;
-                    v[2 * a + b] = D[k] > 1e-300 ? (T)(q[k] / D[k]) : (T)0;
+                    v[2 * a + b] = inv_or_zero(q[k], T.D[k]);
                 }
             rec->qD[k1 * 16 + k2] = {v[0], v[1], v[2], v[3]};
         }
     std::memcpy(rec->types, key, 256);
 }
 
+void build_record32(const uint8_t *key, const double *w, const Cd *r32, const std::vector<double> &q,
+                    RecordF32 *rec)
+{
+    static thread_local Tables T;
+    build_tables(key, w, r32, T);
+    for (int d1 = 0; d1 < 16; ++d1)
+        for (int d2 = 0; d2 < 16; ++d2) {
+            int da = d1 * 16 + d2, db = ((d1 + 15) & 15) * 16 + d2;
+            for (int t = 0; t < 4; ++t) {
+                float *g = rec->GP[t][d1][d2];
+                g[0] = (float)T.Gre[t][da];
+                g[1] = (float)T.Gre[t][db];
+                g[2] = (float)T.Gim[t][da];
+                g[3] = (float)T.Gim[t][db];
+            }
+        }
+    for (int k = 0; k < kK; ++k) rec->invD[k] = (float)inv_or_zero(1.0, T.D[k]);
+    for (int j = 0; j < 8; ++j)
+        for (int k2 = 0; k2 < 16; ++k2)
+            for (int a = 0; a < 2; ++a) {
+                float *v = rec->qDP[j][a][k2];
+                for (int b = 0; b < 2; ++b)
+                    for (int e = 0; e < 2; ++e) {
+                        int k = (2 * j + e + 16 * a) * kW + k2 + 16 * b;
+                        v[2 * b + e] = (float)inv_or_zero(q[k], T.D[k]);
+                    }
+            }
+    std::memcpy(rec->types, key, 256);
+}
+
 void release(rljsde_plan *p)
 {
     if (!p) return;
+    if (p->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
     cudaFree(p->d_records);
     cudaFree(p->d_entries);
     cudaFree(p->d_chunk_table);
@@ -307,7 +349,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     }
     if (!st && !p->direct) {
         // FP64 tables per distinct local matrix, stored in the loop's precision.
-        p->record_bytes = prm->precision ? sizeof(Record<double>) : sizeof(Record<float>);
+        p->record_bytes = prm->precision ? sizeof(Record<double>) : sizeof(RecordF32);
         std::vector<unsigned char> host;
         try {
             host.resize(p->record_bytes * (size_t)p->n_tables);
@@ -319,9 +361,9 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             for (int t = 0; t < p->n_tables; ++t) {
                 const uint8_t *key = (const uint8_t *)keys[t].data();
                 if (prm->precision)
-                    build_record<double>(key, w64, r32, p->q, (Record<double> *)(host.data() + p->record_bytes * t));
+                    build_record64(key, w64, r32, p->q, (Record<double> *)(host.data() + p->record_bytes * t));
                 else
-                    build_record<float>(key, w64, r32, p->q, (Record<float> *)(host.data() + p->record_bytes * t));
+                    build_record32(key, w64, r32, p->q, (RecordF32 *)(host.data() + p->record_bytes * t));
             }
             st = upload(&p->d_records, host.data(), host.size());
         }

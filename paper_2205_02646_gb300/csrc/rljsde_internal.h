@@ -62,8 +62,23 @@ struct Record {
     T invD[kK];           // 1 / D_k, k = k1 * 32 + k2
     uint8_t types[256];   // opaque code per window L-pixel (p * 16 + q), 255 = absent
 };
-static_assert(sizeof(Record<float>) % 16 == 0, "record size must allow bulk copies");
 static_assert(sizeof(Record<double>) % 16 == 0, "record size must allow bulk copies");
+
+// FP32 loop tables, the same quantities laid out for packed two-lane (f32x2)
+// arithmetic over frequency pairs (kap1, kap1 + 1), kap1 even:
+//   GP[t][d1][d2]   = (G_t(d1, d2).re, G_t(d1 - 1, d2).re, G_t(d1, d2).im, G_t(d1 - 1, d2).im)
+//                     (d1 - 1 taken mod 16), so that the update of both members
+//                     of a pair reads one 16-byte entry at d1 = (u - kap1) mod 16;
+//   qDP[j][a][kap2] = (qD(2j, b=0), qD(2j+1, b=0), qD(2j, b=1), qD(2j+1, b=1)) at
+//                     k = (kap1 + 16a, kap2 + 16b).
+// Lanes differ in kap2, so consecutive lanes read consecutive 16-byte entries.
+struct RecordF32 {
+    float GP[4][16][16][4];
+    float qDP[8][2][16][4];
+    float invD[kK];
+    uint8_t types[256];
+};
+static_assert(sizeof(RecordF32) % 16 == 0, "record size must allow bulk copies");
 
 }  // namespace rljsde
 
@@ -77,7 +92,7 @@ struct rljsde_plan {
     int n_entries = 0, n_chunks = 0;
     int direct = 0;                   // path == 2
     int device = 0, sm_count = 0;
-    int warps = 8, ctas_per_sm = 0, grid = 0;
+    int warps = 4, ctas_per_sm = 0, grid = 0, variant = 0;
     // device memory, all owned by the plan
     void *d_records = nullptr;        // n_tables records (float or double)
     size_t record_bytes = 0;
@@ -91,6 +106,7 @@ struct rljsde_plan {
     int *d_status = nullptr;
     rljsde::ImageDesc *d_images = nullptr;
     std::vector<int> ord_base;        // first block ordinal of each image
+    void *graph_exec = nullptr;       // cudaGraphExec_t of one batch launch
 };
 
 namespace rljsde {

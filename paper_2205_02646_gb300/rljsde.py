@@ -51,7 +51,8 @@ class Image(ctypes.Structure):
 EXPORTS = ["rljsde_default_params", "rljsde_plan_create", "rljsde_plan_create_batch",
            "rljsde_reconstruct", "rljsde_reconstruct_trace", "rljsde_set_images",
            "rljsde_reconstruct_batch", "rljsde_set_launch", "rljsde_plan_info", "rljsde_check",
-           "rljsde_plan_destroy", "rljsde_status_string"]
+           "rljsde_plan_destroy", "rljsde_status_string", "rljsde_autotune", "rljsde_graph_capture",
+           "rljsde_graph_launch"]
 
 _LIB = None
 
@@ -77,6 +78,10 @@ def _lib():
         lib.rljsde_check.argtypes = [vp, vp]
         lib.rljsde_plan_destroy.argtypes = [vp]
         lib.rljsde_plan_destroy.restype = None
+        lib.rljsde_autotune.argtypes = [vp, vp, sz, vp, sz, i, vp, ctypes.POINTER(i), ctypes.POINTER(i),
+                                        ctypes.POINTER(ctypes.c_float)]
+        lib.rljsde_graph_capture.argtypes = [vp, vp]
+        lib.rljsde_graph_launch.argtypes = [vp, vp]
         lib.rljsde_status_string.argtypes = [i]
         lib.rljsde_status_string.restype = ctypes.c_char_p
         _LIB = lib
@@ -197,6 +202,28 @@ class Plan:
 
     def reconstruct_batch(self, stream=None):
         _ok(_lib().rljsde_reconstruct_batch(self._h, _stream_ptr(stream)), "rljsde_reconstruct_batch")
+
+    def autotune(self, lr=None, hr=None, reps=3, stream=None) -> dict:
+        """Time every launch shape on this plan's work and keep the fastest."""
+        w, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        if lr is None:
+            st = _lib().rljsde_autotune(self._h, None, 0, None, 0, reps, _stream_ptr(stream),
+                                        ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms))
+        else:
+            lr_h, lr_w = self.shapes[0]
+            _check_tensor(lr, (lr_h, lr_w), "lr")
+            _check_tensor(hr, (2 * lr_h, 2 * lr_w), "hr")
+            st = _lib().rljsde_autotune(self._h, lr.data_ptr(), lr.stride(0), hr.data_ptr(), hr.stride(0), reps,
+                                        _stream_ptr(stream), ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms))
+        _ok(st, "rljsde_autotune")
+        return dict(warps_per_cta=w.value, ctas_per_sm=c.value, ms=ms.value)
+
+    def graph_capture(self, stream):
+        """Capture one batch launch on ``stream`` (a non-default torch stream)."""
+        _ok(_lib().rljsde_graph_capture(self._h, _stream_ptr(stream)), "rljsde_graph_capture")
+
+    def graph_launch(self, stream=None):
+        _ok(_lib().rljsde_graph_launch(self._h, _stream_ptr(stream)), "rljsde_graph_launch")
 
     def check(self, stream=None):
         _ok(_lib().rljsde_check(self._h, _stream_ptr(stream)), "rljsde_check")

@@ -193,3 +193,43 @@ def test_plan_info_counts(rl):
     assert info["n_interior_tables"] == 64                 # Table I: 32^2 / 4^2
     assert info["paper_C_bytes"] == info["n_tables"] * 1024 * 1024 * 8
     assert info["n_blocks"] == 64 * 64
+
+
+def test_batch_graph_and_autotune(rl):
+    """One persistent launch over uneven images, replayed from a CUDA graph,
+    equals the plain batch launch; the autotuner keeps results identical."""
+    import torch
+    sizes = synth.batch_sizes(6, 11, lo=(64, 64), hi=(160, 224))
+    masks, ys = [], []
+    for i, (h, w) in enumerate(sizes):
+        f = synth.image(h, w, 16, 2, 8000 + i)
+        m = synth.recurrent_mask(h // 2, w // 2, 4, 78)
+        masks.append(m)
+        ys.append(synth.measure(f, m).astype(np.float32))
+    plan = rl.Plan(masks, rl.default_params(nu_max=20))
+    lrs = [torch.from_numpy(y).cuda() for y in ys]
+    hr_a = [torch.zeros((h, w), device="cuda") for h, w in sizes]
+    hr_b = [torch.zeros((h, w), device="cuda") for h, w in sizes]
+    plan.set_images(lrs, hr_a)
+    plan.reconstruct_batch()
+    plan.check()
+    tuned = plan.autotune(reps=1)
+    assert tuned["warps_per_cta"] in (4, 8) and tuned["ctas_per_sm"] >= 1
+    s = torch.cuda.Stream()
+    plan.set_images(lrs, hr_b)
+    plan.graph_capture(s)
+    plan.graph_launch(s)
+    s.synchronize()
+    plan.check()
+    for a, b in zip(hr_a, hr_b):
+        assert torch.equal(a, b)
+    # the images of the batch against the oracle on a few blocks each
+    for m, y, hr in zip(masks, ys, hr_b):
+        nbw = m.shape[1] // 2
+        blocks = np.array([0, nbw - 1, (m.shape[0] // 2 - 1) * nbw, 5 * nbw + 5])
+        ohr, tr = oracle_run(y, m, blocks=blocks, nu_max=20)
+        g = hr.cpu().numpy()
+        for b in blocks:
+            bi, bj = divmod(int(b), nbw)
+            err = np.abs(g[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4] - ohr[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4])
+            assert err.max() < TOL or tr["gap"].min() < TIE
