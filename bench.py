@@ -268,6 +268,78 @@ def run_batch(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_precision_study(args):
+    """FP32 loop (tables built in FP64, stored FP32) against the all-FP64 GPU
+    loop on the 4096x3072 image with an 8x8-LR mask tile; both compared with
+    the FP64 oracle on a seeded sample of blocks that includes every border
+    table type, and with each other on the full image."""
+    import torch
+    import oracle
+    from paper_2205_02646_gb300 import build, rljsde, synth
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import compare
+    build.build()
+    torch.cuda.set_device(0)
+    f, mask, y = synth.workload("rljsde_4096x3072")
+    lr_h, lr_w = mask.shape
+    nbh, nbw = lr_h // 2, lr_w // 2
+    lr = torch.from_numpy(y).cuda()
+    out, times, traces = {}, {}, {}
+    nu = args.nu_max
+    for name, prec in (("fp32", 0), ("fp64", 1)):
+        plan = rljsde.Plan(mask, rljsde.default_params(nu_max=nu, precision=prec))
+        hr = torch.empty((2 * lr_h, 2 * lr_w), device="cuda")
+        sel = torch.zeros(nbh * nbw * nu, dtype=torch.int16, device="cuda")
+        dc = torch.zeros(nbh * nbw * nu * 2, device="cuda")
+        plan.reconstruct(lr, hr)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.reconstruct(lr, hr)
+        b.record()
+        torch.cuda.synchronize()
+        times[name] = a.elapsed_time(b)
+        plan.reconstruct_trace(lr, hr, sel, dc)
+        plan.check()
+        out[name] = hr.cpu().numpy()
+        traces[name] = sel.cpu().numpy().reshape(nbh * nbw, nu)
+        info = plan.info()
+        plan.close()
+    # sample: every table type (one block per distinct local mask) + random blocks
+    rng = np.random.default_rng(3)
+    first = {}
+    p0 = rljsde.Plan(mask, rljsde.default_params(nu_max=1))
+    n_tables = p0.info()["n_tables"]
+    p0.close()
+    edge_rows = list(range(4)) + list(range(nbh - 4, nbh))
+    edge_cols = list(range(4)) + list(range(nbw - 4, nbw))
+    cand = [bi * nbw + bj for bi in edge_rows for bj in range(8)] + \
+           [bi * nbw + bj for bi in range(8) for bj in edge_cols] + \
+           [bi * nbw + bj for bi in edge_rows for bj in edge_cols] + \
+           [bi * nbw + bj for bi in range(4, 12) for bj in range(4, 12)]
+    blocks = np.unique(np.concatenate([np.array(cand), rng.choice(nbh * nbw, args.sample, replace=False)]))
+    ohr, tr = oracle.reconstruct(y.astype(np.float64), mask, oracle.Params(nu_max=nu), blocks=blocks, trace=True)
+    res = {}
+    for name in ("fp32", "fp64"):
+        r = compare(out[name], traces[name][blocks], ohr, tr["sel"], tr["gap"], blocks, nbw, tol=1e-4, tie=1e-4)
+        errs = []
+        for b in blocks:
+            bi, bj = divmod(int(b), nbw)
+            errs.append(np.abs(out[name][4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4] - ohr[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4]).max())
+        errs = np.array(errs)
+        res[name] = {"mp_per_s": lr_h * lr_w * 4 / 1e6 / (times[name] / 1e3), "ms": times[name],
+                     "sample_blocks": len(blocks), "matched_blocks": r["matched"], "near_tie_blocks": r["near_ties"],
+                     "failed_blocks": len(r["fails"]), "max_abs_err_matched": r["max_err"],
+                     "median_abs_err": float(np.median(errs)), "max_abs_err_all": float(errs.max())}
+    d = np.abs(out["fp32"] - out["fp64"])
+    line = {"study": "precision", "workload": "rljsde_4096x3072", "nu_max": nu, "tables": n_tables,
+            "fp32_loop": res["fp32"], "fp64_loop": res["fp64"],
+            "fp32_vs_fp64_full_image": {"max_abs": float(d.max()), "mean_abs": float(d.mean()),
+                                        "blocks_over_1e-4": int((d.reshape(nbh, 4, nbw, 4).max(axis=(1, 3)) > 1e-4).sum()),
+                                        "blocks": nbh * nbw}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,6 +350,8 @@ def main():
     ap.add_argument("--nu-max", type=int, default=100)
     ap.add_argument("--ref-blocks", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--study", default=None, choices=[None, "precision"])
+    ap.add_argument("--sample", type=int, default=3072)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -286,6 +360,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.study == "precision":
+        run_precision_study(args)
         return
     if args.workload == "rljsde_batch64":
         run_batch(args, rank, world)
