@@ -162,6 +162,65 @@ int rljsde_autotune(rljsde_plan_t *plan, const float *lr, size_t lr_pitch, float
 int rljsde_graph_capture(rljsde_plan_t *plan, void *stream);
 int rljsde_graph_launch(const rljsde_plan_t *plan, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned candidate proposal.  The paper has no counterpart: this library's
+ * extension, which predicts per block the 64 candidates (of Eq. 11's 1024)
+ * the greedy loop is likely to select, so the loop can search those only.
+ * ---------------------------------------------------------------------- */
+typedef struct rljsde_net rljsde_net_t;   /* weights, Adam state, cuBLAS handle */
+
+/* One block's proposal (device layout, 136 bytes): candidate indices
+ * sigma * W + rho, the network's expected number of likely candidates left
+ * out (sum of sigmoid over the rest), and its iteration output. */
+typedef struct {
+    uint16_t idx[64];
+    float missing;
+    float nu_frac;
+} rljsde_shortlist;
+
+/* Create a network on the current device with seeded random weights. */
+int rljsde_net_create(rljsde_net_t **out, uint64_t seed);
+void rljsde_net_destroy(rljsde_net_t *net);
+int rljsde_net_num_params(void);
+/* Copy all parameters (FP32, fixed order: conv1.w, conv1.b, conv2.w,
+ * conv2.b, conv3.w, conv3.b, head.w (1025 x 288), head.b) to / from host. */
+int rljsde_net_get_params(const rljsde_net_t *net, float *host);
+int rljsde_net_set_params(rljsde_net_t *net, const float *host);
+/* Training patches: x (device, n x 5 x 16 x 16) for blocks (device int32
+ * pairs (bi, bj)) of an image lr (device) with mask (device codes). */
+int rljsde_net_patches(const float *lr, size_t lr_pitch, const uint8_t *mask, int lr_h, int lr_w,
+                       const int32_t *blocks, int n, float *x, void *stream);
+/* Loss and gradient of n patches: targets (device, n x 1024 bytes, 1 = in
+ * the block's reference shortlist), nu_t (device, n floats in [0, 1]).
+ * grad_out (device, num_params floats) may be NULL; loss_host receives the
+ * mean loss.  Synchronous. */
+int rljsde_net_gradient(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
+                        const uint8_t *targets, const float *nu_t, float pos_weight, float nu_weight,
+                        float *grad_out, float *loss_host, void *stream);
+/* The same followed by one Adam step with learning rate lr.  Synchronous. */
+int rljsde_net_train_step(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
+                          const uint8_t *targets, const float *nu_t, float pos_weight, float nu_weight, float lr,
+                          float *loss_host, void *stream);
+/* Logits including bias (device, n x 1025) of n patches.  Synchronous. */
+int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
+                      float *z_out, void *stream);
+/* Device workspace bytes rljsde_propose needs for a single-image plan. */
+size_t rljsde_propose_workspace(const rljsde_plan_t *plan);
+/* Run the network over the whole image (convolutions, then the head as one
+ * BF16 GEMM per chunk of blocks) and write one rljsde_shortlist per block
+ * (device, n_blocks entries, block order bi * (2 lr_w / 4) + bj).
+ * Asynchronous; the caller owns shortlists and workspace. */
+int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
+                   void *shortlists, void *workspace, size_t workspace_bytes, void *stream);
+/* Reconstruct using shortlists: a block whose `missing` <= max_missing runs
+ * the greedy loop over its 64 candidates (nu_max iterations, or the
+ * network's iteration output if use_nu_hat), every other block the full
+ * loop.  sel/dc as for rljsde_reconstruct_trace (unused iterations get
+ * 0xFFFF), n_restricted (device int, added to) may be NULL.  FP32 plans. */
+int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_t lr_pitch, float *hr,
+                               size_t hr_pitch, const void *shortlists, float max_missing, int use_nu_hat,
+                               uint16_t *sel, float *dc, int *n_restricted, void *stream);
+
 typedef struct {
     int n_images;
     int n_blocks;           /* target blocks over all images                  */

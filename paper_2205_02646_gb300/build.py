@@ -9,7 +9,8 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRC = [os.path.join(PKG, "csrc", "kernels.cu"), os.path.join(PKG, "csrc", "plan.cpp")]
+SRC = [os.path.join(PKG, "csrc", "kernels.cu"), os.path.join(PKG, "csrc", "proposal.cu"),
+       os.path.join(PKG, "csrc", "plan.cpp")]
 DEPS = SRC + [os.path.join(PKG, "csrc", "rljsde_internal.h"), os.path.join(ROOT, "include", "rljsde.h")]
 LIB = os.path.join(PKG, "librljsde.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -25,9 +26,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in DEPS):
         return LIB
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "2", "-shared",
+    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "3", "-shared",
            "-Xcompiler", "-fPIC,-fopenmp,-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
-           "-o", tmp] + SRC + ["-lgomp"]
+           "-o", tmp] + SRC + ["-lgomp", "-lcublas"]
     if verbose:
         cmd.insert(4, "-Xptxas=-v")
     subprocess.check_call(cmd)

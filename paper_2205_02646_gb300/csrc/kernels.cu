@@ -135,6 +135,11 @@ struct Args {
     uint16_t *trace_sel;       // [ordinal][nu_max], optional
     float *trace_dc;           // [ordinal][nu_max][2], optional
     int *status;
+    // learned proposal (FP32 loop only)
+    const Shortlist *shortlists;   // per block ordinal, or nullptr
+    float max_missing;             // restrict a block iff its left-out mass <= this
+    int use_nu_hat;                // iterations from the network's output
+    int *n_restricted;             // optional count of restricted blocks
     // direct path only
     const uint8_t *masks;
     const long long *mask_offset;
@@ -501,6 +506,99 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
     }
 }
 
+// ------------------------------------------ restricted (shortlist) loop --
+// The greedy loop of Eqs. 11-17 over the 64 shortlisted candidates only, in
+// the projected-residual form: lane l holds R for candidates S[l], S[l + 32],
+// and the column C_{k,uv} of Eq. 14 is rebuilt from the factored tables,
+// C_{k,uv} = sum_t conj(h_t(k)) h_t(uv) G_t((uv - k) mod 16).
+__device__ __forceinline__ C2<float> h_of(const C2<float> *om, int k, int t)
+{
+    const int k1 = k >> 5, k2 = k & 31;
+    const C2<float> ev = om[k2], eu = om[k1], euv = om[(k1 + k2) & 31];
+    const C2<float> P = cadd(cadd(cadd(C2<float>{1, 0}, ev), eu), euv);
+    return csub(P, t == 0 ? C2<float>{1, 0} : t == 1 ? ev : t == 2 ? eu : euv);
+}
+
+__device__ __forceinline__ void restricted_loop(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+                                                const C2<float> *om, const WorkEntry we, const int lane,
+                                                const C2<float> (&Y)[8][4], const Shortlist &sl, const int nu)
+{
+    const int k2l = lane & 15, h = lane >> 4;
+    const int kc[2] = {sl.idx[lane] & (kK - 1), sl.idx[lane + 32] & (kK - 1)};   // stays in range for any input
+    C2<float> hk[2][4];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) hk[c][t] = h_of(om, kc[c], t);
+    // R^0_k = sum_t conj(h_t(k)) Y_t(k mod 16), Y gathered through the scratch
+    C2<float> R[2] = {{0, 0}, {0, 0}};
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) scratch[((8 * h + i) * 16 + k2l) * 2 + u] = Y[i][2 * pass + u];
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int kap = (((kc[c] >> 5) & 15) << 4) | (kc[c] & 15);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) R[c] = cadd(R[c], cmul(cconj(hk[c][2 * pass + u]), scratch[kap * 2 + u]));
+        }
+    }
+    float qd[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int k1 = kc[c] >> 5, k2 = kc[c] & 31;
+        const int kap1 = k1 & 15, A = k1 >> 4, B = k2 >> 4;
+        qd[c] = rec.qDP[kap1 >> 1][A][k2 & 15][2 * B + (kap1 & 1)];
+    }
+    const float gamma = (float)a.gamma;
+    const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
+    float fpix = 0.f;
+    int u = 0, v = 0;
+    C2<float> g[4];
+    const long long trow = (long long)we.ord * a.nu_max;
+    for (int it = 0; it < nu; ++it) {
+        const float s0 = qd[0] * (R[0].re * R[0].re + R[0].im * R[0].im);
+        const float s1 = qd[1] * (R[1].re * R[1].re + R[1].im * R[1].im);
+        const bool second = s1 > s0 || (s1 == s0 && kc[1] < kc[0]);
+        float bs = second ? s1 : s0;
+        int bk = second ? kc[1] : kc[0];
+        warp_argmax(bs, bk);
+        const unsigned owner = __ballot_sync(0xffffffffu, kc[0] == bk || kc[1] == bk);
+        const int wl = __ffs(owner) - 1;
+        const C2<float> send = kc[0] == bk ? R[0] : R[1];
+        const float Rre = __shfl_sync(0xffffffffu, send.re, wl);
+        const float Rim = __shfl_sync(0xffffffffu, send.im, wl);
+        select_step<float>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
+        // Eq. 17 on the shortlist
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int d1 = (u - (kc[c] >> 5)) & 15, d2 = (v - kc[c]) & 15;
+            C2<float> dR = {0, 0};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float4 G = *reinterpret_cast<const float4 *>(rec.GP[t][d1][d2]);
+                dR = cadd(dR, cmul(cconj(hk[c][t]), cmul(g[t], C2<float>{G.x, G.z})));
+            }
+            R[c] = csub(R[c], dR);
+        }
+    }
+    if (a.trace_sel != nullptr && lane == 0)
+        for (int it = nu; it < a.nu_max; ++it) {
+            a.trace_sel[trow + it] = 0xFFFF;
+            a.trace_dc[2 * (trow + it)] = 0.f;
+            a.trace_dc[2 * (trow + it) + 1] = 0.f;
+        }
+    if (lane < 16) {
+        const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
+        const int yy = 4 * we.bi + (lane >> 2), xx = 4 * we.bj + (lane & 3);
+        img.hr[(long long)yy * img.hr_pitch + xx] = fpix;
+    }
+}
+
 template <typename T> struct Loop;
 template <> struct Loop<float> {
     static __device__ __forceinline__ void run(const Args &a, const RecordF32 &rec, C2<float> *scratch,
@@ -509,6 +607,20 @@ template <> struct Loop<float> {
     {
         C2<float> Y[8][4];
         initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
+        if (a.shortlists != nullptr) {
+            const Shortlist &sl = a.shortlists[we.ord];
+            if (sl.missing <= a.max_missing) {
+                int nu = a.nu_max;
+                if (a.use_nu_hat) {
+                    const float f = sl.nu_frac;
+                    nu = f >= 1.f ? a.nu_max : (int)ceilf(fmaxf(f, 0.08f) * a.nu_max);
+                    nu = nu > a.nu_max ? a.nu_max : nu;
+                }
+                if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 1);
+                restricted_loop(a, rec, scratch, om, we, lane, Y, sl, nu);
+                return;
+            }
+        }
         greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
     }
 };
@@ -890,6 +1002,25 @@ int rljsde_reconstruct(const rljsde_plan_t *plan, const float *lr, size_t lr_pit
                        void *stream)
 {
     return rljsde_reconstruct_trace(plan, lr, lr_pitch, hr, hr_pitch, nullptr, nullptr, stream);
+}
+
+int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_t lr_pitch, float *hr,
+                               size_t hr_pitch, const void *shortlists, float max_missing, int use_nu_hat,
+                               uint16_t *sel, float *dc, int *n_restricted, void *stream)
+{
+    if (!plan || !lr || !hr || !shortlists) return RLJSDE_ERR_INVALID_ARG;
+    if (plan->n_images != 1 || plan->direct || plan->params.precision != 0) return RLJSDE_ERR_UNSUPPORTED;
+    if (lr_pitch < (size_t)plan->lr_w[0] || hr_pitch < (size_t)(2 * plan->lr_w[0])) return RLJSDE_ERR_INVALID_ARG;
+    if ((sel == nullptr) != (dc == nullptr)) return RLJSDE_ERR_INVALID_ARG;
+    Args a = make_args(plan);
+    a.single = {lr, hr, plan->lr_h[0], plan->lr_w[0], (long long)lr_pitch, (long long)hr_pitch};
+    a.trace_sel = sel;
+    a.trace_dc = dc;
+    a.shortlists = static_cast<const Shortlist *>(shortlists);
+    a.max_missing = max_missing;
+    a.use_nu_hat = use_nu_hat;
+    a.n_restricted = n_restricted;
+    return launch(plan, a, (cudaStream_t)stream);
 }
 
 int rljsde_reconstruct_batch(const rljsde_plan_t *plan, void *stream)

@@ -369,10 +369,13 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         }
     }
     if (!st && p->direct) {
-        // Direct path: masks and q on the device, no tables.
+        // Direct path: q on the device, no tables.
         std::vector<float> qf(kK);
         for (int k = 0; k < kK; ++k) qf[k] = (float)p->q[k];
         st = upload(&p->d_qD, qf.data(), qf.size() * sizeof(float));
+    }
+    if (!st) {
+        // The masks on the device (direct path, learned proposal).
         long long tot = 0;
         p->mask_offset.resize(n_images);
         for (int i = 0; i < n_images; ++i) { p->mask_offset[i] = tot; tot += (long long)lr_h[i] * lr_w[i]; }

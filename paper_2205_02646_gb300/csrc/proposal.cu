@@ -1,0 +1,752 @@
+// Learned candidate proposal (this library's addition; the paper has no such
+// step): a small fully convolutional network that reads the L-pixel image
+// and its opaque-quadrant codes and scores, per 4x4 target block, every one
+// of the 1024 DFT candidates of the greedy loop (Sec. IV, Eq. 11), plus an
+// iteration count.  The top-64 candidates of a block become its shortlist
+// and the loop searches only those (kernels.cu, restricted loop); blocks the
+// network is unsure of run the full loop.
+//
+// Network (weights stored FP32 for training and used rounded to bfloat16,
+// activations and accumulation in FP32):
+//   input 5 channels on the L-pixel grid: y / 3 and the one-hot code
+//   conv1 5->32 3x3 s1, conv2 32->32 3x3 s2 (target-block grid),
+//   conv3 32->32 3x3 s1, all zero-padded, ReLU; activations outside the
+//   image are zero after every layer;
+//   head: the 3x3 block-grid neighbourhood of conv3 (288 features) times a
+//   1025 x 288 matrix plus bias: 1024 candidate logits and the iteration
+//   output.
+// Training runs on 16x16 L-pixel patches (rows/cols [2bi - 8, 2bi + 8)), whose
+// centre features equal those of the whole-image pass.
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rljsde_internal.h"
+
+namespace rljsde {
+namespace net {
+
+constexpr int kC = 32;
+constexpr int kOut = 1025;
+constexpr int kHeadIn = 9 * kC;
+// flat parameter layout
+constexpr int kW1 = 0, kB1 = kW1 + kC * 5 * 9, kW2 = kB1 + kC, kB2 = kW2 + kC * kC * 9, kW3 = kB2 + kC,
+              kB3 = kW3 + kC * kC * 9, kWh = kB3 + kC, kBh = kWh + kOut * kHeadIn, kParams = kBh + kOut;
+
+// ------------------------------------------------------------- helpers --
+__global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, float *rounded, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(src[i]);
+        dst[i] = b;
+        rounded[i] = __bfloat162float(b);
+    }
+}
+
+// Input planes of one patch per sample: x[n][5][16][16], plus its origin.
+__global__ void patches_kernel(const float *lr, long long lr_pitch, const uint8_t *mask, int lr_h, int lr_w,
+                               const int2 *blocks, int n, float *x)
+{
+    const int s = blockIdx.x;
+    if (s >= n) return;
+    const int2 b = blocks[s];
+    const int y0 = 2 * b.x - 8, x0 = 2 * b.y - 8;
+    float *o = x + (size_t)s * 5 * 256;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const int P = y0 + i / 16, Q = x0 + i % 16;
+        float v = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        if (P >= 0 && P < lr_h && Q >= 0 && Q < lr_w) {
+            const float yv = lr[(long long)P * lr_pitch + Q];
+            v = isfinite(yv) ? yv / 3.0f : 0.f;
+            const int c = mask[(long long)P * lr_w + Q];
+            c0 = c == 0; c1 = c == 1; c2 = c == 2; c3 = c == 3;
+        }
+        o[i] = v; o[256 + i] = c0; o[512 + i] = c1; o[768 + i] = c2; o[1024 + i] = c3;
+    }
+}
+
+// Input planes of a whole image: x[5][lr_h][lr_w].
+__global__ void image_input_kernel(const float *lr, long long lr_pitch, const uint8_t *mask, int lr_h, int lr_w,
+                                   float *x)
+{
+    const long long plane = (long long)lr_h * lr_w;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int P = (int)(i / lr_w), Q = (int)(i % lr_w);
+        const float yv = lr[(long long)P * lr_pitch + Q];
+        const int c = mask[i];
+        x[i] = isfinite(yv) ? yv / 3.0f : 0.f;
+        x[plane + i] = c == 0;
+        x[2 * plane + i] = c == 1;
+        x[3 * plane + i] = c == 2;
+        x[4 * plane + i] = c == 3;
+    }
+}
+
+// Geometry of one conv layer over n samples.  A sample's output position
+// (ho, wo) is inside the image iff (oy + ho, ox + wo) lies in [0, gh) x [0, gw)
+// where (oy, ox) = origin / scale of that sample.
+struct ConvGeom {
+    int n, ci, hi, wi, ho, wo, stride;
+    int scale;           // grid step of the output in L-pixels (1 or 2)
+    const int2 *origin;  // per-sample L-pixel origin, nullptr = (0, 0)
+    int lr_h, lr_w;      // image size in L-pixels
+};
+
+__device__ __forceinline__ bool inside(const ConvGeom &g, int s, int ho, int wo)
+{
+    int oy = 0, ox = 0;
+    if (g.origin) { oy = g.origin[s].x / g.scale; ox = g.origin[s].y / g.scale; }
+    const int gh = g.lr_h / g.scale, gw = g.lr_w / g.scale;
+    const int y = oy + ho, x = ox + wo;
+    return y >= 0 && y < gh && x >= 0 && x < gw;
+}
+
+// out[s][co][ho][wo] = relu(b[co] + sum_ci,dy,dx w[co][ci][dy][dx] in[s][ci][S ho + dy - 1][S wo + dx - 1]),
+// zero outside the image.  One thread per output position, all 32 channels.
+template <int CI>
+__global__ void __launch_bounds__(128) conv_fwd_kernel(const float *in, const float *w, const float *b, float *out,
+                                                       ConvGeom g)
+{
+    __shared__ float ws[kC * CI * 9];
+    __shared__ float bs[kC];
+    for (int i = threadIdx.x; i < kC * CI * 9; i += blockDim.x) ws[i] = w[i];
+    for (int i = threadIdx.x; i < kC; i += blockDim.x) bs[i] = b[i];
+    __syncthreads();
+    const long long per = (long long)g.ho * g.wo;
+    const long long total = per * g.n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / per);
+        const int pos = (int)(idx % per);
+        const int ho = pos / g.wo, wo = pos % g.wo;
+        float *o = out + (size_t)s * kC * per + pos;
+        if (!inside(g, s, ho, wo)) {
+            for (int co = 0; co < kC; ++co) o[co * per] = 0.f;
+            continue;
+        }
+        float acc[kC];
+#pragma unroll
+        for (int co = 0; co < kC; ++co) acc[co] = bs[co];
+        const float *src = in + (size_t)s * CI * g.hi * g.wi;
+        for (int ci = 0; ci < CI; ++ci) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int y = g.stride * ho + t / 3 - 1, x = g.stride * wo + t % 3 - 1;
+                if (y < 0 || y >= g.hi || x < 0 || x >= g.wi) continue;
+                const float v = src[((size_t)ci * g.hi + y) * g.wi + x];
+#pragma unroll
+                for (int co = 0; co < kC; ++co) acc[co] += ws[(co * CI + ci) * 9 + t] * v;
+            }
+        }
+#pragma unroll
+        for (int co = 0; co < kC; ++co) o[co * per] = fmaxf(acc[co], 0.f);
+    }
+}
+
+// gin[s][ci][y][x] = (sum_co,t w[co][ci][t] gout[s][co][ho][wo]) * (a_in > 0),
+// gout already carries the ReLU derivative of its own layer.
+template <int CI>
+__global__ void __launch_bounds__(128) conv_bwd_data_kernel(const float *gout, const float *w, const float *a_in,
+                                                            float *gin, ConvGeom g)
+{
+    __shared__ float ws[kC * CI * 9];
+    for (int i = threadIdx.x; i < kC * CI * 9; i += blockDim.x) ws[i] = w[i];
+    __syncthreads();
+    const long long per_in = (long long)g.hi * g.wi, per_out = (long long)g.ho * g.wo;
+    const long long total = per_in * g.n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / per_in);
+        const int pos = (int)(idx % per_in);
+        const int y = pos / g.wi, x = pos % g.wi;
+        float acc[CI];
+#pragma unroll
+        for (int ci = 0; ci < CI; ++ci) acc[ci] = 0.f;
+        const float *go = gout + (size_t)s * kC * per_out;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int ny = y + 1 - t / 3, nx = x + 1 - t % 3;    // = S ho, S wo
+            if (ny < 0 || nx < 0 || ny % g.stride || nx % g.stride) continue;
+            const int ho = ny / g.stride, wo = nx / g.stride;
+            if (ho >= g.ho || wo >= g.wo) continue;
+            for (int co = 0; co < kC; ++co) {
+                const float gv = go[co * per_out + ho * g.wo + wo];
+#pragma unroll
+                for (int ci = 0; ci < CI; ++ci) acc[ci] += ws[(co * CI + ci) * 9 + t] * gv;
+            }
+        }
+        float *gi = gin + (size_t)s * CI * per_in + pos;
+        const float *ai = a_in + (size_t)s * CI * per_in + pos;
+#pragma unroll
+        for (int ci = 0; ci < CI; ++ci) gi[ci * per_in] = ai[ci * per_in] > 0.f ? acc[ci] : 0.f;
+    }
+}
+
+// gw[co][ci][t] += sum_s,pos gout[s][co][pos] in[s][ci][S ho + dy - 1][S wo + dx - 1],
+// gb[co] += sum gout.  Each thread owns a few weights; samples are split
+// across CTAs and the partial sums added atomically.
+template <int CI>
+__global__ void __launch_bounds__(256) conv_bwd_w_kernel(const float *gout, const float *in, float *gw, float *gb,
+                                                         ConvGeom g)
+{
+    constexpr int NW = kC * CI * 9;
+    constexpr int PER = (NW + 255) / 256;
+    float acc[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) acc[j] = 0.f;
+    float bacc = 0.f;
+    const long long per_in = (long long)g.hi * g.wi, per_out = (long long)g.ho * g.wo;
+    for (int s = blockIdx.x; s < g.n; s += gridDim.x) {
+        const float *go = gout + (size_t)s * kC * per_out;
+        const float *src = in + (size_t)s * CI * per_in;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int wi = threadIdx.x + j * 256;
+            if (wi >= NW) break;
+            const int co = wi / (CI * 9), ci = (wi / 9) % CI, t = wi % 9;
+            const int dy = t / 3 - 1, dx = t % 3 - 1;
+            float a = 0.f;
+            for (int ho = 0; ho < g.ho; ++ho) {
+                const int y = g.stride * ho + dy;
+                if (y < 0 || y >= g.hi) continue;
+                for (int wo = 0; wo < g.wo; ++wo) {
+                    const int x = g.stride * wo + dx;
+                    if (x < 0 || x >= g.wi) continue;
+                    a += go[co * per_out + ho * g.wo + wo] * src[(ci * g.hi + y) * g.wi + x];
+                }
+            }
+            acc[j] += a;
+        }
+        if (threadIdx.x < kC) {
+            float a = 0.f;
+            for (long long p = 0; p < per_out; ++p) a += go[threadIdx.x * per_out + p];
+            bacc += a;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int wi = threadIdx.x + j * 256;
+        if (wi < NW) atomicAdd(&gw[wi], acc[j]);
+    }
+    if (threadIdx.x < kC) atomicAdd(&gb[threadIdx.x], bacc);
+}
+
+__global__ void origins_kernel(const int2 *blocks, int2 *origin, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) origin[i] = make_int2(2 * blocks[i].x - 8, 2 * blocks[i].y - 8);
+}
+
+__global__ void add_bias_kernel(const float *z, const float *b, float *out, int n, int k)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < (long long)n * k) out[i] = z[i] + b[i % k];
+}
+
+// Head features of the patch centre block: f[s][c * 9 + t] = a3[s][c][3 + t/3][3 + t%3].
+__global__ void gather_centre_kernel(const float *a3, float *f, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kHeadIn; i += gridDim.x * blockDim.x) {
+        const int s = i / kHeadIn, j = i % kHeadIn, c = j / 9, t = j % 9;
+        f[i] = a3[((size_t)s * kC + c) * 64 + (3 + t / 3) * 8 + 3 + t % 3];
+    }
+}
+
+// g3 = scatter of the feature gradient back to the centre 3x3, times ReLU'.
+__global__ void scatter_centre_kernel(const float *gf, const float *a3, float *g3, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kC * 64; i += gridDim.x * blockDim.x) {
+        const int s = i / (kC * 64), c = (i / 64) % kC, p = i % 64, y = p / 8, x = p % 8;
+        float v = 0.f;
+        if (y >= 3 && y < 6 && x >= 3 && x < 6 && a3[i] > 0.f) v = gf[(size_t)s * kHeadIn + c * 9 + (y - 3) * 3 + x - 3];
+        g3[i] = v;
+    }
+}
+
+// C[m][n] = beta C[m][n] + sum_k A(m, k) B(k, n) with A(m, k) = A[m sam + k sak],
+// B(k, n) = B[k sbk + n sbn]; 64x64 tiles, 16-deep K steps, 4x4 outputs per thread.
+__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *A, long long sam, long long sak,
+                                                   const float *B, long long sbk, long long sbn, float *C, long long ldc,
+                                                   float beta)
+{
+    __shared__ float As[16][65];
+    __shared__ float Bs[16][65];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+            const int kk = i / 64, mm = i % 64;
+            const int m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < M && k < K) ? A[m * sam + k * sak] : 0.f;
+            const int n = n0 + mm;
+            Bs[kk][mm] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+            if (m < M && n < N) {
+                float *c = &C[(long long)m * ldc + n];
+                *c = (beta == 0.f ? 0.f : beta * *c) + acc[i][j];
+            }
+        }
+}
+
+// Loss (mean over samples) and its gradient w.r.t. z = logits (+bias added here).
+__global__ void loss_kernel(float *z, const float *bias, const uint8_t *t, const float *nu_t, int n, float pos_w,
+                            float nu_w, float *gz, float *loss)
+{
+    const int s = blockIdx.x;
+    if (s >= n) return;
+    __shared__ float red[256];
+    float l = 0.f;
+    for (int k = threadIdx.x; k < kOut; k += blockDim.x) {
+        const float zk = z[(size_t)s * kOut + k] + bias[k];
+        z[(size_t)s * kOut + k] = zk;
+        float g;
+        if (k < 1024) {
+            const float tk = t[(size_t)s * 1024 + k] ? 1.f : 0.f;
+            const float w = tk > 0.5f ? pos_w : 1.f;
+            const float sp = fmaxf(zk, 0.f) + log1pf(expf(-fabsf(zk)));
+            l += w * (sp - tk * zk) / 1024.f;
+            g = w * (1.f / (1.f + expf(-zk)) - tk) / 1024.f;
+        } else {
+            const float d = zk - nu_t[s];
+            l += nu_w * d * d;
+            g = 2.f * nu_w * d;
+        }
+        gz[(size_t)s * kOut + k] = g / n;
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] / n);
+}
+
+__global__ void colsum_kernel(const float *g, int n, int cols, float *out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float a = 0.f;
+    for (int s = 0; s < n; ++s) a += g[(size_t)s * cols + c];
+    out[c] += a;
+}
+
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------- whole-image pass --
+// im2col of the head: f[b][c * 9 + t] (bf16) for block b = by * nbw + bx of a
+// chunk, from a3[c][nbh][nbw] with zero padding.
+__global__ void head_features_kernel(const float *a3, int nbh, int nbw, long long b0, int nb, __nv_bfloat16 *f)
+{
+    const long long total = (long long)nb * kHeadIn;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = b0 + i / kHeadIn;
+        const int j = (int)(i % kHeadIn), c = j / 9, t = j % 9;
+        const int by = (int)(b / nbw) + t / 3 - 1, bx = (int)(b % nbw) + t % 3 - 1;
+        float v = 0.f;
+        if (by >= 0 && by < nbh && bx >= 0 && bx < nbw) v = a3[((long long)c * nbh + by) * nbw + bx];
+        f[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Per block (one warp): logits + bias -> shortlist of the 64 largest (ties to
+// the lower index), the expected number of likely candidates left out
+// (sum of sigmoid over the rest), and the iteration output.
+__global__ void shortlist_kernel(const float *z, const float *bias, long long b0, int nb, Shortlist *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (long long bl = (long long)blockIdx.x * wpb + wib; bl < nb; bl += (long long)gridDim.x * wpb) {
+        // z rows are relative to the chunk, shortlists are indexed by block
+        const float *zb = z + bl * kOut;
+        float v[32];
+        uint32_t key[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            v[j] = zb[j * 32 + lane] + bias[j * 32 + lane];
+            // order-preserving unsigned key of the float
+            const uint32_t u = __float_as_uint(v[j]);
+            key[j] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+        }
+        // the 64th largest key: binary search on the key bits, counting with ballots
+        uint32_t thr = 0;
+        for (int bit = 31; bit >= 0; --bit) {
+            const uint32_t cand = thr | (1u << bit);
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cnt += key[j] >= cand;
+            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (cnt >= kShortlist) thr = cand;
+        }
+        // take keys > thr, then keys == thr by increasing index, up to 64
+        int above = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) above += key[j] > thr;
+        int above_total = above;
+        for (int o = 16; o; o >>= 1) above_total += __shfl_xor_sync(0xffffffffu, above_total, o);
+        int base = above;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, base, o);
+            if (lane >= o) base += y;
+        }
+        base -= above;                           // exclusive prefix
+        Shortlist &sl = out[b0 + bl];
+        int pos = base;
+        float rest = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (key[j] > thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
+        // equal keys, in increasing candidate index k = j * 32 + lane
+        int slot = above_total;
+        for (int j = 0; j < 32 && slot < kShortlist; ++j) {
+            const unsigned eq = __ballot_sync(0xffffffffu, key[j] == thr);
+            const int before = __popc(eq & ((1u << lane) - 1));
+            if (((eq >> lane) & 1u) && slot + before < kShortlist) sl.idx[slot + before] = (uint16_t)(j * 32 + lane);
+            slot += __popc(eq);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (key[j] < thr) rest += 1.f / (1.f + __expf(-v[j]));
+        for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+        if (lane == 0) {
+            sl.missing = rest;
+            sl.nu_frac = zb[1024] + bias[1024];
+        }
+    }
+}
+
+}  // namespace net
+}  // namespace rljsde
+
+using namespace rljsde;
+using namespace rljsde::net;
+
+struct rljsde_net {
+    float *master = nullptr, *rounded = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *w16 = nullptr;
+    int step = 0;
+    cublasHandle_t blas = nullptr;
+    // training buffers, sized for `cap` samples
+    int cap = 0;
+    float *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *g1 = nullptr, *g2 = nullptr, *g3 = nullptr;
+    float *f = nullptr, *gf = nullptr, *z = nullptr, *gz = nullptr, *loss = nullptr;
+    int2 *origin = nullptr;
+};
+
+namespace {
+
+void free_train(rljsde_net *n)
+{
+    cudaFree(n->x); cudaFree(n->a1); cudaFree(n->a2); cudaFree(n->a3); cudaFree(n->g1); cudaFree(n->g2);
+    cudaFree(n->g3); cudaFree(n->f); cudaFree(n->gf); cudaFree(n->z); cudaFree(n->gz); cudaFree(n->loss);
+    cudaFree(n->origin);
+    n->x = n->a1 = n->a2 = n->a3 = n->g1 = n->g2 = n->g3 = n->f = n->gf = n->z = n->gz = n->loss = nullptr;
+    n->origin = nullptr;
+    n->cap = 0;
+}
+
+int ensure_train(rljsde_net *n, int cap)
+{
+    if (cap <= n->cap) return RLJSDE_OK;
+    free_train(n);
+    size_t s = cap;
+    bool ok = cudaMalloc(&n->x, s * 5 * 256 * 4) == cudaSuccess && cudaMalloc(&n->a1, s * kC * 256 * 4) == cudaSuccess &&
+              cudaMalloc(&n->a2, s * kC * 64 * 4) == cudaSuccess && cudaMalloc(&n->a3, s * kC * 64 * 4) == cudaSuccess &&
+              cudaMalloc(&n->g1, s * kC * 256 * 4) == cudaSuccess && cudaMalloc(&n->g2, s * kC * 64 * 4) == cudaSuccess &&
+              cudaMalloc(&n->g3, s * kC * 64 * 4) == cudaSuccess && cudaMalloc(&n->f, s * kHeadIn * 4) == cudaSuccess &&
+              cudaMalloc(&n->gf, s * kHeadIn * 4) == cudaSuccess && cudaMalloc(&n->z, s * kOut * 4) == cudaSuccess &&
+              cudaMalloc(&n->gz, s * kOut * 4) == cudaSuccess && cudaMalloc(&n->loss, 4) == cudaSuccess &&
+              cudaMalloc(&n->origin, s * sizeof(int2)) == cudaSuccess;
+    if (!ok) { free_train(n); return RLJSDE_ERR_OUT_OF_MEMORY; }
+    n->cap = cap;
+    return RLJSDE_OK;
+}
+
+int grid_for(long long work, int threads)
+{
+    long long g = (work + threads - 1) / threads;
+    return (int)(g < 1 ? 1 : (g > 65535 * 16 ? 65535 * 16 : g));
+}
+
+void refresh_bf16(rljsde_net *n, cudaStream_t s)
+{
+    to_bf16_kernel<<<grid_for(kParams, 256), 256, 0, s>>>(n->master, n->w16, n->rounded, kParams);
+}
+
+// Forward over n patches already in n->x with origins in n->origin; the
+// head logits (without bias) land in n->z.
+void forward_patches(rljsde_net *net, int n, int lr_h, int lr_w, cudaStream_t s)
+{
+    const float *r = net->rounded, *b = net->master;     // weights bf16-rounded, biases FP32
+    ConvGeom g1{n, 5, 16, 16, 16, 16, 1, 1, net->origin, lr_h, lr_w};
+    conv_fwd_kernel<5><<<grid_for((long long)n * 256, 128), 128, 0, s>>>(net->x, r + kW1, b + kB1, net->a1, g1);
+    ConvGeom g2{n, kC, 16, 16, 8, 8, 2, 2, net->origin, lr_h, lr_w};
+    conv_fwd_kernel<kC><<<grid_for((long long)n * 64, 128), 128, 0, s>>>(net->a1, r + kW2, b + kB2, net->a2, g2);
+    ConvGeom g3{n, kC, 8, 8, 8, 8, 1, 2, net->origin, lr_h, lr_w};
+    conv_fwd_kernel<kC><<<grid_for((long long)n * 64, 128), 128, 0, s>>>(net->a2, r + kW3, b + kB3, net->a3, g3);
+    gather_centre_kernel<<<grid_for((long long)n * kHeadIn, 256), 256, 0, s>>>(net->a3, net->f, n);
+    // z[s][k] = sum_j f[s][j] Wh[k][j]
+    dim3 gg((kOut + 63) / 64, (n + 63) / 64);
+    gemm_kernel<<<gg, 256, 0, s>>>(n, kOut, kHeadIn, net->f, kHeadIn, 1, r + kWh, 1, kHeadIn, net->z, kOut, 0.f);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rljsde_net_create(rljsde_net_t **out, uint64_t seed)
+{
+    if (!out) return RLJSDE_ERR_INVALID_ARG;
+    *out = nullptr;
+    rljsde_net *n = new (std::nothrow) rljsde_net();
+    if (!n) return RLJSDE_ERR_OUT_OF_MEMORY;
+    size_t b = (size_t)kParams * 4;
+    bool ok = cudaMalloc(&n->master, b) == cudaSuccess && cudaMalloc(&n->rounded, b) == cudaSuccess &&
+              cudaMalloc(&n->grad, b) == cudaSuccess && cudaMalloc(&n->m, b) == cudaSuccess &&
+              cudaMalloc(&n->v, b) == cudaSuccess && cudaMalloc(&n->w16, (size_t)kParams * 2) == cudaSuccess;
+    if (!ok || cublasCreate(&n->blas) != CUBLAS_STATUS_SUCCESS) { rljsde_net_destroy(n); return RLJSDE_ERR_OUT_OF_MEMORY; }
+    // He-style uniform init from a SplitMix64 stream; biases zero
+    std::vector<float> h(kParams, 0.f);
+    uint64_t st = seed;
+    auto next = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    auto fill = [&](int off, int cnt, double fan_in) {
+        const double a = std::sqrt(6.0 / fan_in);
+        for (int i = 0; i < cnt; ++i) h[off + i] = (float)((2.0 * next() - 1.0) * a);
+    };
+    fill(kW1, kB1 - kW1, 45.0);
+    fill(kW2, kB2 - kW2, 288.0);
+    fill(kW3, kB3 - kW3, 288.0);
+    fill(kWh, kBh - kWh, 288.0 * 8.0);
+    for (int k = 0; k < 1024; ++k) h[kBh + k] = -3.0f;     // start near the ~6% positive rate
+    h[kBh + 1024] = 1.0f;
+    if (cudaMemcpy(n->master, h.data(), b, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(n->m, 0, b) != cudaSuccess || cudaMemset(n->v, 0, b) != cudaSuccess) {
+        rljsde_net_destroy(n);
+        return RLJSDE_ERR_CUDA;
+    }
+    refresh_bf16(n, 0);
+    if (cudaDeviceSynchronize() != cudaSuccess) { rljsde_net_destroy(n); return RLJSDE_ERR_CUDA; }
+    *out = n;
+    return RLJSDE_OK;
+}
+
+void rljsde_net_destroy(rljsde_net_t *n)
+{
+    if (!n) return;
+    free_train(n);
+    cudaFree(n->master); cudaFree(n->rounded); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v); cudaFree(n->w16);
+    if (n->blas) cublasDestroy(n->blas);
+    delete n;
+}
+
+int rljsde_net_num_params(void) { return kParams; }
+
+int rljsde_net_get_params(const rljsde_net_t *n, float *host)
+{
+    if (!n || !host) return RLJSDE_ERR_INVALID_ARG;
+    return cudaMemcpy(host, n->master, (size_t)kParams * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? RLJSDE_OK
+                                                                                                  : RLJSDE_ERR_CUDA;
+}
+
+int rljsde_net_set_params(rljsde_net_t *n, const float *host)
+{
+    if (!n || !host) return RLJSDE_ERR_INVALID_ARG;
+    if (cudaMemcpy(n->master, host, (size_t)kParams * 4, cudaMemcpyHostToDevice) != cudaSuccess) return RLJSDE_ERR_CUDA;
+    refresh_bf16(n, 0);
+    return cudaDeviceSynchronize() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
+int rljsde_net_patches(const float *lr, size_t lr_pitch, const uint8_t *mask, int lr_h, int lr_w,
+                       const int32_t *blocks, int n, float *x, void *stream)
+{
+    if (!lr || !mask || !blocks || !x || n < 0 || lr_h < 4 || lr_w < 4 || (lr_h & 1) || (lr_w & 1))
+        return RLJSDE_ERR_INVALID_ARG;
+    if (n == 0) return RLJSDE_OK;
+    patches_kernel<<<n, 256, 0, (cudaStream_t)stream>>>(lr, (long long)lr_pitch, mask, lr_h, lr_w,
+                                                         reinterpret_cast<const int2 *>(blocks), n, x);
+    return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
+// Loss and gradients of n patches (x: device [n][5][16][16], blocks: device
+// [n][2] (bi, bj) of the image lr_h x lr_w they come from).  grad (device,
+// num_params) receives the gradient; *loss_host the mean loss.
+static int loss_grad(rljsde_net *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
+                     const uint8_t *targets, const float *nu_t, float pos_w, float nu_w, float *loss_host,
+                     cudaStream_t s)
+{
+    int st = ensure_train(net, n);
+    if (st) return st;
+    cudaMemcpyAsync(net->x, x, (size_t)n * 5 * 256 * 4, cudaMemcpyDeviceToDevice, s);
+    origins_kernel<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const int2 *>(blocks), net->origin, n);
+    forward_patches(net, n, lr_h, lr_w, s);
+    cudaMemsetAsync(net->loss, 0, 4, s);
+    const float *r = net->rounded;
+    loss_kernel<<<n, 256, 0, s>>>(net->z, net->master + kBh, targets, nu_t, n, pos_w, nu_w, net->gz, net->loss);
+    cudaMemsetAsync(net->grad, 0, (size_t)kParams * 4, s);
+    // head: gWh[k][j] = sum_s gz[s][k] f[s][j]; gbh = sum_s gz; gf[s][j] = sum_k gz[s][k] Wh[k][j]
+    dim3 gw((kHeadIn + 63) / 64, (kOut + 63) / 64);
+    gemm_kernel<<<gw, 256, 0, s>>>(kOut, kHeadIn, n, net->gz, 1, kOut, net->f, kHeadIn, 1, net->grad + kWh, kHeadIn, 0.f);
+    colsum_kernel<<<(kOut + 255) / 256, 256, 0, s>>>(net->gz, n, kOut, net->grad + kBh);
+    dim3 gf((kHeadIn + 63) / 64, (n + 63) / 64);
+    gemm_kernel<<<gf, 256, 0, s>>>(n, kHeadIn, kOut, net->gz, kOut, 1, r + kWh, kHeadIn, 1, net->gf, kHeadIn, 0.f);
+    scatter_centre_kernel<<<grid_for((long long)n * kC * 64, 256), 256, 0, s>>>(net->gf, net->a3, net->g3, n);
+    const int wg = 2 * 152;
+    ConvGeom g3{n, kC, 8, 8, 8, 8, 1, 2, net->origin, lr_h, lr_w};
+    conv_bwd_w_kernel<kC><<<wg, 256, 0, s>>>(net->g3, net->a2, net->grad + kW3, net->grad + kB3, g3);
+    conv_bwd_data_kernel<kC><<<grid_for((long long)n * 64, 128), 128, 0, s>>>(net->g3, r + kW3, net->a2, net->g2, g3);
+    ConvGeom g2{n, kC, 16, 16, 8, 8, 2, 2, net->origin, lr_h, lr_w};
+    conv_bwd_w_kernel<kC><<<wg, 256, 0, s>>>(net->g2, net->a1, net->grad + kW2, net->grad + kB2, g2);
+    conv_bwd_data_kernel<kC><<<grid_for((long long)n * 256, 128), 128, 0, s>>>(net->g2, r + kW2, net->a1, net->g1, g2);
+    ConvGeom g1{n, 5, 16, 16, 16, 16, 1, 1, net->origin, lr_h, lr_w};
+    conv_bwd_w_kernel<5><<<wg, 256, 0, s>>>(net->g1, net->x, net->grad + kW1, net->grad + kB1, g1);
+    if (cudaGetLastError() != cudaSuccess) return RLJSDE_ERR_CUDA;
+    if (loss_host && cudaMemcpyAsync(loss_host, net->loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return RLJSDE_ERR_CUDA;
+    return RLJSDE_OK;
+}
+
+int rljsde_net_gradient(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
+                        const uint8_t *targets, const float *nu_t, float pos_w, float nu_w, float *grad_out,
+                        float *loss_host, void *stream)
+{
+    if (!net || !x || !blocks || !targets || !nu_t || n < 1) return RLJSDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = loss_grad(net, x, blocks, n, lr_h, lr_w, targets, nu_t, pos_w, nu_w, loss_host, s);
+    if (st) return st;
+    if (grad_out && cudaMemcpyAsync(grad_out, net->grad, (size_t)kParams * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return RLJSDE_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
+int rljsde_net_train_step(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
+                          const uint8_t *targets, const float *nu_t, float pos_w, float nu_w, float lr,
+                          float *loss_host, void *stream)
+{
+    if (!net || !x || !blocks || !targets || !nu_t || n < 1 || !(lr > 0.f)) return RLJSDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = loss_grad(net, x, blocks, n, lr_h, lr_w, targets, nu_t, pos_w, nu_w, loss_host, s);
+    if (st) return st;
+    net->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+    adam_kernel<<<grid_for(kParams, 256), 256, 0, s>>>(net->master, net->grad, net->m, net->v, kParams, lr, b1, b2,
+                                                       1e-8f, c1, c2);
+    refresh_bf16(net, s);
+    if (cudaGetLastError() != cudaSuccess) return RLJSDE_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
+// Logits (+bias) of n patches: z_out device [n][1025].
+int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
+                      float *z_out, void *stream)
+{
+    if (!net || !x || !blocks || !z_out || n < 1) return RLJSDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = ensure_train(net, n);
+    if (st) return st;
+    cudaMemcpyAsync(net->x, x, (size_t)n * 5 * 256 * 4, cudaMemcpyDeviceToDevice, s);
+    origins_kernel<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const int2 *>(blocks), net->origin, n);
+    forward_patches(net, n, lr_h, lr_w, s);
+    add_bias_kernel<<<grid_for((long long)n * kOut, 256), 256, 0, s>>>(net->z, net->master + kBh, z_out, n, kOut);
+    if (cudaGetLastError() != cudaSuccess) return RLJSDE_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
+size_t rljsde_propose_workspace(const rljsde_plan_t *plan)
+{
+    if (!plan || plan->n_images != 1) return 0;
+    const size_t P = (size_t)plan->lr_h[0] * plan->lr_w[0], nb = (size_t)plan->n_blocks;
+    const size_t chunk = nb < 65536 ? nb : 65536;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4) + al(chunk * kHeadIn * 2) + al(chunk * kOut * 4);
+}
+
+int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
+                   void *shortlists, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!plan || !net || !lr || !shortlists || !workspace) return RLJSDE_ERR_INVALID_ARG;
+    if (plan->n_images != 1 || lr_pitch < (size_t)plan->lr_w[0]) return RLJSDE_ERR_INVALID_ARG;
+    if (ws_bytes < rljsde_propose_workspace(plan)) return RLJSDE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int lr_h = plan->lr_h[0], lr_w = plan->lr_w[0], nbh = lr_h / 2, nbw = lr_w / 2;
+    const size_t P = (size_t)lr_h * lr_w, nb = (size_t)plan->n_blocks;
+    const size_t chunk = nb < 65536 ? nb : 65536;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    char *w = static_cast<char *>(workspace);
+    float *x = reinterpret_cast<float *>(w);            w += al(5 * P * 4);
+    float *a1 = reinterpret_cast<float *>(w);           w += al(kC * P * 4);
+    float *a2 = reinterpret_cast<float *>(w);           w += al(kC * nb * 4);
+    float *a3 = reinterpret_cast<float *>(w);           w += al(kC * nb * 4);
+    __nv_bfloat16 *f16 = reinterpret_cast<__nv_bfloat16 *>(w); w += al(chunk * kHeadIn * 2);
+    float *z = reinterpret_cast<float *>(w);
+    const float *r = net->rounded, *b = net->master;
+    const int cap = 8 * 152;
+    auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
+    image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
+    ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
+    conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
+    ConvGeom g2{1, kC, lr_h, lr_w, nbh, nbw, 2, 2, nullptr, lr_h, lr_w};
+    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a1, r + kW2, b + kB2, a2, g2);
+    ConvGeom g3{1, kC, nbh, nbw, nbh, nbw, 1, 2, nullptr, lr_h, lr_w};
+    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a2, r + kW3, b + kB3, a3, g3);
+    if (cublasSetStream(net->blas, s) != CUBLAS_STATUS_SUCCESS) return RLJSDE_ERR_CUDA;
+    const float one = 1.f, zero = 0.f;
+    for (size_t b0 = 0; b0 < nb; b0 += chunk) {
+        const int m = (int)(nb - b0 < chunk ? nb - b0 : chunk);
+        head_features_kernel<<<gcap((long long)m * kHeadIn, 256), 256, 0, s>>>(a3, nbh, nbw, (long long)b0, m, f16);
+        // z (row-major m x 1025) = f16 (m x 288) * Wh^T: column-major z^T = Wh * f16^T
+        if (cublasGemmEx(net->blas, CUBLAS_OP_T, CUBLAS_OP_N, kOut, m, kHeadIn, &one, net->w16 + kWh, CUDA_R_16BF,
+                         kHeadIn, f16, CUDA_R_16BF, kHeadIn, &zero, z, CUDA_R_32F, kOut, CUBLAS_COMPUTE_32F,
+                         CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+            return RLJSDE_ERR_CUDA;
+        shortlist_kernel<<<gcap(((long long)m + 7) / 8 * 256, 256), 256, 0, s>>>(
+            z, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
+    }
+    return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
+}  // extern "C"

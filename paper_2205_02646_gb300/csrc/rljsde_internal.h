@@ -80,6 +80,17 @@ struct RecordF32 {
 };
 static_assert(sizeof(RecordF32) % 16 == 0, "record size must allow bulk copies");
 
+// Learned proposal of one block: the candidates the loop may select, the
+// network's expected number of likely candidates left out, and its
+// iteration output (fraction of nu_max).
+constexpr int kShortlist = 64;
+struct Shortlist {
+    uint16_t idx[kShortlist];
+    float missing;
+    float nu_frac;
+};
+static_assert(sizeof(Shortlist) == 136, "shortlist layout");
+
 }  // namespace rljsde
 
 // The opaque plan object of the C ABI.

@@ -52,7 +52,12 @@ EXPORTS = ["rljsde_default_params", "rljsde_plan_create", "rljsde_plan_create_ba
            "rljsde_reconstruct", "rljsde_reconstruct_trace", "rljsde_set_images",
            "rljsde_reconstruct_batch", "rljsde_set_launch", "rljsde_plan_info", "rljsde_check",
            "rljsde_plan_destroy", "rljsde_status_string", "rljsde_autotune", "rljsde_graph_capture",
-           "rljsde_graph_launch"]
+           "rljsde_graph_launch", "rljsde_net_create", "rljsde_net_destroy", "rljsde_net_num_params",
+           "rljsde_net_get_params", "rljsde_net_set_params", "rljsde_net_patches", "rljsde_net_gradient",
+           "rljsde_net_train_step", "rljsde_net_logits", "rljsde_propose_workspace", "rljsde_propose",
+           "rljsde_reconstruct_learned"]
+
+SHORTLIST_BYTES = 136
 
 _LIB = None
 
@@ -82,6 +87,21 @@ def _lib():
                                         ctypes.POINTER(ctypes.c_float)]
         lib.rljsde_graph_capture.argtypes = [vp, vp]
         lib.rljsde_graph_launch.argtypes = [vp, vp]
+        f, u64, i32p = ctypes.c_float, ctypes.c_uint64, ctypes.c_void_p
+        lib.rljsde_net_create.argtypes = [ctypes.POINTER(vp), u64]
+        lib.rljsde_net_destroy.argtypes = [vp]
+        lib.rljsde_net_destroy.restype = None
+        lib.rljsde_net_num_params.argtypes = []
+        lib.rljsde_net_get_params.argtypes = [vp, vp]
+        lib.rljsde_net_set_params.argtypes = [vp, vp]
+        lib.rljsde_net_patches.argtypes = [vp, sz, vp, i, i, i32p, i, vp, vp]
+        lib.rljsde_net_gradient.argtypes = [vp, vp, i32p, i, i, i, vp, vp, f, f, vp, ctypes.POINTER(f), vp]
+        lib.rljsde_net_train_step.argtypes = [vp, vp, i32p, i, i, i, vp, vp, f, f, f, ctypes.POINTER(f), vp]
+        lib.rljsde_net_logits.argtypes = [vp, vp, i32p, i, i, i, vp, vp]
+        lib.rljsde_propose_workspace.argtypes = [vp]
+        lib.rljsde_propose_workspace.restype = ctypes.c_size_t
+        lib.rljsde_propose.argtypes = [vp, vp, vp, sz, vp, vp, sz, vp]
+        lib.rljsde_reconstruct_learned.argtypes = [vp, vp, sz, vp, sz, vp, f, i, vp, vp, vp, vp]
         lib.rljsde_status_string.argtypes = [i]
         lib.rljsde_status_string.restype = ctypes.c_char_p
         _LIB = lib
@@ -225,6 +245,34 @@ class Plan:
     def graph_launch(self, stream=None):
         _ok(_lib().rljsde_graph_launch(self._h, _stream_ptr(stream)), "rljsde_graph_launch")
 
+    def propose(self, net, lr, shortlists=None, workspace=None, stream=None):
+        """Run the proposal network over the image; returns the shortlist
+        buffer (uint8 CUDA tensor, 136 bytes per block)."""
+        import torch
+        lr_h, lr_w = self.shapes[0]
+        _check_tensor(lr, (lr_h, lr_w), "lr")
+        nb = (lr_h // 2) * (lr_w // 2)
+        if shortlists is None:
+            shortlists = torch.empty(nb * SHORTLIST_BYTES, dtype=torch.uint8, device=lr.device)
+        need = _lib().rljsde_propose_workspace(self._h)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=lr.device)
+        _ok(_lib().rljsde_propose(self._h, net.handle, lr.data_ptr(), lr.stride(0), shortlists.data_ptr(),
+                                  workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)), "rljsde_propose")
+        self._ws = workspace
+        return shortlists
+
+    def reconstruct_learned(self, lr, hr, shortlists, max_missing=1.0, use_nu_hat=False, sel=None, dc=None,
+                            counter=None, stream=None):
+        lr_h, lr_w = self.shapes[0]
+        _check_tensor(lr, (lr_h, lr_w), "lr")
+        _check_tensor(hr, (2 * lr_h, 2 * lr_w), "hr")
+        _ok(_lib().rljsde_reconstruct_learned(
+            self._h, lr.data_ptr(), lr.stride(0), hr.data_ptr(), hr.stride(0), shortlists.data_ptr(),
+            float(max_missing), int(bool(use_nu_hat)), None if sel is None else sel.data_ptr(),
+            None if dc is None else dc.data_ptr(), None if counter is None else counter.data_ptr(),
+            _stream_ptr(stream)), "rljsde_reconstruct_learned")
+
     def check(self, stream=None):
         _ok(_lib().rljsde_check(self._h, _stream_ptr(stream)), "rljsde_check")
 
@@ -244,3 +292,96 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def shortlist_view(buf, n_blocks):
+    """Host view of a shortlist buffer: (idx (n, 64) uint16, missing (n,), nu_frac (n,))."""
+    raw = buf.cpu().numpy() if hasattr(buf, "cpu") else np.asarray(buf)
+    rec = np.dtype([("idx", "<u2", (64,)), ("missing", "<f4"), ("nu_frac", "<f4")])
+    arr = raw[: n_blocks * SHORTLIST_BYTES].view(rec)
+    return arr["idx"], arr["missing"], arr["nu_frac"]
+
+
+def shortlist_from_indices(idx, missing=None, nu_frac=None):
+    """Pack (n, 64) candidate indices into a shortlist buffer (uint8 numpy)."""
+    idx = np.asarray(idx, dtype=np.uint16)
+    n = idx.shape[0]
+    rec = np.dtype([("idx", "<u2", (64,)), ("missing", "<f4"), ("nu_frac", "<f4")])
+    arr = np.zeros(n, rec)
+    arr["idx"] = idx
+    arr["missing"] = 0.0 if missing is None else missing
+    arr["nu_frac"] = 1.0 if nu_frac is None else nu_frac
+    return arr.view(np.uint8)
+
+
+class Net:
+    """The proposal network (``rljsde_net_t``): seeded init, training steps
+    and parameter access; all arithmetic in the CUDA library."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        _ok(_lib().rljsde_net_create(ctypes.byref(h), ctypes.c_uint64(seed)), "rljsde_net_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @staticmethod
+    def num_params() -> int:
+        return _lib().rljsde_net_num_params()
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params(), np.float32)
+        _ok(_lib().rljsde_net_get_params(self._h, out.ctypes.data), "rljsde_net_get_params")
+        return out
+
+    def set_params(self, arr):
+        arr = np.ascontiguousarray(arr, dtype=np.float32)
+        assert arr.size == self.num_params()
+        _ok(_lib().rljsde_net_set_params(self._h, arr.ctypes.data), "rljsde_net_set_params")
+
+    @staticmethod
+    def patches(lr, mask_dev, blocks_dev, stream=None):
+        """x (n, 5, 16, 16) for blocks (CUDA int32 (n, 2)) of lr with mask (CUDA uint8)."""
+        import torch
+        n = blocks_dev.shape[0]
+        x = torch.empty((n, 5, 16, 16), dtype=torch.float32, device=lr.device)
+        _ok(_lib().rljsde_net_patches(lr.data_ptr(), lr.stride(0), mask_dev.data_ptr(), lr.shape[0], lr.shape[1],
+                                      blocks_dev.data_ptr(), n, x.data_ptr(), _stream_ptr(stream)),
+            "rljsde_net_patches")
+        return x
+
+    def gradient(self, x, blocks, lr_shape, targets, nu_t, pos_weight=8.0, nu_weight=0.1, stream=None):
+        import torch
+        g = torch.empty(self.num_params(), dtype=torch.float32, device=x.device)
+        loss = ctypes.c_float()
+        _ok(_lib().rljsde_net_gradient(self._h, x.data_ptr(), blocks.data_ptr(), x.shape[0], lr_shape[0],
+                                       lr_shape[1], targets.data_ptr(), nu_t.data_ptr(), pos_weight, nu_weight,
+                                       g.data_ptr(), ctypes.byref(loss), _stream_ptr(stream)), "rljsde_net_gradient")
+        return g, loss.value
+
+    def train_step(self, x, blocks, lr_shape, targets, nu_t, lr=1e-3, pos_weight=8.0, nu_weight=0.1, stream=None):
+        loss = ctypes.c_float()
+        _ok(_lib().rljsde_net_train_step(self._h, x.data_ptr(), blocks.data_ptr(), x.shape[0], lr_shape[0],
+                                         lr_shape[1], targets.data_ptr(), nu_t.data_ptr(), pos_weight, nu_weight,
+                                         lr, ctypes.byref(loss), _stream_ptr(stream)), "rljsde_net_train_step")
+        return loss.value
+
+    def logits(self, x, blocks, lr_shape, stream=None):
+        import torch
+        z = torch.empty((x.shape[0], 1025), dtype=torch.float32, device=x.device)
+        _ok(_lib().rljsde_net_logits(self._h, x.data_ptr(), blocks.data_ptr(), x.shape[0], lr_shape[0],
+                                     lr_shape[1], z.data_ptr(), _stream_ptr(stream)), "rljsde_net_logits")
+        return z
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().rljsde_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

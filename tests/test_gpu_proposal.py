@@ -1,0 +1,176 @@
+"""GPU tests of the learned candidate proposal (this library's extension):
+network gradients against the FP64 reference, the whole-image pass against
+per-patch logits, and the shortlist-restricted greedy loop against the FP64
+oracle (the loop with q = 0 outside the shortlist is the same problem)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn_ref
+from paper_2205_02646_gb300 import synth
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_02646_gb300 import build, rljsde
+    build.build()
+    rljsde.load()
+    return rljsde
+
+
+def _image(h=48, w=64, seed=5):
+    f = synth.image(2 * h, 2 * w, 24, 3, 9100 + seed)
+    mask = synth.recurrent_mask(h, w, 4, 30 + seed)
+    y = synth.measure(f, mask).astype(np.float32)
+    return f, mask, y
+
+
+def test_gradients_match_fp64_reference(rl):
+    import torch
+    f, mask, y = _image(24, 24)
+    net = rl.Net(seed=3)
+    rng = np.random.default_rng(0)
+    params = net.get_params()
+    # larger head weights than the init so every term of the gradient matters
+    params[cnn_ref.N_PARAMS - 1025 - 1025 * 288:cnn_ref.N_PARAMS - 1025] = rng.normal(0, 0.05, 1025 * 288)
+    net.set_params(params)
+    blocks = np.array([[0, 0], [5, 7], [11, 2], [6, 11]], np.int32)
+    lr = torch.from_numpy(y).cuda()
+    md = torch.from_numpy(mask).cuda()
+    bd = torch.from_numpy(blocks).cuda()
+    x = rl.Net.patches(lr, md, bd)
+    targets = (rng.random((4, 1024)) < 0.07).astype(np.uint8)
+    nus = rng.random(4).astype(np.float32)
+    g, loss = net.gradient(x, bd, mask.shape, torch.from_numpy(targets).cuda(), torch.from_numpy(nus).cuda())
+    xs, origins = zip(*[cnn_ref.patch(y, mask, int(bi), int(bj)) for bi, bj in blocks])
+    np.testing.assert_allclose(x.cpu().numpy(), np.array(xs), rtol=0, atol=1e-7)
+    ref_loss, ref_g = cnn_ref.loss_and_grads(cnn_ref.unflatten(params), list(xs), list(origins), mask.shape,
+                                             list(targets.astype(float)), list(nus.astype(float)))
+    assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss)
+    got = cnn_ref.unflatten(g.cpu().numpy())
+    for name, _ in cnn_ref.SHAPES:
+        a, b = got[name], ref_g[name]
+        scale = np.abs(b).max() + 1e-12
+        assert np.abs(a - b).max() <= 2e-3 * scale, (name, np.abs(a - b).max(), scale)
+
+
+def test_whole_image_shortlists_match_patch_logits(rl):
+    import torch
+    f, mask, y = _image()
+    net = rl.Net(seed=7)
+    plan = rl.Plan(mask, rl.default_params(nu_max=10))
+    lr = torch.from_numpy(y).cuda()
+    buf = plan.propose(net, lr)
+    torch.cuda.synchronize()
+    nbh, nbw = mask.shape[0] // 2, mask.shape[1] // 2
+    idx, missing, nu_frac = rl.shortlist_view(buf, nbh * nbw)
+    for row in idx:
+        assert len(set(row.tolist())) == 64 and row.max() < 1024
+    blocks = np.array([[0, 0], [3, 5], [nbh - 1, nbw - 1], [10, 0], [7, 20]], np.int32)
+    z = net.logits(rl.Net.patches(lr, torch.from_numpy(mask).cuda(), torch.from_numpy(blocks).cuda()),
+                   torch.from_numpy(blocks).cuda(), mask.shape).cpu().numpy()
+    for (bi, bj), zb in zip(blocks, z):
+        top = set(np.argsort(-zb[:1024], kind="stable")[:64].tolist())
+        got = set(idx[bi * nbw + bj].tolist())
+        assert len(top & got) >= 56          # head features go through bf16 in the whole-image pass
+        assert abs(nu_frac[bi * nbw + bj] - zb[1024]) < 0.05 * (1 + abs(zb[1024]))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_restricted_loop_matches_oracle_with_q_zero_outside(rl, seed):
+    import torch
+    f, mask, y = _image(24, 24, seed)
+    nbh, nbw = 12, 12
+    nb = nbh * nbw
+    nu = 40
+    rng = np.random.default_rng(seed)
+    idx = np.stack([rng.choice(1024, 64, replace=False) for _ in range(nb)])
+    buf = torch.from_numpy(rl.shortlist_from_indices(idx)).cuda()
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.zeros((48, 48), device="cuda")
+    sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
+    dc = torch.zeros(nb * nu * 2, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    plan.reconstruct_learned(lr, hr, buf, max_missing=1e9, sel=sel, dc=dc, counter=cnt)
+    plan.check()
+    assert int(cnt.item()) == nb
+    g_hr, g_sel = hr.cpu().numpy(), sel.cpu().numpy().reshape(nb, nu)
+    qd = oracle.frequency_weight(oracle.Params()).ravel()
+    blocks = list(range(0, nb, 5))
+    o_hr = np.full((48, 48), np.nan)
+    o_sel, o_gap = [], []
+    for b in blocks:
+        qt = np.zeros(1024)
+        qt[idx[b]] = qd[idx[b]]
+        h_b, tr = oracle.reconstruct(y.astype(np.float64), mask, oracle.Params(nu_max=nu, q_mode=2, q_table=qt),
+                                     blocks=[b], trace=True)
+        bi, bj = divmod(b, nbw)
+        o_hr[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4] = h_b[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4]
+        o_sel.append(tr["sel"][0])
+        o_gap.append(tr["gap"][0])
+    res = compare(g_hr, g_sel[blocks], o_hr, np.array(o_sel), np.array(o_gap), blocks, nbw, tol=1e-4, tie=1e-4)
+    assert not res["fails"], res["fails"][:3]
+
+
+def test_shortlist_of_plain_selections_reproduces_plain_loop(rl):
+    """If the shortlist holds every candidate the full loop selects, the
+    restricted argmax makes the same choices."""
+    import torch
+    f, mask, y = _image(32, 32, 4)
+    nu = 40
+    nb = 16 * 16
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.zeros((64, 64), device="cuda")
+    sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
+    dc = torch.zeros(nb * nu * 2, device="cuda")
+    plan.reconstruct_trace(lr, hr, sel, dc)
+    ps = sel.cpu().numpy().reshape(nb, nu).astype(np.int64) & 0xFFFF
+    idx = np.zeros((nb, 64), np.int64)
+    for b in range(nb):
+        seen = list(dict.fromkeys(ps[b].tolist()))
+        rest = [k for k in range(1024) if k not in seen]
+        idx[b] = (seen + rest)[:64]
+    buf = torch.from_numpy(rl.shortlist_from_indices(idx)).cuda()
+    hr2 = torch.zeros_like(hr)
+    sel2 = torch.zeros_like(sel)
+    dc2 = torch.zeros_like(dc)
+    plan.reconstruct_learned(lr, hr2, buf, max_missing=1e9, sel=sel2, dc=dc2)
+    plan.check()
+    s2 = sel2.cpu().numpy().reshape(nb, nu).astype(np.int64) & 0xFFFF
+    same = (s2 == ps).all(axis=1)
+    assert same.mean() >= 0.97
+    d = np.abs(hr2.cpu().numpy() - hr.cpu().numpy()).reshape(16, 4, 16, 4).max(axis=(1, 3)).ravel()
+    assert d[same].max() <= 1e-4
+
+
+def test_training_lowers_the_loss(rl):
+    import torch
+    f, mask, y = _image(64, 64, 9)
+    nu = 30
+    nb = 32 * 32
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.zeros((128, 128), device="cuda")
+    sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
+    dc = torch.zeros(nb * nu * 2, device="cuda")
+    plan.reconstruct_trace(lr, hr, sel, dc)
+    s = sel.cpu().numpy().reshape(nb, nu).astype(np.int64) & 0xFFFF
+    targets = np.zeros((nb, 1024), np.uint8)
+    for b in range(nb):
+        targets[b, list(dict.fromkeys(s[b].tolist()))[:64]] = 1
+    blocks = np.array([[b // 32, b % 32] for b in range(nb)], np.int32)
+    bd = torch.from_numpy(blocks).cuda()
+    x = rl.Net.patches(lr, torch.from_numpy(mask).cuda(), bd)
+    td = torch.from_numpy(targets).cuda()
+    nud = torch.ones(nb, device="cuda")
+    net = rl.Net(seed=1)
+    losses = [net.train_step(x, bd, mask.shape, td, nud, lr=2e-3) for _ in range(40)]
+    assert losses[-1] < 0.8 * losses[0], losses[::8]
