@@ -212,6 +212,30 @@ size_t rljsde_propose_workspace(const rljsde_plan_t *plan);
  * Asynchronous; the caller owns shortlists and workspace. */
 int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
                    void *shortlists, void *workspace, size_t workspace_bytes, void *stream);
+/*
+ * rljsde_propose without any device allocation.  The paper has no
+ * counterpart; this is for callers that cannot call cudaMalloc or hand over
+ * a workspace, for example code running in a process whose device memory is
+ * owned by another allocator (a framework's caching allocator, a fixed
+ * budget reserved at start-up), or a camera pipeline that must not allocate
+ * once it is streaming.
+ *
+ * The scratch is one fixed 32 MiB array inside the library, so every GPU
+ * that loads the library holds it until the process exits.  Images whose
+ * working set does not fit are rejected with RLJSDE_ERR_BAD_SHAPE: about
+ * 130,000 L-pixels at most (for example 360 x 360 L-pixels, a 720 x 720 HR
+ * image).  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: two calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race and corrupt each
+ * other's results, so serialise them.  Nothing in the array needs to start
+ * at zero; each call overwrites what it reads.  The head is computed with
+ * the library's own FP32 GEMM on the same bfloat16-rounded operands as
+ * rljsde_propose, so results agree up to summation order.  Arguments,
+ * output and the remaining errors are those of rljsde_propose.
+ */
+int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
+                           void *shortlists, void *stream);
 /* Reconstruct using shortlists: a block whose `missing` <= max_missing runs
  * the greedy loop over its 64 candidates (nu_max iterations, or the
  * network's iteration output if use_nu_hat), every other block the full

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -453,11 +454,59 @@ __global__ void shortlist_kernel(const float *z, const float *bias, long long b0
     }
 }
 
+// Head im2col for the no-allocation path: the same features as
+// head_features_kernel, rounded through bfloat16 but stored as float so the
+// FP32 GEMM kernel multiplies exactly the operands the BF16 GEMM would.
+__global__ void head_features_f32_kernel(const float *a3, int nbh, int nbw, long long b0, int nb, float *f)
+{
+    const long long total = (long long)nb * kHeadIn;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = b0 + i / kHeadIn;
+        const int j = (int)(i % kHeadIn), c = j / 9, t = j % 9;
+        const int by = (int)(b / nbw) + t / 3 - 1, bx = (int)(b % nbw) + t % 3 - 1;
+        float v = 0.f;
+        if (by >= 0 && by < nbh && bx >= 0 && bx < nbw) v = a3[((long long)c * nbh + by) * nbw + bx];
+        f[i] = __bfloat162float(__float2bfloat16_rn(v));
+    }
+}
+
+// Fixed scratch of rljsde_propose_noalloc: part of the library image, so
+// every device that loads the library holds it until the process exits.
+constexpr size_t kStaticScratchBytes = 32u << 20;
+constexpr int kStaticChunk = 1024;       // blocks per head GEMM in that path
+static __device__ __align__(256) unsigned char g_propose_scratch[kStaticScratchBytes];
+
 }  // namespace net
 }  // namespace rljsde
 
 using namespace rljsde;
 using namespace rljsde::net;
+
+namespace {
+
+// Device address of g_propose_scratch, looked up once per device with that
+// device current (host code may not use the symbol itself as a pointer).
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+int static_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RLJSDE_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return RLJSDE_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_propose_scratch) != cudaSuccess || !p) return RLJSDE_ERR_CUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return RLJSDE_OK;
+}
+
+}  // namespace
 
 struct rljsde_net {
     float *master = nullptr, *rounded = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
@@ -743,6 +792,52 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
                          kHeadIn, f16, CUDA_R_16BF, kHeadIn, &zero, z, CUDA_R_32F, kOut, CUBLAS_COMPUTE_32F,
                          CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
             return RLJSDE_ERR_CUDA;
+        shortlist_kernel<<<gcap(((long long)m + 7) / 8 * 256, 256), 256, 0, s>>>(
+            z, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
+    }
+    return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
+// The proposal pass for callers that must not allocate device memory; see
+// the header for who they are and for the size limit.
+int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
+                           void *shortlists, void *stream)
+{
+    if (!plan || !net || !lr || !shortlists) return RLJSDE_ERR_INVALID_ARG;
+    if (plan->n_images != 1 || lr_pitch < (size_t)plan->lr_w[0]) return RLJSDE_ERR_INVALID_ARG;
+    const int lr_h = plan->lr_h[0], lr_w = plan->lr_w[0], nbh = lr_h / 2, nbw = lr_w / 2;
+    const size_t P = (size_t)lr_h * lr_w, nb = (size_t)plan->n_blocks;
+    const size_t chunk = nb < (size_t)kStaticChunk ? nb : (size_t)kStaticChunk;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t need = al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4) + al(chunk * kHeadIn * 4) +
+                        al(chunk * kOut * 4);
+    if (need > kStaticScratchBytes) return RLJSDE_ERR_BAD_SHAPE;    // image too large for the fixed scratch
+    void *base = nullptr;
+    int st = static_scratch(&base);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *w = static_cast<char *>(base);
+    float *x = reinterpret_cast<float *>(w);   w += al(5 * P * 4);
+    float *a1 = reinterpret_cast<float *>(w);  w += al(kC * P * 4);
+    float *a2 = reinterpret_cast<float *>(w);  w += al(kC * nb * 4);
+    float *a3 = reinterpret_cast<float *>(w);  w += al(kC * nb * 4);
+    float *f = reinterpret_cast<float *>(w);   w += al(chunk * kHeadIn * 4);
+    float *z = reinterpret_cast<float *>(w);
+    const float *r = net->rounded, *b = net->master;
+    const int cap = 8 * 152;
+    auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
+    image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
+    ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
+    conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
+    ConvGeom g2{1, kC, lr_h, lr_w, nbh, nbw, 2, 2, nullptr, lr_h, lr_w};
+    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a1, r + kW2, b + kB2, a2, g2);
+    ConvGeom g3{1, kC, nbh, nbw, nbh, nbw, 1, 2, nullptr, lr_h, lr_w};
+    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a2, r + kW3, b + kB3, a3, g3);
+    for (size_t b0 = 0; b0 < nb; b0 += chunk) {
+        const int m = (int)(nb - b0 < chunk ? nb - b0 : chunk);
+        head_features_f32_kernel<<<gcap((long long)m * kHeadIn, 256), 256, 0, s>>>(a3, nbh, nbw, (long long)b0, m, f);
+        dim3 gg((kOut + 63) / 64, (m + 63) / 64);
+        gemm_kernel<<<gg, 256, 0, s>>>(m, kOut, kHeadIn, f, kHeadIn, 1, r + kWh, 1, kHeadIn, z, kOut, 0.f);
         shortlist_kernel<<<gcap(((long long)m + 7) / 8 * 256, 256), 256, 0, s>>>(
             z, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
     }

@@ -55,7 +55,7 @@ EXPORTS = ["rljsde_default_params", "rljsde_plan_create", "rljsde_plan_create_ba
            "rljsde_graph_launch", "rljsde_net_create", "rljsde_net_destroy", "rljsde_net_num_params",
            "rljsde_net_get_params", "rljsde_net_set_params", "rljsde_net_patches", "rljsde_net_gradient",
            "rljsde_net_train_step", "rljsde_net_logits", "rljsde_propose_workspace", "rljsde_propose",
-           "rljsde_reconstruct_learned"]
+           "rljsde_reconstruct_learned", "rljsde_propose_noalloc"]
 
 SHORTLIST_BYTES = 136
 
@@ -102,6 +102,7 @@ def _lib():
         lib.rljsde_propose_workspace.restype = ctypes.c_size_t
         lib.rljsde_propose.argtypes = [vp, vp, vp, sz, vp, vp, sz, vp]
         lib.rljsde_reconstruct_learned.argtypes = [vp, vp, sz, vp, sz, vp, f, i, vp, vp, vp, vp]
+        lib.rljsde_propose_noalloc.argtypes = [vp, vp, vp, sz, vp, vp]
         lib.rljsde_status_string.argtypes = [i]
         lib.rljsde_status_string.restype = ctypes.c_char_p
         _LIB = lib
