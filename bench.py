@@ -340,6 +340,89 @@ def run_precision_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Learned candidate proposal on the 4096x3072 image with a recurrent
+    4x4-LR tile: train the network (untimed), then time the plain loop and
+    the proposal + shortlist loop, and compare their PSNR to the ground truth
+    for a sweep of the fallback threshold."""
+    import torch
+    from paper_2205_02646_gb300 import build, proposal, rljsde, synth
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    f, mask, y = synth.workload("rljsde_4096x3072_t4")
+    tiles = [synth.recurrent_mask(256, 256, 4, 1000 + t) for t in range(15)]
+    tiles.append(np.ascontiguousarray(np.tile(mask[:4, :4], (64, 64))))
+    data = proposal.make_dataset(args.train_images, tiles=tiles, nu_max=args.nu_max, seed=1)
+    held = proposal.make_dataset(16, tiles=tiles, nu_max=args.nu_max, seed=2)
+    t_data = time.time() - t0
+    net = rljsde.Net(seed=5)
+    losses = proposal.train(net, data, epochs=args.epochs, lr=args.lr)
+    t_train = time.time() - t0 - t_data
+    rec = proposal.recall(net, held)
+    del data
+    plan = rljsde.Plan(mask, rljsde.default_params(nu_max=args.nu_max))
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.empty((2 * mask.shape[0], 2 * mask.shape[1]), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    nb = plan.info()["n_blocks"]
+    mp = hr.numel() / 1e6
+    truth = torch.from_numpy(f).cuda()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        total = 0.0
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        return total / reps
+
+    ms_plain = timed(lambda: plan.reconstruct(lr, hr), args.steps)
+    plan.check()
+    psnr_plain = proposal.psnr(hr.double(), truth)
+    hr_plain = hr.clone()
+    sl = torch.empty(nb * rljsde.SHORTLIST_BYTES, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(rljsde.load().rljsde_propose_workspace(plan.handle), dtype=torch.uint8, device="cuda")
+    ms_prop = timed(lambda: plan.propose(net, lr, sl, ws), args.steps)
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    points = []
+    for tau in (1.0, 4.0, 16.0, 1e9):
+        for use_nu in (False, True):
+            cnt.zero_()
+            plan.reconstruct_learned(lr, hr, sl, max_missing=tau, use_nu_hat=use_nu, counter=cnt)
+            torch.cuda.synchronize()
+            restricted = int(cnt.item())
+            ms_loop = timed(lambda: plan.reconstruct_learned(lr, hr, sl, max_missing=tau, use_nu_hat=use_nu), args.steps)
+            plan.check()
+            p = proposal.psnr(hr.double(), truth)
+            points.append({"max_missing": tau, "use_nu_hat": use_nu, "mp_per_s": mp / ((ms_prop + ms_loop) / 1e3),
+                           "ms_propose": ms_prop, "ms_loop": ms_loop, "fallback_rate": 1.0 - restricted / nb,
+                           "psnr": p, "psnr_delta_db": psnr_plain - p,
+                           "max_abs_vs_plain": float((hr - hr_plain).abs().max())})
+    # control: the same path with an untrained network (random weights)
+    untrained = rljsde.Net(seed=5)
+    plan.propose(untrained, lr, sl, ws)
+    plan.reconstruct_learned(lr, hr, sl, max_missing=1e9)
+    plan.check()
+    control = {"network": "untrained (random init)", "psnr": proposal.psnr(hr.double(), truth)}
+    control["psnr_delta_db"] = psnr_plain - control["psnr"]
+    ok = [q for q in points if q["psnr_delta_db"] <= 0.05]
+    best = max(ok, key=lambda q: q["mp_per_s"]) if ok else None
+    line = {"study": "learned_proposal", "workload": "rljsde_4096x3072_t4", "nu_max": args.nu_max,
+            "plain_mp_per_s": mp / (ms_plain / 1e3), "plain_psnr": psnr_plain,
+            "train": {"images": args.train_images, "samples": args.train_images * 256, "epochs": args.epochs,
+                      "data_s": t_data, "train_s": t_train, "loss_first": losses[0], "loss_last": losses[-1],
+                      "heldout_recall_at_64": rec},
+            "best_within_0.05dB": best, "untrained_control": control, "points": points}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,6 +435,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", default=None, choices=[None, "precision"])
     ap.add_argument("--sample", type=int, default=3072)
+    ap.add_argument("--train-images", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--lr", type=float, default=2e-3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -363,6 +449,9 @@ def main():
         return
     if args.study == "precision":
         run_precision_study(args)
+        return
+    if args.workload == "rljsde_learned":
+        run_learned(args)
         return
     if args.workload == "rljsde_batch64":
         run_batch(args, rank, world)

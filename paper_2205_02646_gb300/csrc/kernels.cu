@@ -524,7 +524,34 @@ __device__ __forceinline__ void restricted_loop(const Args &a, const RecordF32 &
                                                 const C2<float> (&Y)[8][4], const Shortlist &sl, const int nu)
 {
     const int k2l = lane & 15, h = lane >> 4;
-    const int kc[2] = {sl.idx[lane] & (kK - 1), sl.idx[lane + 32] & (kK - 1)};   // stays in range for any input
+    // Reorder the 64 candidates so that the 8 lanes of a quarter warp hold
+    // candidates with distinct (k2 mod 8) where possible: the per-iteration
+    // table reads at ((u - k1) mod 16, (v - k2) mod 16) then fall in distinct
+    // shared-memory bank groups.  Sorted position i (by k2 mod 8, then by
+    // index) goes to quarter group g = i mod 8, member i / 8; the order does
+    // not change any result (ties are broken on the candidate index).
+    int kc[2];
+    {
+        const int c0 = sl.idx[lane] & (kK - 1), c1 = sl.idx[lane + 32] & (kK - 1);   // in range for any input
+        // rank in (k2 mod 8, k) order over all 64 candidates (distinct keys)
+        const int key0 = ((c0 & 7) << 10) | c0, key1 = ((c1 & 7) << 10) | c1;
+        int r0 = 0, r1 = 0;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const int o0 = __shfl_sync(0xffffffffu, key0, j), o1 = __shfl_sync(0xffffffffu, key1, j);
+            r0 += (o0 < key0) + (o1 < key0);
+            r1 += (o0 < key1) + (o1 < key1);
+        }
+        // scatter through the scratch: position i -> lane (g % 4) * 8 + i / 8, slot g / 4
+        int *pos = reinterpret_cast<int *>(scratch);
+        __syncwarp();
+        const int g0 = r0 & 7, g1 = r1 & 7;
+        pos[(g0 >> 2) * 32 + (g0 & 3) * 8 + (r0 >> 3)] = c0;
+        pos[(g1 >> 2) * 32 + (g1 & 3) * 8 + (r1 >> 3)] = c1;
+        __syncwarp();
+        kc[0] = pos[lane] & (kK - 1);               // duplicates in a caller's list leave slots unset
+        kc[1] = pos[32 + lane] & (kK - 1);
+    }
     C2<float> hk[2][4];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
@@ -599,17 +626,28 @@ __device__ __forceinline__ void restricted_loop(const Args &a, const RecordF32 &
     }
 }
 
-template <typename T> struct Loop;
-template <> struct Loop<float> {
+// Kernel modes: 0 = full loop on every block; 1 = shortlist loop on the
+// blocks whose left-out mass is <= max_missing, other blocks untouched;
+// 2 = full loop on the other blocks only.  Modes 1 and 2 together cover
+// every block once; each is its own instantiation, so the register budget
+// of one does not constrain the other.
+template <typename T, int MODE> struct Loop;
+template <int MODE> struct Loop<float, MODE> {
     static __device__ __forceinline__ void run(const Args &a, const RecordF32 &rec, C2<float> *scratch,
                                                const C2<float> *om, const C2<float> *omc, const PairTables &pt,
                                                const float *wt, const WorkEntry we, const int lane)
     {
-        C2<float> Y[8][4];
-        initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-        if (a.shortlists != nullptr) {
+        if constexpr (MODE == 0) {
+            C2<float> Y[8][4];
+            initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
+            greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
+        } else {
             const Shortlist &sl = a.shortlists[we.ord];
-            if (sl.missing <= a.max_missing) {
+            const bool restricted = sl.missing <= a.max_missing;
+            if (restricted != (MODE == 1)) return;
+            C2<float> Y[8][4];
+            initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
+            if constexpr (MODE == 1) {
                 int nu = a.nu_max;
                 if (a.use_nu_hat) {
                     const float f = sl.nu_frac;
@@ -618,13 +656,13 @@ template <> struct Loop<float> {
                 }
                 if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 1);
                 restricted_loop(a, rec, scratch, om, we, lane, Y, sl, nu);
-                return;
+            } else {
+                greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
             }
         }
-        greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
     }
 };
-template <> struct Loop<double> {
+template <int MODE> struct Loop<double, MODE> {
     static __device__ __forceinline__ void run(const Args &a, const Record<double> &rec, C2<double> *scratch,
                                                const C2<double> *om, const C2<double> *omc, const PairTables &,
                                                const double *wt, const WorkEntry we, const int lane)
@@ -636,7 +674,7 @@ template <> struct Loop<double> {
 };
 
 // --------------------------------------------------- persistent kernel --
-template <typename T, int WARPS, int MINB>
+template <typename T, int WARPS, int MINB, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args a)
 {
     using L = SmemLayout<T, WARPS>;
@@ -707,7 +745,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
         }
         for (int e = warp; e < kChunk; e += WARPS) {
             const WorkEntry we = a.entries[(size_t)c * kChunk + e];
-            if (we.img >= 0) Loop<T>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane);
+            if (we.img >= 0) Loop<T, MODE>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane);
         }
         __syncthreads();                       // every warp is done with slot s
         const int c2 = blockIdx.x + (r + 2) * gridDim.x;
@@ -884,14 +922,16 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
 // Instantiations of the persistent kernel: loop precision, warps per CTA and
 // the minimum resident CTAs per SM the register budget is sized for.
 struct Variant {
-    int fp64, warps, minb;
+    int fp64, warps, minb, mode;
     void (*fn)(Args);
     size_t smem;
 };
-#define RLJSDE_VARIANT(T, W, M) {sizeof(T) == 8, W, M, recurrent_kernel<T, W, M>, SmemLayout<T, W>::bytes}
+#define RLJSDE_VARIANT(T, W, M, MODE) \
+    {sizeof(T) == 8, W, M, MODE, recurrent_kernel<T, W, M, MODE>, SmemLayout<T, W>::bytes}
 const Variant kVariants[] = {
-    RLJSDE_VARIANT(float, 4, 3), RLJSDE_VARIANT(float, 4, 4), RLJSDE_VARIANT(float, 8, 2),
-    RLJSDE_VARIANT(float, 8, 1), RLJSDE_VARIANT(double, 4, 1), RLJSDE_VARIANT(double, 8, 1),
+    RLJSDE_VARIANT(float, 4, 3, 0), RLJSDE_VARIANT(float, 4, 4, 0), RLJSDE_VARIANT(float, 8, 2, 0),
+    RLJSDE_VARIANT(float, 8, 1, 0), RLJSDE_VARIANT(double, 4, 1, 0), RLJSDE_VARIANT(double, 8, 1, 0),
+    RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 3, 2),
 };
 #undef RLJSDE_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -935,6 +975,22 @@ int launch(const rljsde_plan *p, const Args &a, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
 
+// Launch of one learned-mode variant (mode 1 or 2) with its full occupancy.
+int launch_mode(const rljsde_plan *p, const Args &a, int mode, int warps, cudaStream_t s)
+{
+    for (int i = 0; i < kNumVariants; ++i) {
+        const Variant &v = kVariants[i];
+        if (v.mode != mode || v.warps != warps || v.fp64) continue;
+        const int occ = occupancy(v);
+        if (occ <= 0) return RLJSDE_ERR_CUDA;
+        long long g = (long long)p->sm_count * occ;
+        const int grid = (int)(p->n_chunks < g ? (p->n_chunks > 0 ? p->n_chunks : 1) : g);
+        v.fn<<<grid, v.warps * 32, v.smem, s>>>(a);
+        return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+    }
+    return RLJSDE_ERR_UNSUPPORTED;
+}
+
 }  // namespace
 
 int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
@@ -960,7 +1016,7 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
     for (int pass = 0; pass < 2 && best < 0; ++pass)    // second pass: smallest budget above the request
         for (int i = 0; i < kNumVariants; ++i) {
             const Variant &v = kVariants[i];
-            if (v.fp64 != fp64 || v.warps != warps) continue;
+                if (v.fp64 != fp64 || v.warps != warps || v.mode != 0) continue;
             if (pass == 0 && ctas_per_sm > 0 && v.minb > ctas_per_sm) continue;
             const int occ = occupancy(v);
             if (occ < 0) return RLJSDE_ERR_CUDA;
@@ -1020,7 +1076,10 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
     a.max_missing = max_missing;
     a.use_nu_hat = use_nu_hat;
     a.n_restricted = n_restricted;
-    return launch(plan, a, (cudaStream_t)stream);
+    // shortlist blocks first, then the full loop on the rest
+    int st = launch_mode(plan, a, 1, plan->learned_warps, (cudaStream_t)stream);
+    if (st == RLJSDE_OK) st = launch_mode(plan, a, 2, 4, (cudaStream_t)stream);
+    return st;
 }
 
 int rljsde_reconstruct_batch(const rljsde_plan_t *plan, void *stream)

@@ -35,6 +35,7 @@ namespace net {
 
 constexpr int kC = 32;
 constexpr int kOut = 1025;
+constexpr int kOutPad = 1040;    // head rows padded so the BF16 GEMM sees 16-element-aligned strides
 constexpr int kHeadIn = 9 * kC;
 // flat parameter layout
 constexpr int kW1 = 0, kB1 = kW1 + kC * 5 * 9, kW2 = kB1 + kC, kB2 = kW2 + kC * kC * 9, kW3 = kB2 + kC,
@@ -48,6 +49,13 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, float *roun
         dst[i] = b;
         rounded[i] = __bfloat162float(b);
     }
+}
+
+// Head weights in bfloat16, padded with zero rows to kOutPad x 288.
+__global__ void head_pad_kernel(const float *wh, __nv_bfloat16 *out, int rows, int rows_pad, int cols)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows_pad * cols; i += gridDim.x * blockDim.x)
+        out[i] = i < rows * cols ? __float2bfloat16_rn(wh[i]) : __float2bfloat16_rn(0.f);
 }
 
 // Input planes of one patch per sample: x[n][5][16][16], plus its origin.
@@ -391,13 +399,13 @@ __global__ void head_features_kernel(const float *a3, int nbh, int nbw, long lon
 // Per block (one warp): logits + bias -> shortlist of the 64 largest (ties to
 // the lower index), the expected number of likely candidates left out
 // (sum of sigmoid over the rest), and the iteration output.
-__global__ void shortlist_kernel(const float *z, const float *bias, long long b0, int nb, Shortlist *out)
+__global__ void shortlist_kernel(const float *z, int ldz, const float *bias, long long b0, int nb, Shortlist *out)
 {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     for (long long bl = (long long)blockIdx.x * wpb + wib; bl < nb; bl += (long long)gridDim.x * wpb) {
         // z rows are relative to the chunk, shortlists are indexed by block
-        const float *zb = z + bl * kOut;
+        const float *zb = z + bl * ldz;
         float v[32];
         uint32_t key[32];
 #pragma unroll
@@ -511,6 +519,7 @@ int static_scratch(void **out)
 struct rljsde_net {
     float *master = nullptr, *rounded = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *w16 = nullptr;
+    __nv_bfloat16 *head16 = nullptr;     // kOutPad x 288, zero-padded head rows
     int step = 0;
     cublasHandle_t blas = nullptr;
     // training buffers, sized for `cap` samples
@@ -558,6 +567,8 @@ int grid_for(long long work, int threads)
 void refresh_bf16(rljsde_net *n, cudaStream_t s)
 {
     to_bf16_kernel<<<grid_for(kParams, 256), 256, 0, s>>>(n->master, n->w16, n->rounded, kParams);
+    head_pad_kernel<<<grid_for(kOutPad * kHeadIn, 256), 256, 0, s>>>(n->master + kWh, n->head16, kOut, kOutPad,
+                                                                     kHeadIn);
 }
 
 // Forward over n patches already in n->x with origins in n->origin; the
@@ -590,7 +601,8 @@ int rljsde_net_create(rljsde_net_t **out, uint64_t seed)
     size_t b = (size_t)kParams * 4;
     bool ok = cudaMalloc(&n->master, b) == cudaSuccess && cudaMalloc(&n->rounded, b) == cudaSuccess &&
               cudaMalloc(&n->grad, b) == cudaSuccess && cudaMalloc(&n->m, b) == cudaSuccess &&
-              cudaMalloc(&n->v, b) == cudaSuccess && cudaMalloc(&n->w16, (size_t)kParams * 2) == cudaSuccess;
+              cudaMalloc(&n->v, b) == cudaSuccess && cudaMalloc(&n->w16, (size_t)kParams * 2) == cudaSuccess &&
+              cudaMalloc(&n->head16, (size_t)kOutPad * kHeadIn * 2) == cudaSuccess;
     if (!ok || cublasCreate(&n->blas) != CUBLAS_STATUS_SUCCESS) { rljsde_net_destroy(n); return RLJSDE_ERR_OUT_OF_MEMORY; }
     // He-style uniform init from a SplitMix64 stream; biases zero
     std::vector<float> h(kParams, 0.f);
@@ -628,6 +640,7 @@ void rljsde_net_destroy(rljsde_net_t *n)
     if (!n) return;
     free_train(n);
     cudaFree(n->master); cudaFree(n->rounded); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v); cudaFree(n->w16);
+    cudaFree(n->head16);
     if (n->blas) cublasDestroy(n->blas);
     delete n;
 }
@@ -751,7 +764,7 @@ size_t rljsde_propose_workspace(const rljsde_plan_t *plan)
     const size_t P = (size_t)plan->lr_h[0] * plan->lr_w[0], nb = (size_t)plan->n_blocks;
     const size_t chunk = nb < 65536 ? nb : 65536;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    return al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4) + al(chunk * kHeadIn * 2) + al(chunk * kOut * 4);
+    return al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4) + al(chunk * kHeadIn * 2) + al(chunk * kOutPad * 4);
 }
 
 int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
@@ -787,13 +800,13 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
     for (size_t b0 = 0; b0 < nb; b0 += chunk) {
         const int m = (int)(nb - b0 < chunk ? nb - b0 : chunk);
         head_features_kernel<<<gcap((long long)m * kHeadIn, 256), 256, 0, s>>>(a3, nbh, nbw, (long long)b0, m, f16);
-        // z (row-major m x 1025) = f16 (m x 288) * Wh^T: column-major z^T = Wh * f16^T
-        if (cublasGemmEx(net->blas, CUBLAS_OP_T, CUBLAS_OP_N, kOut, m, kHeadIn, &one, net->w16 + kWh, CUDA_R_16BF,
-                         kHeadIn, f16, CUDA_R_16BF, kHeadIn, &zero, z, CUDA_R_32F, kOut, CUBLAS_COMPUTE_32F,
+        // z (row-major m x 1040) = f16 (m x 288) * Wh_pad^T: column-major z^T = Wh_pad * f16^T
+        if (cublasGemmEx(net->blas, CUBLAS_OP_T, CUBLAS_OP_N, kOutPad, m, kHeadIn, &one, net->head16, CUDA_R_16BF,
+                         kHeadIn, f16, CUDA_R_16BF, kHeadIn, &zero, z, CUDA_R_32F, kOutPad, CUBLAS_COMPUTE_32F,
                          CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
             return RLJSDE_ERR_CUDA;
         shortlist_kernel<<<gcap(((long long)m + 7) / 8 * 256, 256), 256, 0, s>>>(
-            z, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
+            z, kOutPad, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
     }
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
@@ -839,7 +852,7 @@ int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, c
         dim3 gg((kOut + 63) / 64, (m + 63) / 64);
         gemm_kernel<<<gg, 256, 0, s>>>(m, kOut, kHeadIn, f, kHeadIn, 1, r + kWh, 1, kHeadIn, z, kOut, 0.f);
         shortlist_kernel<<<gcap(((long long)m + 7) / 8 * 256, 256), 256, 0, s>>>(
-            z, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
+            z, kOut, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
     }
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }

@@ -1,0 +1,115 @@
+"""Training data, training loop and evaluation of the learned candidate
+proposal (the network itself and every step of its arithmetic live in the
+CUDA library; this module only moves tensors between those calls).
+
+Labels come from the plain method: for every block of a training image the
+GPU loop runs with ``nu_max`` iterations and records its selections; the
+block's target set is the first 64 distinct candidates it selected (the
+shortlist that would reproduce most of its model), and its iteration target
+is the number of iterations after which the remaining coefficient changes
+add up to less than ``eps`` (as a fraction of ``nu_max``).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import rljsde, synth
+
+SHORTLIST = 64
+
+
+def labels_from_trace(sel, dc, nu_max: int, k: int = SHORTLIST, eps: float = 2e-3):
+    """Targets (n, 1024) uint8 and iteration fractions (n,) from a trace."""
+    import torch
+    n = sel.shape[0]
+    s = sel.long() & 0xFFFF
+    it = torch.arange(nu_max, device=sel.device).expand(n, nu_max)
+    first = torch.full((n, 1024), nu_max, dtype=torch.long, device=sel.device)
+    first.scatter_reduce_(1, s, it, reduce="amin")
+    order = torch.topk(-first, k, dim=1).indices
+    chosen = torch.gather(first, 1, order) < nu_max
+    targets = torch.zeros((n, 1024), dtype=torch.uint8, device=sel.device)
+    targets.scatter_(1, order, chosen.to(torch.uint8))
+    mag = torch.sqrt(dc[..., 0] ** 2 + dc[..., 1] ** 2)
+    tail = torch.flip(torch.cumsum(torch.flip(mag, [1]), 1), [1])
+    nu_t = (tail >= eps).sum(1).float() / nu_max
+    return targets, nu_t
+
+
+def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu_max: int = 100,
+                 tiles=None, seed: int = 0, n_sin: int = 256, n_edges: int = 32, device: str = "cuda"):
+    """Patches, block coordinates, targets and iteration targets for
+    ``blocks_per_image`` random blocks of each of ``n_images`` synthetic
+    size x size images (mask tiles cycled from ``tiles``)."""
+    import torch
+    lr = size // 2
+    nb_side = lr // 2
+    tiles = tiles if tiles is not None else [synth.recurrent_mask(lr, lr, 4, 1000 + t) for t in range(16)]
+    plans = [rljsde.Plan(m, rljsde.default_params(nu_max=nu_max)) for m in tiles]
+    masks_d = [torch.from_numpy(m).to(device) for m in tiles]
+    nb = nb_side * nb_side
+    sel = torch.empty(nb * nu_max, dtype=torch.int16, device=device)
+    dc = torch.empty(nb * nu_max * 2, dtype=torch.float32, device=device)
+    hr = torch.empty((size, size), device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    xs, bs, ts, ns = [], [], [], []
+    for i in range(n_images):
+        t = i % len(tiles)
+        f = synth.image_torch(size, size, n_sin, n_edges, seed * 100003 + i, 0.005, device)
+        y = synth.measure_torch(f, masks_d[t]).float().contiguous()
+        plans[t].reconstruct_trace(y, hr, sel, dc)
+        tg, nu_t = labels_from_trace(sel.view(nb, nu_max), dc.view(nb, nu_max, 2), nu_max)
+        pick = torch.randperm(nb, generator=g, device=device)[:blocks_per_image]
+        blk = torch.stack([pick // nb_side, pick % nb_side], 1).int().contiguous()
+        xs.append(rljsde.Net.patches(y, masks_d[t], blk))
+        bs.append(blk)
+        ts.append(tg[pick])
+        ns.append(nu_t[pick])
+    for p in plans:
+        p.check()
+    return torch.cat(xs), torch.cat(bs), torch.cat(ts), torch.cat(ns), (lr, lr)
+
+
+def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None):
+    """Adam with cosine decay over ``epochs`` passes of ``data``."""
+    import torch
+    x, blocks, targets, nu_t, shape = data
+    n = x.shape[0]
+    g = torch.Generator(device=x.device)
+    g.manual_seed(seed)
+    steps = epochs * max(1, n // batch)
+    step = 0
+    losses = []
+    for e in range(epochs):
+        perm = torch.randperm(n, generator=g, device=x.device)
+        for i in range(0, n - batch + 1, batch):
+            idx = perm[i:i + batch]
+            rate = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps))
+            losses.append(net.train_step(x[idx].contiguous(), blocks[idx].contiguous(), shape,
+                                         targets[idx].contiguous(), nu_t[idx].contiguous(), lr=rate))
+            step += 1
+        if log:
+            log("epoch %d loss %.4f" % (e, float(np.mean(losses[-max(1, n // batch):]))))
+    return losses
+
+
+def recall(net, data, k: int = SHORTLIST):
+    """Mean fraction of each block's target set found in its top-k logits."""
+    import torch
+    x, blocks, targets, nu_t, shape = data
+    hits, total = 0, 0
+    for i in range(0, x.shape[0], 8192):
+        z = net.logits(x[i:i + 8192].contiguous(), blocks[i:i + 8192].contiguous(), shape)
+        top = torch.topk(z[:, :1024], k, dim=1).indices
+        hits += int(torch.gather(targets[i:i + 8192], 1, top).sum())
+        total += int(targets[i:i + 8192].sum())
+    return hits / max(total, 1)
+
+
+def psnr(a, b):
+    mse = float(((a - b) ** 2).mean())
+    return 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")

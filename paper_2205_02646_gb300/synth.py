@@ -33,7 +33,7 @@ import numpy as np
 
 __all__ = [
     "image", "recurrent_mask", "random_mask", "measure", "workload",
-    "batch_sizes", "OPAQUE_OFFSETS",
+    "batch_sizes", "OPAQUE_OFFSETS", "image_torch", "measure_torch",
 ]
 
 # (row, col) offset of the opaque sub-pixel inside the 2x2 footprint, by code.
@@ -70,6 +70,45 @@ def image(h: int, w: int, n_sin: int, n_edges: int, seed: int,
     if sigma > 0.0:
         img = img + rng.normal(0.0, sigma, img.shape)
     return np.clip(img, 0.0, 1.0)
+
+
+def image_torch(h: int, w: int, n_sin: int, n_edges: int, seed: int, sigma: float = 0.0,
+                device: str = "cuda"):
+    """The recipe of :func:`image` drawn with torch's generator on ``device``
+    (for bulk training data; the values differ from :func:`image`'s)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+
+    def u(n):
+        return torch.rand(n, generator=g, device=device, dtype=torch.float64)
+
+    fy, fx, ph, amp = u(n_sin) - 0.5, u(n_sin) - 0.5, 2.0 * np.pi * u(n_sin), u(n_sin)
+    yy = torch.arange(h, device=device, dtype=torch.float64)
+    xx = torch.arange(w, device=device, dtype=torch.float64)
+    ay = 2.0 * np.pi * torch.outer(yy, fy) + ph[None, :]
+    bx = 2.0 * np.pi * torch.outer(fx, xx)
+    img = torch.cat([torch.sin(ay) * amp, torch.cos(ay) * amp], 1) @ torch.cat([torch.cos(bx), torch.sin(bx)], 0)
+    mean_amp = float(amp.mean()) if n_sin else 1.0
+    py, px, th = h * u(n_edges), w * u(n_edges), np.pi * u(n_edges)
+    hgt = (2.0 * u(n_edges) - 1.0) * mean_amp
+    for e in range(n_edges):
+        side = (yy[:, None] - py[e]) * torch.sin(th[e]) + (xx[None, :] - px[e]) * torch.cos(th[e]) > 0.0
+        img = img + hgt[e] * side
+    lo, hi = img.min(), img.max()
+    img = (img - lo) / (hi - lo) if float(hi) > float(lo) else torch.zeros_like(img)
+    if sigma > 0.0:
+        img = img + sigma * torch.randn(img.shape, generator=g, device=device, dtype=torch.float64)
+    return img.clamp(0.0, 1.0)
+
+
+def measure_torch(f, mask):
+    """:func:`measure` for torch tensors (f: HR image, mask: LR codes)."""
+    import torch
+    lr_h, lr_w = mask.shape
+    q = f[: 2 * lr_h, : 2 * lr_w].reshape(lr_h, 2, lr_w, 2).permute(0, 2, 1, 3).reshape(lr_h, lr_w, 4)
+    opaque = torch.gather(q, 2, mask.long()[..., None])[..., 0]
+    return q.sum(2) - opaque
 
 
 def recurrent_mask(lr_h: int, lr_w: int, tile: int, seed: int) -> np.ndarray:
@@ -115,6 +154,7 @@ _WORKLOADS = {
     "rljsde_64x64":      dict(h=64,   w=64,   n_sin=32,   n_edges=4,   sigma=0.0,   tile=4, seed=1000, mseed=8),
     "rljsde_1024x1024":  dict(h=1024, w=1024, n_sin=256,  n_edges=32,  sigma=0.005, tile=4, seed=2000, mseed=9),
     "rljsde_4096x3072":  dict(h=3072, w=4096, n_sin=2048, n_edges=256, sigma=0.0,   tile=8, seed=3000, mseed=10),
+    "rljsde_4096x3072_t4": dict(h=3072, w=4096, n_sin=2048, n_edges=256, sigma=0.0,  tile=4, seed=5000, mseed=12),
     "rljsde_1200x1200":  dict(h=1200, w=1200, n_sin=256,  n_edges=32,  sigma=0.005, tile=16, seed=6000, mseed=13),
 }
 
