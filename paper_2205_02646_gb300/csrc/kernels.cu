@@ -519,10 +519,23 @@ __device__ __forceinline__ C2<float> h_of(const C2<float> *om, int k, int t)
     return csub(P, t == 0 ? C2<float>{1, 0} : t == 1 ? ev : t == 2 ? eu : euv);
 }
 
-__device__ __forceinline__ void restricted_loop(const Args &a, const RecordF32 &rec, C2<float> *scratch,
-                                                const C2<float> *om, const WorkEntry we, const int lane,
-                                                const C2<float> (&Y)[8][4], const Shortlist &sl, const int nu)
+// Setup of one block for the shortlist loop: its DFT state, the reordered
+// candidates of this lane, h_t(k), R^0_k = sum_t conj(h_t(k)) Y_t(k mod 16)
+// (Y gathered through the scratch) and q_k / D_k.
+struct ShortState {
+    int kc[2];
+    C2<float> hk[2][4];
+    C2<float> R[2];
+    float qd[2];
+};
+
+__device__ __forceinline__ void shortlist_setup(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+                                                const C2<float> *om, const C2<float> *omc, const float *wt,
+                                                const WorkEntry we, const Shortlist &sl, const int lane,
+                                                ShortState &st)
 {
+    C2<float> Y[8][4];
+    initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
     const int k2l = lane & 15, h = lane >> 4;
     // Reorder the 64 candidates so that the 8 lanes of a quarter warp hold
     // candidates with distinct (k2 mod 8) where possible: the per-iteration
@@ -530,7 +543,6 @@ __device__ __forceinline__ void restricted_loop(const Args &a, const RecordF32 &
     // shared-memory bank groups.  Sorted position i (by k2 mod 8, then by
     // index) goes to quarter group g = i mod 8, member i / 8; the order does
     // not change any result (ties are broken on the candidate index).
-    int kc[2];
     {
         const int c0 = sl.idx[lane] & (kK - 1), c1 = sl.idx[lane + 32] & (kK - 1);   // in range for any input
         // rank in (k2 mod 8, k) order over all 64 candidates (distinct keys)
@@ -549,16 +561,14 @@ __device__ __forceinline__ void restricted_loop(const Args &a, const RecordF32 &
         pos[(g0 >> 2) * 32 + (g0 & 3) * 8 + (r0 >> 3)] = c0;
         pos[(g1 >> 2) * 32 + (g1 & 3) * 8 + (r1 >> 3)] = c1;
         __syncwarp();
-        kc[0] = pos[lane] & (kK - 1);               // duplicates in a caller's list leave slots unset
-        kc[1] = pos[32 + lane] & (kK - 1);
+        st.kc[0] = pos[lane] & (kK - 1);               // duplicates in a caller's list leave slots unset
+        st.kc[1] = pos[32 + lane] & (kK - 1);
     }
-    C2<float> hk[2][4];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) hk[c][t] = h_of(om, kc[c], t);
-    // R^0_k = sum_t conj(h_t(k)) Y_t(k mod 16), Y gathered through the scratch
-    C2<float> R[2] = {{0, 0}, {0, 0}};
+        for (int t = 0; t < 4; ++t) st.hk[c][t] = h_of(om, st.kc[c], t);
+    st.R[0] = st.R[1] = C2<float>{0, 0};
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
         __syncwarp();
@@ -569,61 +579,117 @@ __device__ __forceinline__ void restricted_loop(const Args &a, const RecordF32 &
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const int kap = (((kc[c] >> 5) & 15) << 4) | (kc[c] & 15);
+            const int kap = (((st.kc[c] >> 5) & 15) << 4) | (st.kc[c] & 15);
 #pragma unroll
-            for (int u = 0; u < 2; ++u) R[c] = cadd(R[c], cmul(cconj(hk[c][2 * pass + u]), scratch[kap * 2 + u]));
+            for (int u = 0; u < 2; ++u)
+                st.R[c] = cadd(st.R[c], cmul(cconj(st.hk[c][2 * pass + u]), scratch[kap * 2 + u]));
         }
     }
-    float qd[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        const int k1 = kc[c] >> 5, k2 = kc[c] & 31;
+        const int k1 = st.kc[c] >> 5, k2 = st.kc[c] & 31;
         const int kap1 = k1 & 15, A = k1 >> 4, B = k2 >> 4;
-        qd[c] = rec.qDP[kap1 >> 1][A][k2 & 15][2 * B + (kap1 & 1)];
+        st.qd[c] = rec.qDP[kap1 >> 1][A][k2 & 15][2 * B + (kap1 & 1)];
     }
+}
+
+// The greedy loop of Eqs. 11-17 over the 64 shortlisted candidates of NB
+// blocks at once (one warp; NB = 2 interleaves two independent iteration
+// chains, hiding each other's shuffle and shared-memory latency), in the
+// projected-residual form: lane l holds R for two candidates per block, and
+// the column C_{k,uv} of Eq. 14 is rebuilt from the factored tables,
+// C_{k,uv} = sum_t conj(h_t(k)) h_t(uv) G_t((uv - k) mod 16).
+template <int NB>
+__device__ __forceinline__ void shortlist_loop(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+                                               const C2<float> *om, const C2<float> *omc, const float *wt,
+                                               const WorkEntry (&we)[NB], const Shortlist *const (&sl)[NB],
+                                               const int (&nu)[NB], const int lane)
+{
+    ShortState st[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) shortlist_setup(a, rec, scratch, om, omc, wt, we[b], *sl[b], lane, st[b]);
     const float gamma = (float)a.gamma;
     const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
-    float fpix = 0.f;
-    int u = 0, v = 0;
-    C2<float> g[4];
-    const long long trow = (long long)we.ord * a.nu_max;
-    for (int it = 0; it < nu; ++it) {
-        const float s0 = qd[0] * (R[0].re * R[0].re + R[0].im * R[0].im);
-        const float s1 = qd[1] * (R[1].re * R[1].re + R[1].im * R[1].im);
-        const bool second = s1 > s0 || (s1 == s0 && kc[1] < kc[0]);
-        float bs = second ? s1 : s0;
-        int bk = second ? kc[1] : kc[0];
-        warp_argmax(bs, bk);
-        const unsigned owner = __ballot_sync(0xffffffffu, kc[0] == bk || kc[1] == bk);
-        const int wl = __ffs(owner) - 1;
-        const C2<float> send = kc[0] == bk ? R[0] : R[1];
-        const float Rre = __shfl_sync(0xffffffffu, send.re, wl);
-        const float Rim = __shfl_sync(0xffffffffu, send.im, wl);
-        select_step<float>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
-        // Eq. 17 on the shortlist
+    float fpix[NB];
+    int u[NB], v[NB];
+    C2<float> g[NB][4];
+    long long trow[NB];
+    int numax = 0;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int d1 = (u - (kc[c] >> 5)) & 15, d2 = (v - kc[c]) & 15;
-            C2<float> dR = {0, 0};
+    for (int b = 0; b < NB; ++b) {
+        fpix[b] = 0.f;
+        u[b] = v[b] = 0;
+        trow[b] = (long long)we[b].ord * a.nu_max;
+        numax = nu[b] > numax ? nu[b] : numax;
+    }
+    for (int it = 0; it < numax; ++it) {
+        float bs[NB];
+        int bk[NB];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float4 G = *reinterpret_cast<const float4 *>(rec.GP[t][d1][d2]);
-                dR = cadd(dR, cmul(cconj(hk[c][t]), cmul(g[t], C2<float>{G.x, G.z})));
+        for (int b = 0; b < NB; ++b) {
+            const ShortState &s = st[b];
+            const float s0 = s.qd[0] * (s.R[0].re * s.R[0].re + s.R[0].im * s.R[0].im);
+            const float s1 = s.qd[1] * (s.R[1].re * s.R[1].re + s.R[1].im * s.R[1].im);
+            const bool second = s1 > s0 || (s1 == s0 && s.kc[1] < s.kc[0]);
+            bs[b] = second ? s1 : s0;
+            bk[b] = second ? s.kc[1] : s.kc[0];
+        }
+        // warp argmax of every block in the same rounds, ties to the lower index
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const float os = __shfl_xor_sync(0xffffffffu, bs[b], m);
+                const int ok = __shfl_xor_sync(0xffffffffu, bk[b], m);
+                if (os > bs[b] || (os == bs[b] && ok < bk[b])) { bs[b] = os; bk[b] = ok; }
             }
-            R[c] = csub(R[c], dR);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (it >= nu[b]) continue;                 // this block is done (warp-uniform)
+            ShortState &s = st[b];
+            const unsigned owner = __ballot_sync(0xffffffffu, s.kc[0] == bk[b] || s.kc[1] == bk[b]);
+            const int wl = __ffs(owner) - 1;
+            const C2<float> send = s.kc[0] == bk[b] ? s.R[0] : s.R[1];
+            const float Rre = __shfl_sync(0xffffffffu, send.re, wl);
+            const float Rim = __shfl_sync(0xffffffffu, send.im, wl);
+            select_step<float>(a, om, rec.invD[bk[b]], gamma, bk[b], Rre, Rim, eta, gam, lane, trow[b], it, u[b],
+                               v[b], g[b], fpix[b]);
+            // Eq. 17 on the shortlist
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int d1 = (u[b] - (s.kc[c] >> 5)) & 15, d2 = (v[b] - s.kc[c]) & 15;
+                C2<float> dR = {0, 0};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float4 G = *reinterpret_cast<const float4 *>(rec.GP[t][d1][d2]);
+                    dR = cadd(dR, cmul(cconj(s.hk[c][t]), cmul(g[b][t], C2<float>{G.x, G.z})));
+                }
+                s.R[c] = csub(s.R[c], dR);
+            }
         }
     }
-    if (a.trace_sel != nullptr && lane == 0)
-        for (int it = nu; it < a.nu_max; ++it) {
-            a.trace_sel[trow + it] = 0xFFFF;
-            a.trace_dc[2 * (trow + it)] = 0.f;
-            a.trace_dc[2 * (trow + it) + 1] = 0.f;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        if (a.trace_sel != nullptr && lane == 0)
+            for (int it = nu[b]; it < a.nu_max; ++it) {
+                a.trace_sel[trow[b] + it] = 0xFFFF;
+                a.trace_dc[2 * (trow[b] + it)] = 0.f;
+                a.trace_dc[2 * (trow[b] + it) + 1] = 0.f;
+            }
+        if (lane < 16) {
+            const ImageDesc img = a.descs ? a.descs[we[b].img] : a.single;
+            const int yy = 4 * we[b].bi + (lane >> 2), xx = 4 * we[b].bj + (lane & 3);
+            img.hr[(long long)yy * img.hr_pitch + xx] = fpix[b];
         }
-    if (lane < 16) {
-        const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
-        const int yy = 4 * we.bi + (lane >> 2), xx = 4 * we.bj + (lane & 3);
-        img.hr[(long long)yy * img.hr_pitch + xx] = fpix;
     }
+}
+
+__device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortlist &sl)
+{
+    if (!a.use_nu_hat) return a.nu_max;
+    const float f = sl.nu_frac;
+    int nu = f >= 1.f ? a.nu_max : (int)ceilf(fmaxf(f, 0.08f) * a.nu_max);
+    return nu > a.nu_max ? a.nu_max : nu;
 }
 
 // Kernel modes: 0 = full loop on every block; 1 = shortlist loop on the
@@ -641,24 +707,41 @@ template <int MODE> struct Loop<float, MODE> {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
             greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
+        } else if constexpr (MODE == 1) {
+            const Shortlist &sl = a.shortlists[we.ord];
+            if (!(sl.missing <= a.max_missing)) return;
+            const WorkEntry w1[1] = {we};
+            const Shortlist *const s1[1] = {&sl};
+            const int n1[1] = {shortlist_iterations(a, sl)};
+            if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 1);
+            shortlist_loop<1>(a, rec, scratch, om, omc, wt, w1, s1, n1, lane);
         } else {
             const Shortlist &sl = a.shortlists[we.ord];
-            const bool restricted = sl.missing <= a.max_missing;
-            if (restricted != (MODE == 1)) return;
+            if (sl.missing <= a.max_missing) return;
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            if constexpr (MODE == 1) {
-                int nu = a.nu_max;
-                if (a.use_nu_hat) {
-                    const float f = sl.nu_frac;
-                    nu = f >= 1.f ? a.nu_max : (int)ceilf(fmaxf(f, 0.08f) * a.nu_max);
-                    nu = nu > a.nu_max ? a.nu_max : nu;
-                }
-                if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 1);
-                restricted_loop(a, rec, scratch, om, we, lane, Y, sl, nu);
-            } else {
-                greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
-            }
+            greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
+        }
+    }
+
+    // Mode 1 with two entries per warp: blocks that both take the shortlist
+    // loop run it interleaved.
+    static __device__ __forceinline__ void run_pair(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+                                                    const C2<float> *om, const C2<float> *omc,
+                                                    const PairTables &pt, const float *wt, const WorkEntry e0,
+                                                    const WorkEntry e1, const int lane)
+    {
+        const bool r0 = e0.img >= 0 && a.shortlists[e0.ord].missing <= a.max_missing;
+        const bool r1 = e1.img >= 0 && a.shortlists[e1.ord].missing <= a.max_missing;
+        if (r0 && r1) {
+            const WorkEntry w2[2] = {e0, e1};
+            const Shortlist *const s2[2] = {&a.shortlists[e0.ord], &a.shortlists[e1.ord]};
+            const int n2[2] = {shortlist_iterations(a, *s2[0]), shortlist_iterations(a, *s2[1])};
+            if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 2);
+            shortlist_loop<2>(a, rec, scratch, om, omc, wt, w2, s2, n2, lane);
+        } else {
+            if (e0.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e0, lane);
+            if (e1.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e1, lane);
         }
     }
 };
@@ -670,6 +753,14 @@ template <int MODE> struct Loop<double, MODE> {
         C2<double> Y[8][4];
         initial_projection<double>(a, rec, scratch, omc, wt, we, lane, Y);
         greedy_loop<double>(a, rec, om, omc, we, lane, Y);
+    }
+    static __device__ __forceinline__ void run_pair(const Args &a, const Record<double> &rec, C2<double> *scratch,
+                                                    const C2<double> *om, const C2<double> *omc,
+                                                    const PairTables &pt, const double *wt, const WorkEntry e0,
+                                                    const WorkEntry e1, const int lane)
+    {
+        if (e0.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e0, lane);
+        if (e1.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e1, lane);
     }
 };
 
@@ -743,9 +834,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
             parity ^= 1u << s;
             pending &= ~(1u << s);
         }
-        for (int e = warp; e < kChunk; e += WARPS) {
-            const WorkEntry we = a.entries[(size_t)c * kChunk + e];
-            if (we.img >= 0) Loop<T, MODE>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane);
+        if constexpr (MODE == 1 && WARPS * 2 == kChunk) {
+            const WorkEntry e0 = a.entries[(size_t)c * kChunk + warp];
+            const WorkEntry e1 = a.entries[(size_t)c * kChunk + warp + WARPS];
+            Loop<T, MODE>::run_pair(a, *slot(s), scratch, om, omc, *pt, wt, e0, e1, lane);
+        } else {
+            for (int e = warp; e < kChunk; e += WARPS) {
+                const WorkEntry we = a.entries[(size_t)c * kChunk + e];
+                if (we.img >= 0) Loop<T, MODE>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane);
+            }
         }
         __syncthreads();                       // every warp is done with slot s
         const int c2 = blockIdx.x + (r + 2) * gridDim.x;

@@ -445,7 +445,8 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
             if (key[j] > thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
         // equal keys, in increasing candidate index k = j * 32 + lane
         int slot = above_total;
-        for (int j = 0; j < 32 && slot < kShortlist; ++j) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
             const unsigned eq = __ballot_sync(0xffffffffu, key[j] == thr);
             const int before = __popc(eq & ((1u << lane) - 1));
             if (((eq >> lane) & 1u) && slot + before < kShortlist) sl.idx[slot + before] = (uint16_t)(j * 32 + lane);

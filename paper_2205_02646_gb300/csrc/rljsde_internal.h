@@ -104,7 +104,7 @@ struct rljsde_plan {
     int direct = 0;                   // path == 2
     int device = 0, sm_count = 0;
     int warps = 4, ctas_per_sm = 0, grid = 0, variant = 0;
-    int learned_warps = 8;            // warps per CTA of the shortlist-loop kernel
+    int learned_warps = 4;            // warps per CTA of the shortlist-loop kernel (4: two blocks per warp)
     // device memory, all owned by the plan
     void *d_records = nullptr;        // n_tables records (float or double)
     size_t record_bytes = 0;
