@@ -423,6 +423,27 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned_launch(args):
+    """The learned inference path (whole-image proposal, shortlist loop,
+    fallback pass) run twice with a seeded untrained network: the launch
+    sequence the profiles are taken on (the weights do not change it)."""
+    import torch
+    from paper_2205_02646_gb300 import build, rljsde, synth
+    build.build()
+    torch.cuda.set_device(0)
+    f, mask, y = synth.workload(args.workload if args.workload != "rljsde_1024x1024" else "rljsde_4096x3072_t4")
+    plan = rljsde.Plan(mask, rljsde.default_params(nu_max=args.nu_max))
+    net = rljsde.Net(seed=3)
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.empty((2 * mask.shape[0], 2 * mask.shape[1]), device="cuda")
+    for _ in range(2):
+        sl = plan.propose(net, lr)
+        plan.reconstruct_learned(lr, hr, sl, max_missing=1e9)
+    plan.check()
+    torch.cuda.synchronize()
+    print(json.dumps({"study": "learned-launch", "workload": "rljsde_4096x3072_t4", "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,7 +454,7 @@ def main():
     ap.add_argument("--nu-max", type=int, default=100)
     ap.add_argument("--ref-blocks", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "precision"])
+    ap.add_argument("--study", default=None, choices=[None, "precision", "learned-launch"])
     ap.add_argument("--sample", type=int, default=3072)
     ap.add_argument("--train-images", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=6)
@@ -449,6 +470,9 @@ def main():
         return
     if args.study == "precision":
         run_precision_study(args)
+        return
+    if args.study == "learned-launch":
+        run_learned_launch(args)
         return
     if args.workload == "rljsde_learned":
         run_learned(args)

@@ -127,6 +127,7 @@ struct Args {
     int n_chunks;
     const unsigned char *records;
     uint32_t record_bytes;
+    const unsigned char *records_short;    // RecordShortF32 per table (shortlist loop)
     const Consts *consts;
     ImageDesc single;          // used when descs == nullptr
     const ImageDesc *descs;
@@ -146,9 +147,10 @@ struct Args {
     const float *q;
 };
 
-template <typename T> struct RecOf;
-template <> struct RecOf<float> { using type = RecordF32; };
-template <> struct RecOf<double> { using type = Record<double>; };
+template <typename T, int MODE = 0> struct RecOf;
+template <int MODE> struct RecOf<float, MODE> { using type = RecordF32; };
+template <> struct RecOf<float, 1> { using type = RecordShortF32; };
+template <int MODE> struct RecOf<double, MODE> { using type = Record<double>; };
 
 // Pair tables of the FP32 loop: for kap1 pair j, (cos, cos, sin, sin) of
 // 2 pi kap1 / 32 for kap1 = 2j, 2j+1, and (-sin, -sin); the same for the
@@ -161,9 +163,9 @@ struct PairTables {
 };
 
 // Shared memory of the recurrent kernel.
-template <typename T, int WARPS>
+template <typename T, int WARPS, int MODE = 0>
 struct SmemLayout {
-    static constexpr size_t rec = sizeof(typename RecOf<T>::type);
+    static constexpr size_t rec = sizeof(typename RecOf<T, MODE>::type);
     static constexpr size_t scratch = 256 * 2 * sizeof(C2<T>);   // per warp
     static constexpr size_t off_slots = 0;
     static constexpr size_t off_scratch = 2 * rec;
@@ -176,6 +178,7 @@ struct SmemLayout {
 };
 
 __device__ __forceinline__ const uint8_t *rec_types(const RecordF32 &r) { return r.types; }
+__device__ __forceinline__ const uint8_t *rec_types(const RecordShortF32 &r) { return r.types; }
 __device__ __forceinline__ const uint8_t *rec_types(const Record<double> &r) { return r.types; }
 
 // ------------------------------------------- initial projected residual --
@@ -529,7 +532,7 @@ struct ShortState {
     float qd[2];
 };
 
-__device__ __forceinline__ void shortlist_setup(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+__device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShortF32 &rec, C2<float> *scratch,
                                                 const C2<float> *om, const C2<float> *omc, const float *wt,
                                                 const WorkEntry we, const Shortlist &sl, const int lane,
                                                 ShortState &st)
@@ -586,11 +589,7 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordF32 &
         }
     }
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const int k1 = st.kc[c] >> 5, k2 = st.kc[c] & 31;
-        const int kap1 = k1 & 15, A = k1 >> 4, B = k2 >> 4;
-        st.qd[c] = rec.qDP[kap1 >> 1][A][k2 & 15][2 * B + (kap1 & 1)];
-    }
+    for (int c = 0; c < 2; ++c) st.qd[c] = rec.qD[st.kc[c]];
 }
 
 // The greedy loop of Eqs. 11-17 over the 64 shortlisted candidates of NB
@@ -600,7 +599,7 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordF32 &
 // the column C_{k,uv} of Eq. 14 is rebuilt from the factored tables,
 // C_{k,uv} = sum_t conj(h_t(k)) h_t(uv) G_t((uv - k) mod 16).
 template <int NB>
-__device__ __forceinline__ void shortlist_loop(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+__device__ __forceinline__ void shortlist_loop(const Args &a, const RecordShortF32 &rec, C2<float> *scratch,
                                                const C2<float> *om, const C2<float> *omc, const float *wt,
                                                const WorkEntry (&we)[NB], const Shortlist *const (&sl)[NB],
                                                const int (&nu)[NB], const int lane)
@@ -658,12 +657,13 @@ __device__ __forceinline__ void shortlist_loop(const Args &a, const RecordF32 &r
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int d1 = (u[b] - (s.kc[c] >> 5)) & 15, d2 = (v[b] - s.kc[c]) & 15;
+                // two 16-byte loads at (d1, d2): bank group (v - k2) mod 8, which the
+                // candidate order keeps distinct within each quarter warp
+                const float4 G01 = lds4(rec.G01[d1 * 16 + d2]), G23 = lds4(rec.G23[d1 * 16 + d2]);
+                const C2<float> G[4] = {{G01.x, G01.y}, {G01.z, G01.w}, {G23.x, G23.y}, {G23.z, G23.w}};
                 C2<float> dR = {0, 0};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float4 G = *reinterpret_cast<const float4 *>(rec.GP[t][d1][d2]);
-                    dR = cadd(dR, cmul(cconj(s.hk[c][t]), cmul(g[b][t], C2<float>{G.x, G.z})));
-                }
+                for (int t = 0; t < 4; ++t) dR = cadd(dR, cmul(cconj(s.hk[c][t]), cmul(g[b][t], G[t])));
                 s.R[c] = csub(s.R[c], dR);
             }
         }
@@ -699,7 +699,8 @@ __device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortli
 // of one does not constrain the other.
 template <typename T, int MODE> struct Loop;
 template <int MODE> struct Loop<float, MODE> {
-    static __device__ __forceinline__ void run(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+    using Rec = typename RecOf<float, MODE>::type;
+    static __device__ __forceinline__ void run(const Args &a, const Rec &rec, C2<float> *scratch,
                                                const C2<float> *om, const C2<float> *omc, const PairTables &pt,
                                                const float *wt, const WorkEntry we, const int lane)
     {
@@ -726,7 +727,7 @@ template <int MODE> struct Loop<float, MODE> {
 
     // Mode 1 with two entries per warp: blocks that both take the shortlist
     // loop run it interleaved.
-    static __device__ __forceinline__ void run_pair(const Args &a, const RecordF32 &rec, C2<float> *scratch,
+    static __device__ __forceinline__ void run_pair(const Args &a, const Rec &rec, C2<float> *scratch,
                                                     const C2<float> *om, const C2<float> *omc,
                                                     const PairTables &pt, const float *wt, const WorkEntry e0,
                                                     const WorkEntry e1, const int lane)
@@ -768,8 +769,8 @@ template <int MODE> struct Loop<double, MODE> {
 template <typename T, int WARPS, int MINB, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args a)
 {
-    using L = SmemLayout<T, WARPS>;
-    using Rec = typename RecOf<T>::type;
+    using L = SmemLayout<T, WARPS, MODE>;
+    using Rec = typename RecOf<T, MODE>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     auto slot = [&](int s) { return reinterpret_cast<Rec *>(smem + L::off_slots + s * L::rec); };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -809,7 +810,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
     }
     __syncthreads();
 
-    const uint32_t rb = a.record_bytes;
+    const uint32_t rb = (uint32_t)sizeof(Rec);
+    const unsigned char *records = MODE == 1 ? a.records_short : a.records;
     // Per slot s: table held (held0/held1), a load in flight (bit s of
     // pending) and the mbarrier parity to wait for (bit s of parity).
     int held0 = -1, held1 = -1;
@@ -818,7 +820,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
         const int c = blockIdx.x + s * gridDim.x;
         if (c < a.n_chunks) {
             const int t = a.chunk_table[c];
-            if (threadIdx.x == 0) bulk_load(slot(s), a.records + (size_t)t * rb, rb, &bar[s]);
+            if (threadIdx.x == 0) bulk_load(slot(s), records + (size_t)t * rb, rb, &bar[s]);
             if (s == 0) held0 = t; else held1 = t;
             pending |= 1u << s;
         }
@@ -851,7 +853,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
             if (t2 != (s == 0 ? held0 : held1)) {
                 if (threadIdx.x == 0) {
                     fence_proxy_async();
-                    bulk_load(slot(s), a.records + (size_t)t2 * rb, rb, &bar[s]);
+                    bulk_load(slot(s), records + (size_t)t2 * rb, rb, &bar[s]);
                 }
                 if (s == 0) held0 = t2; else held1 = t2;
                 pending |= 1u << s;
@@ -1024,7 +1026,7 @@ struct Variant {
     size_t smem;
 };
 #define RLJSDE_VARIANT(T, W, M, MODE) \
-    {sizeof(T) == 8, W, M, MODE, recurrent_kernel<T, W, M, MODE>, SmemLayout<T, W>::bytes}
+    {sizeof(T) == 8, W, M, MODE, recurrent_kernel<T, W, M, MODE>, SmemLayout<T, W, MODE>::bytes}
 const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 0), RLJSDE_VARIANT(float, 4, 4, 0), RLJSDE_VARIANT(float, 8, 2, 0),
     RLJSDE_VARIANT(float, 8, 1, 0), RLJSDE_VARIANT(double, 4, 1, 0), RLJSDE_VARIANT(double, 8, 1, 0),
@@ -1049,6 +1051,7 @@ Args make_args(const rljsde_plan *p)
     a.chunk_table = p->d_chunk_table;
     a.n_chunks = p->n_chunks;
     a.records = static_cast<const unsigned char *>(p->d_records);
+    a.records_short = static_cast<const unsigned char *>(p->d_records_short);
     a.record_bytes = (uint32_t)p->record_bytes;
     a.consts = p->d_consts;
     a.descs = nullptr;
@@ -1073,11 +1076,11 @@ int launch(const rljsde_plan *p, const Args &a, cudaStream_t s)
 }
 
 // Launch of one learned-mode variant (mode 1 or 2) with its full occupancy.
-int launch_mode(const rljsde_plan *p, const Args &a, int mode, int warps, cudaStream_t s)
+int launch_mode(const rljsde_plan *p, const Args &a, int mode, int warps, int minb, cudaStream_t s)
 {
     for (int i = 0; i < kNumVariants; ++i) {
         const Variant &v = kVariants[i];
-        if (v.mode != mode || v.warps != warps || v.fp64) continue;
+        if (v.mode != mode || v.warps != warps || v.fp64 || (minb && v.minb != minb)) continue;
         const int occ = occupancy(v);
         if (occ <= 0) return RLJSDE_ERR_CUDA;
         long long g = (long long)p->sm_count * occ;
@@ -1174,8 +1177,8 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
     a.use_nu_hat = use_nu_hat;
     a.n_restricted = n_restricted;
     // shortlist blocks first, then the full loop on the rest
-    int st = launch_mode(plan, a, 1, plan->learned_warps, (cudaStream_t)stream);
-    if (st == RLJSDE_OK) st = launch_mode(plan, a, 2, 4, (cudaStream_t)stream);
+    int st = launch_mode(plan, a, 1, plan->learned_warps, plan->learned_minb, (cudaStream_t)stream);
+    if (st == RLJSDE_OK) st = launch_mode(plan, a, 2, 4, 0, (cudaStream_t)stream);
     return st;
 }
 

@@ -140,10 +140,20 @@ void build_record64(const uint8_t *key, const double *w, const Cd *r32, const st
 }
 
 void build_record32(const uint8_t *key, const double *w, const Cd *r32, const std::vector<double> &q,
-                    RecordF32 *rec)
+                    RecordF32 *rec, RecordShortF32 *sh)
 {
     static thread_local Tables T;
     build_tables(key, w, r32, T);
+    for (int d = 0; d < 256; ++d) {
+        float *a = sh->G01[d], *b = sh->G23[d];
+        a[0] = (float)T.Gre[0][d]; a[1] = (float)T.Gim[0][d]; a[2] = (float)T.Gre[1][d]; a[3] = (float)T.Gim[1][d];
+        b[0] = (float)T.Gre[2][d]; b[1] = (float)T.Gim[2][d]; b[2] = (float)T.Gre[3][d]; b[3] = (float)T.Gim[3][d];
+    }
+    for (int k = 0; k < kK; ++k) {
+        sh->qD[k] = (float)inv_or_zero(q[k], T.D[k]);
+        sh->invD[k] = (float)inv_or_zero(1.0, T.D[k]);
+    }
+    std::memcpy(sh->types, key, 256);
     for (int d1 = 0; d1 < 16; ++d1)
         for (int d2 = 0; d2 < 16; ++d2) {
             int da = d1 * 16 + d2, db = ((d1 + 15) & 15) * 16 + d2;
@@ -174,6 +184,7 @@ void release(rljsde_plan *p)
     if (!p) return;
     if (p->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
     cudaFree(p->d_records);
+    cudaFree(p->d_records_short);
     cudaFree(p->d_entries);
     cudaFree(p->d_chunk_table);
     cudaFree(p->d_consts);
@@ -350,9 +361,10 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     if (!st && !p->direct) {
         // FP64 tables per distinct local matrix, stored in the loop's precision.
         p->record_bytes = prm->precision ? sizeof(Record<double>) : sizeof(RecordF32);
-        std::vector<unsigned char> host;
+        std::vector<unsigned char> host, host_short;
         try {
             host.resize(p->record_bytes * (size_t)p->n_tables);
+            if (!prm->precision) host_short.resize(sizeof(RecordShortF32) * (size_t)p->n_tables);
         } catch (...) {
             st = RLJSDE_ERR_OUT_OF_MEMORY;
         }
@@ -363,9 +375,11 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
                 if (prm->precision)
                     build_record64(key, w64, r32, p->q, (Record<double> *)(host.data() + p->record_bytes * t));
                 else
-                    build_record32(key, w64, r32, p->q, (RecordF32 *)(host.data() + p->record_bytes * t));
+                    build_record32(key, w64, r32, p->q, (RecordF32 *)(host.data() + p->record_bytes * t),
+                                   (RecordShortF32 *)(host_short.data() + sizeof(RecordShortF32) * t));
             }
             st = upload(&p->d_records, host.data(), host.size());
+            if (!st && !prm->precision) st = upload(&p->d_records_short, host_short.data(), host_short.size());
         }
     }
     if (!st && p->direct) {
