@@ -392,7 +392,9 @@ def run_learned(args):
     ms_prop = timed(lambda: plan.propose(net, lr, sl, ws), args.steps)
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
     points = []
-    for tau in (1.0, 4.0, 16.0, 1e9):
+    _, missing, _ = rljsde.shortlist_view(sl, nb)
+    taus = [float(np.quantile(missing, qq)) for qq in (0.25, 0.5, 0.75, 0.9)] + [1e9]
+    for tau in taus:
         for use_nu in (False, True):
             cnt.zero_()
             plan.reconstruct_learned(lr, hr, sl, max_missing=tau, use_nu_hat=use_nu, counter=cnt)
@@ -419,6 +421,8 @@ def run_learned(args):
             "train": {"images": args.train_images, "samples": args.train_images * 256, "epochs": args.epochs,
                       "data_s": t_data, "train_s": t_train, "loss_first": losses[0], "loss_last": losses[-1],
                       "heldout_recall_at_64": rec},
+            "missing_quantiles": {"p10": float(np.quantile(missing, 0.1)), "p50": float(np.quantile(missing, 0.5)),
+                                  "p90": float(np.quantile(missing, 0.9))},
             "best_within_0.05dB": best, "untrained_control": control, "points": points}
     print(json.dumps(line), flush=True)
 

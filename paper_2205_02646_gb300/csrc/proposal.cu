@@ -415,8 +415,10 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
             const uint32_t u = __float_as_uint(v[j]);
             key[j] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
         }
-        // the 64th largest key: binary search on the key bits, counting with ballots
+        // Binary search on the key bits for the 64th largest key; stop early
+        // once exactly 64 keys reach the candidate (then they are the set).
         uint32_t thr = 0;
+        bool exact = false;
         for (int bit = 31; bit >= 0; --bit) {
             const uint32_t cand = thr | (1u << bit);
             int cnt = 0;
@@ -424,8 +426,35 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
             for (int j = 0; j < 32; ++j) cnt += key[j] >= cand;
             for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
             if (cnt >= kShortlist) thr = cand;
+            if (cnt == kShortlist) { exact = true; break; }       // warp-uniform
         }
-        // take keys > thr, then keys == thr by increasing index, up to 64
+        Shortlist &sl = out[b0 + bl];
+        float rest = 0.f;
+        if (exact) {
+            // exactly the keys >= thr, in lane-major order
+            int mine = 0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) mine += key[j] >= thr;
+            int base = mine;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, base, o);
+                if (lane >= o) base += y;
+            }
+            int pos = base - mine;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (key[j] >= thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (key[j] < thr) rest += 1.f / (1.f + __expf(-v[j]));
+            for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+            if (lane == 0) {
+                sl.missing = rest;
+                sl.nu_frac = zb[1024] + bias[1024];
+            }
+            continue;
+        }
+        // thr is the 64th largest key: take keys > thr, then keys == thr by increasing index
         int above = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) above += key[j] > thr;
@@ -437,9 +466,7 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
             if (lane >= o) base += y;
         }
         base -= above;                           // exclusive prefix
-        Shortlist &sl = out[b0 + bl];
         int pos = base;
-        float rest = 0.f;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
             if (key[j] > thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
