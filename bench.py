@@ -427,6 +427,53 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_random_mask(args):
+    """The 1024x1024 image behind a fully random (non-recurrent) mask:
+    tables built per block in the kernel on the full image, and the direct
+    L-JSDE path (O(W^4) per iteration) on a 128x128 crop, beside the
+    recurrent 4x4-tile image."""
+    import torch
+    from paper_2205_02646_gb300 import build, rljsde, synth
+    build.build()
+    torch.cuda.set_device(0)
+    out = {"study": "random-mask", "workload": "rljsde_1024x1024", "nu_max": args.nu_max}
+
+    def timed(plan, lr, hr, reps):
+        plan.reconstruct(lr, hr)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.reconstruct(lr, hr)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        plan.check()
+        return best
+
+    for name, random in (("recurrent_4x4_tile", False), ("random_mask", True)):
+        f, mask, y = synth.workload("rljsde_1024x1024", random=random)
+        t0 = time.perf_counter()
+        plan = rljsde.Plan(mask, rljsde.default_params(nu_max=args.nu_max))
+        t_plan = time.perf_counter() - t0
+        lr = torch.from_numpy(y).cuda()
+        hr = torch.empty((1024, 1024), device="cuda")
+        ms = timed(plan, lr, hr, args.steps)
+        info = plan.info()
+        out[name] = {"mp_per_s": 1.048576 / (ms / 1e3), "ms": ms, "plan_s": t_plan, "tables": info["n_tables"],
+                     "tables_in_kernel": info["device_table_bytes"] == 0}
+        if random:
+            crop_m = np.ascontiguousarray(mask[:64, :64])
+            crop_y = np.ascontiguousarray(y[:64, :64])
+            dplan = rljsde.Plan(crop_m, rljsde.default_params(nu_max=args.nu_max, path=2))
+            dlr = torch.from_numpy(crop_y).cuda()
+            dhr = torch.empty((128, 128), device="cuda")
+            dms = timed(dplan, dlr, dhr, 1)
+            out["direct_l_jsde_128x128_crop"] = {"mp_per_s": 0.016384 / (dms / 1e3), "ms": dms, "blocks": 1024}
+    print(json.dumps(out), flush=True)
+
+
 def run_learned_launch(args):
     """The learned inference path (whole-image proposal, shortlist loop,
     fallback pass) run twice with a seeded untrained network: the launch
@@ -458,7 +505,7 @@ def main():
     ap.add_argument("--nu-max", type=int, default=100)
     ap.add_argument("--ref-blocks", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "precision", "learned-launch"])
+    ap.add_argument("--study", default=None, choices=[None, "precision", "learned-launch", "random-mask"])
     ap.add_argument("--sample", type=int, default=3072)
     ap.add_argument("--train-images", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=6)
@@ -477,6 +524,9 @@ def main():
         return
     if args.study == "learned-launch":
         run_learned_launch(args)
+        return
+    if args.study == "random-mask":
+        run_random_mask(args)
         return
     if args.workload == "rljsde_learned":
         run_learned(args)

@@ -65,10 +65,15 @@ typedef struct {
     const double *q_table;/* host, W*W entries row-major over (sigma, rho), q_mode 2 */
     int precision;        /* 0 = FP32 loop (tables built in FP64, stored FP32);
                              1 = FP64 loop                                           */
-    int path;             /* 0 = recurrent (one table set per distinct local
-                             measurement matrix, Eqs. 11-17); 2 = direct L-JSDE
-                             (Eqs. 4-10: residual r kept, O(W^4) projection every
-                             iteration, no tables)                                   */
+    int path;             /* 1 = recurrent with one table set per distinct local
+                             measurement matrix built on the host (Eqs. 11-17);
+                             2 = direct L-JSDE (Eqs. 4-10: residual r kept, O(W^4)
+                             projection every iteration, no tables); 3 = recurrent
+                             with each block's tables built in the kernel in FP32
+                             (for non-recurrent sensors, FP32 loops only);
+                             0 = auto: 3 if precision is 0 and there are more than
+                             4096 distinct local matrices, more than a quarter of
+                             the blocks, else 1                                    */
 } rljsde_params;
 
 /* Fill *p with the defaults above.  Returns RLJSDE_ERR_INVALID_ARG on NULL. */

@@ -184,7 +184,9 @@ __device__ __forceinline__ const uint8_t *rec_types(const Record<double> &r) { r
 // ------------------------------------------- initial projected residual --
 // Steps 1-2 for one block: gather the weighted window and run the 16x16 DFTs
 // per type; returns Y[i][t] for kap = (8h + i, lane & 15), h = lane >> 4.
-template <typename T, typename Rec>
+// With UNIT, y is taken as 1 for every present L-pixel: the result is then
+// the DFT of the type-split spatial weights, whose conjugate is G_t.
+template <typename T, bool UNIT = false, typename Rec>
 __device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec, C2<T> *scratch,
                                                    const C2<T> *omc, const T *wt, const WorkEntry we,
                                                    const int lane, C2<T> (&Y)[8][4])
@@ -205,9 +207,13 @@ __device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec
             const int code = types[p * 16 + q];
             T v = 0;
             if (code < 4 && P >= 0 && P < img.lr_h && Q >= 0 && Q < img.lr_w) {
-                const float y = img.lr[(long long)P * img.lr_pitch + Q];
-                if (isfinite(y)) v = wt[p * 16 + q] * (T)y;
-                else bad = true;
+                if (UNIT) {
+                    v = wt[p * 16 + q];
+                } else {
+                    const float y = img.lr[(long long)P * img.lr_pitch + Q];
+                    if (isfinite(y)) v = wt[p * 16 + q] * (T)y;
+                    else bad = true;
+                }
             }
             Vec4<T> o = {code == 0 ? v : T(0), code == 1 ? v : T(0), code == 2 ? v : T(0), code == 3 ? v : T(0)};
             st4(&x4[p * 16 + q], o);
@@ -868,6 +874,136 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
     }
 }
 
+// ------------------------------------------- tables built per block --
+// For masks whose local measurement matrices rarely repeat (a non-recurrent
+// sensor), each warp builds its block's factored tables itself, in FP32:
+//   G_t(d) = conj(DFT of the type-t spatial weights)(d)     (the UNIT DFT),
+//   D_k = sum_t |h_t(k)|^2 G_t(0),  q/D and 1/D per candidate,
+// into a per-warp RecordF32 in shared memory, then runs the same FP32 loop.
+// The DFT scratch of the warp aliases the record's invD array, which is
+// written only after the last DFT.
+constexpr int kFlyWarps = 4;
+struct FlySmem {
+    static constexpr size_t rec = sizeof(RecordF32);
+    static constexpr size_t off_rec = 0;                                   // kFlyWarps records
+    static constexpr size_t off_om = kFlyWarps * rec;
+    static constexpr size_t off_omc = off_om + 32 * sizeof(C2<float>);
+    static constexpr size_t off_pair = off_omc + 32 * sizeof(C2<float>);
+    static constexpr size_t off_w = off_pair + sizeof(PairTables);
+    static constexpr size_t off_q = off_w + 256 * sizeof(float);            // q per candidate
+    static constexpr size_t bytes = off_q + kK * sizeof(float);
+};
+static_assert(offsetof(RecordF32, invD) % 16 == 0 && sizeof(RecordF32::invD) >= 256 * 2 * sizeof(C2<float>),
+              "the DFT scratch must fit in invD");
+
+__global__ void __launch_bounds__(kFlyWarps * 32, 2) onthefly_kernel(const Args a, int n_entries)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    using L = FlySmem;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RecordF32 &rec = *reinterpret_cast<RecordF32 *>(smem + L::off_rec + warp * L::rec);
+    C2<float> *scratch = reinterpret_cast<C2<float> *>(rec.invD);
+    C2<float> *om = reinterpret_cast<C2<float> *>(smem + L::off_om);
+    C2<float> *omc = reinterpret_cast<C2<float> *>(smem + L::off_omc);
+    PairTables *pt = reinterpret_cast<PairTables *>(smem + L::off_pair);
+    float *wt = reinterpret_cast<float *>(smem + L::off_w);
+    float *qv = reinterpret_cast<float *>(smem + L::off_q);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) wt[i] = a.consts->w32[i];
+    for (int i = threadIdx.x; i < kK; i += blockDim.x) qv[i] = a.q[i];
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+        const float re = a.consts->om32[2 * i], im = a.consts->om32[2 * i + 1];
+        om[i] = {re, im};
+        omc[i] = {re, -im};
+        const int n1 = (i + 1) & 31;
+        pt->e12[i] = make_float4(re, a.consts->om32[2 * n1], im, a.consts->om32[2 * n1 + 1]);
+        pt->e12n[i] = make_float2(-im, -a.consts->om32[2 * n1 + 1]);
+        if (i < 8) {
+            const float ca = a.consts->om32[4 * i], sa = a.consts->om32[4 * i + 1];
+            const float cb = a.consts->om32[4 * i + 2], sb = a.consts->om32[4 * i + 3];
+            pt->e2[i] = make_float4(ca, cb, sa, sb);
+            pt->e2n[i] = make_float2(-sa, -sb);
+        }
+    }
+    __syncthreads();
+    const int k2 = lane & 15, h = lane >> 4;
+    for (int e = blockIdx.x * kFlyWarps + warp; e < n_entries; e += gridDim.x * kFlyWarps) {
+        const WorkEntry we = a.entries[e];
+        if (we.img < 0) continue;
+        const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
+        const uint8_t *mask = a.masks + a.mask_offset[we.img];
+        const int p0 = 2 * we.bi - kOff / 2, q0 = 2 * we.bj - kOff / 2;
+        __syncwarp();                       // the previous block is done with the record
+        for (int m = lane; m < 256; m += 32) {
+            const int P = p0 + (m >> 4), Q = q0 + (m & 15);
+            rec.types[m] = (P >= 0 && P < img.lr_h && Q >= 0 && Q < img.lr_w) ? mask[(long long)P * img.lr_w + Q] : 255;
+        }
+        __syncwarp();
+        // G_t(d1, d2) = conj(Yw_t(d1, d2)) for d1 = 8h + i, d2 = k2
+        C2<float> Yw[8][4];
+        initial_projection<float, true>(a, rec, scratch, omc, wt, we, lane, Yw);
+        C2<float> prev[4];                  // G_t(8h - 1, k2), owned by the other half
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            prev[t].re = __shfl_xor_sync(0xffffffffu, Yw[7][t].re, 16);
+            prev[t].im = -__shfl_xor_sync(0xffffffffu, Yw[7][t].im, 16);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int d1 = 8 * h + i;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const C2<float> ga = cconj(Yw[i][t]);
+                const C2<float> gb = i > 0 ? cconj(Yw[i - 1][t]) : prev[t];
+                *reinterpret_cast<float4 *>(rec.GP[t][d1][k2]) = make_float4(ga.re, gb.re, ga.im, gb.im);
+            }
+        }
+        // G_t(0) = total weight of type t: from lane 0 (d = (0, 0))
+        float W0[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) W0[t] = __shfl_sync(0xffffffffu, Yw[0][t].re, 0);
+        // D, q/D for this lane's 32 candidates k = (8h + i + 16A, k2 + 16B)
+        float invd[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float qd[4];
+#pragma unroll
+            for (int A = 0; A < 2; ++A)
+#pragma unroll
+                for (int B = 0; B < 2; ++B) {
+                    const int k = (8 * h + i + 16 * A) * kW + k2 + 16 * B;
+                    float D = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const C2<float> ht = h_of(om, k, t);
+                        D += (ht.re * ht.re + ht.im * ht.im) * W0[t];
+                    }
+                    const float inv = D > 1e-30f ? 1.0f / D : 0.f;
+                    invd[i][2 * A + B] = inv;
+                    qd[2 * A + B] = qv[k] * inv;
+                }
+            // qDP[j][A][k2] = (qD(2j, B=0), qD(2j+1, B=0), qD(2j, B=1), qD(2j+1, B=1))
+            const int j = (8 * h + i) >> 1, el = i & 1;
+#pragma unroll
+            for (int A = 0; A < 2; ++A) {
+                rec.qDP[j][A][k2][el] = qd[2 * A];
+                rec.qDP[j][A][k2][2 + el] = qd[2 * A + 1];
+            }
+        }
+        C2<float> Y[8][4];
+        initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
+        __syncwarp();                       // scratch (= invD) no longer needed
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int A = 0; A < 2; ++A)
+#pragma unroll
+                for (int B = 0; B < 2; ++B) rec.invD[(8 * h + i + 16 * A) * kW + k2 + 16 * B] = invd[i][2 * A + B];
+        __syncwarp();
+        greedy_loop_f32(a, rec, om, omc, *pt, we, lane, Y);
+    }
+}
+
 // ---------------------------------------------------------- direct path --
 // Direct L-JSDE (Eqs. 4-10): per block the residual r (256 complex, in the
 // warp's scratch) and, every iteration, N_k = sum_m conj(a_m(k)) w_m r_m for
@@ -1068,6 +1204,8 @@ int launch(const rljsde_plan *p, const Args &a, cudaStream_t s)
 {
     if (p->direct) {
         direct_kernel<<<p->grid, kDirectWarps * 32, 0, s>>>(a, p->n_entries);
+    } else if (p->onthefly) {
+        onthefly_kernel<<<p->grid, kFlyWarps * 32, FlySmem::bytes, s>>>(a, p->n_entries);
     } else {
         const Variant &v = kVariants[p->variant];
         v.fn<<<p->grid, v.warps * 32, v.smem, s>>>(a);
@@ -1095,6 +1233,21 @@ int launch_mode(const rljsde_plan *p, const Args &a, int mode, int warps, int mi
 
 int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
 {
+    if (p->onthefly) {
+        int n = 0;
+        if (cudaFuncSetAttribute(onthefly_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FlySmem::bytes) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, onthefly_kernel, kFlyWarps * 32, FlySmem::bytes) !=
+                cudaSuccess)
+            return RLJSDE_ERR_CUDA;
+        if (n < 1) return RLJSDE_ERR_UNSUPPORTED;
+        p->warps = kFlyWarps;
+        p->ctas_per_sm = ctas_per_sm > 0 ? (ctas_per_sm < n ? ctas_per_sm : n) : n;
+        long long want = ((long long)p->n_entries + kFlyWarps - 1) / kFlyWarps;
+        long long g = (long long)p->sm_count * p->ctas_per_sm;
+        p->grid = (int)(want < g ? (want > 0 ? want : 1) : g);
+        return RLJSDE_OK;
+    }
     if (p->direct) {
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_kernel, kDirectWarps * 32, 0) != cudaSuccess)
@@ -1165,7 +1318,8 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
                                uint16_t *sel, float *dc, int *n_restricted, void *stream)
 {
     if (!plan || !lr || !hr || !shortlists) return RLJSDE_ERR_INVALID_ARG;
-    if (plan->n_images != 1 || plan->direct || plan->params.precision != 0) return RLJSDE_ERR_UNSUPPORTED;
+    if (plan->n_images != 1 || plan->direct || plan->onthefly || plan->params.precision != 0)
+        return RLJSDE_ERR_UNSUPPORTED;
     if (lr_pitch < (size_t)plan->lr_w[0] || hr_pitch < (size_t)(2 * plan->lr_w[0])) return RLJSDE_ERR_INVALID_ARG;
     if ((sel == nullptr) != (dc == nullptr)) return RLJSDE_ERR_INVALID_ARG;
     Args a = make_args(plan);
@@ -1212,7 +1366,7 @@ int rljsde_autotune(rljsde_plan_t *plan, const float *lr, size_t lr_pitch, float
     int best_w = keep_w, best_c = keep_c, st = RLJSDE_OK;
     const int shapes[][2] = {{4, 1}, {4, 2}, {4, 3}, {4, 4}, {8, 1}, {8, 2}};
     for (const auto &sh : shapes) {
-        if (plan->direct) break;
+        if (plan->direct || plan->onthefly) break;
         if (choose_launch(plan, sh[0], sh[1]) != RLJSDE_OK) continue;
         if (plan->ctas_per_sm != sh[1]) continue;          // did not fit
         if ((st = launch(plan, a, s)) != RLJSDE_OK) break; // warm-up

@@ -208,8 +208,8 @@ int check_params(const rljsde_params *p)
         for (int k = 0; k < kK; ++k)
             if (!(p->q_table[k] >= 0.0) || !std::isfinite(p->q_table[k])) return RLJSDE_ERR_INVALID_ARG;
     if (p->precision != 0 && p->precision != 1) return RLJSDE_ERR_INVALID_ARG;
-    if (p->path != 0 && p->path != 2) return RLJSDE_ERR_INVALID_ARG;
-    if (p->path == 2 && p->precision != 0) return RLJSDE_ERR_UNSUPPORTED;
+    if (p->path < 0 || p->path > 3) return RLJSDE_ERR_INVALID_ARG;
+    if ((p->path == 2 || p->path == 3) && p->precision != 0) return RLJSDE_ERR_UNSUPPORTED;
     return RLJSDE_OK;
 }
 
@@ -310,6 +310,13 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         }
         p->n_tables = (int)keys.size();
         for (char c : interior) p->n_interior += c;
+        // Mostly unique windows (a non-recurrent sensor): build each block's
+        // tables in the kernel instead of one host table set per block.
+        // (Small images keep host tables: their build is cheap.)
+        p->onthefly = prm->path == 3 ||
+                      (prm->path == 0 && prm->precision == 0 && 4ll * p->n_tables > ord && p->n_tables > 4096);
+        if (p->onthefly)
+            for (auto &t : table_of) t = 0;
     } else {
         for (int i = 0; i < n_images; ++i) {
             p->ord_base[i] = ord;
@@ -324,7 +331,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
 
     // Work list: blocks sorted by table, each table's run padded to whole
     // chunks so that every chunk uses exactly one table.
-    int n_groups = p->direct ? 1 : p->n_tables;
+    int n_groups = (p->direct || p->onthefly) ? 1 : p->n_tables;
     std::vector<int> count(n_groups, 0), start(n_groups + 1, 0);
     for (int t : table_of) ++count[t];
     for (int g = 0; g < n_groups; ++g) start[g + 1] = start[g] + (count[g] + kChunk - 1) / kChunk * kChunk;
@@ -358,7 +365,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         for (int i = 0; i < n_images; ++i) descs[i] = {nullptr, nullptr, lr_h[i], lr_w[i], 0, 0};
         st = upload(&p->d_images, descs.data(), descs.size() * sizeof(ImageDesc));
     }
-    if (!st && !p->direct) {
+    if (!st && !p->direct && !p->onthefly) {
         // FP64 tables per distinct local matrix, stored in the loop's precision.
         p->record_bytes = prm->precision ? sizeof(Record<double>) : sizeof(RecordF32);
         std::vector<unsigned char> host, host_short;
@@ -382,8 +389,8 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             if (!st && !prm->precision) st = upload(&p->d_records_short, host_short.data(), host_short.size());
         }
     }
-    if (!st && p->direct) {
-        // Direct path: q on the device, no tables.
+    if (!st && (p->direct || p->onthefly)) {
+        // Direct path and in-kernel tables: q on the device, no host tables.
         std::vector<float> qf(kK);
         for (int k = 0; k < kK; ++k) qf[k] = (float)p->q[k];
         st = upload(&p->d_qD, qf.data(), qf.size() * sizeof(float));

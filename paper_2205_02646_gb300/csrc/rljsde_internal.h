@@ -114,6 +114,7 @@ struct rljsde_plan {
     int n_blocks = 0, n_tables = 0, n_interior = 0;
     int n_entries = 0, n_chunks = 0;
     int direct = 0;                   // path == 2
+    int onthefly = 0;                 // tables built per block in the kernel (path 3, or auto)
     int device = 0, sm_count = 0;
     int warps = 4, ctas_per_sm = 0, grid = 0, variant = 0;
     int learned_warps = 4;            // warps per CTA of the shortlist-loop kernel (4: two blocks per warp)

@@ -233,3 +233,27 @@ def test_batch_graph_and_autotune(rl):
             bi, bj = divmod(int(b), nbw)
             err = np.abs(g[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4] - ohr[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4])
             assert err.max() < TOL or tr["gap"].min() < TIE
+
+
+def test_random_mask_tables_built_in_kernel_vs_oracle(rl):
+    """A non-recurrent sensor: every window is its own local matrix, so the
+    plan builds each block's tables in the kernel (FP32)."""
+    f = synth.image(64, 64, 32, 4, 1234)
+    mask = synth.random_mask(32, 32, 99)
+    y = synth.measure(f, mask).astype(np.float32)
+    g = gpu_run(rl, y, mask, path=3)
+    assert g["plan"].info()["device_table_bytes"] == 0          # no host tables
+    hr, tr = oracle_run(y, mask)
+    res = compare(g["hr"], g["sel"], hr, tr["sel"], tr["gap"], np.arange(256), 16, TOL, TIE,
+                  gpu_dc=g["dc"], orc_dc=tr["dc"])
+    check(res)
+
+
+def test_tables_built_in_kernel_equal_host_tables(rl):
+    f, mask, y = synth.workload("rljsde_64x64", index=7)
+    a = gpu_run(rl, y, mask, path=1)
+    b = gpu_run(rl, y, mask, path=3)
+    same = (a["sel"] == b["sel"]).all(axis=1)
+    assert same.mean() >= 0.97
+    d = np.abs(a["hr"] - b["hr"]).reshape(16, 4, 16, 4).max(axis=(1, 3)).ravel()
+    assert d[same].max() <= 1e-4
