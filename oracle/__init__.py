@@ -9,14 +9,18 @@ this module only marshals numpy arrays into it.
 
 Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``):
 
-* ``measure``            -- pinned: hand-evaluated sums, linearity.
+* ``measure``            -- pinned: hand-evaluated sums, linearity; the
+  aperture layout against the three-quarter codes it generalises.
 * ``window_solve``       -- pinned: brute-force weighted least squares per
   candidate on tiny windows, energy identity, single-atom recovery,
   identity-measurement reduction to ``numpy.fft.fft2`` with exact sparse
   recovery, measurement consistency, invariances.
 * ``window_tables``      -- pinned: dense ``M^H diag(w) M`` built with
   ``numpy.exp``, Hermitian symmetry, Cauchy-Schwarz bound.
-* ``reconstruct``        -- pinned through the above plus direct == recurrent.
+* ``reconstruct``        -- pinned through the above plus direct == recurrent;
+  aperture layouts: three-quarter apertures == opaque codes, quarter
+  sampling and the full 2x2 aperture reduce to closed forms built on
+  ``numpy.fft.fft2``, unobservable Nyquist candidates never selected.
 * ``frequency_weight``   -- the paper gives no formula (Sec. IV only says q
   prefers low frequencies): parity unpinned against the paper; the tests
   check the stated reading's properties (1 at DC, symmetric, isotropic,
@@ -33,7 +37,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Params", "measure", "window_solve", "window_tables", "reconstruct",
+__all__ = ["Params", "LAYOUT_THREE_QUARTER", "LAYOUT_APERTURE", "measure", "window_solve", "window_tables", "reconstruct",
            "count_local_masks", "frequency_weight", "load"]
 
 _lib = None
@@ -42,24 +46,31 @@ _lib = None
 class _CParams(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("block", ctypes.c_int), ("nu_max", ctypes.c_int),
                 ("gamma_odc", ctypes.c_double), ("rho_decay", ctypes.c_double),
-                ("q_mode", ctypes.c_int), ("q_table", ctypes.POINTER(ctypes.c_double))]
+                ("q_mode", ctypes.c_int), ("q_table", ctypes.POINTER(ctypes.c_double)),
+                ("layout", ctypes.c_int)]
+
+
+LAYOUT_THREE_QUARTER = 0   # mask code = index 2 * dy + dx of the opaque sub-pixel
+LAYOUT_APERTURE = 1        # mask code = bit set of the transparent sub-pixels
 
 
 class Params:
-    """Reconstruction parameters (window W, block B, nu_max, gamma_odc, rho, q)."""
+    """Reconstruction parameters (window W, block B, nu_max, gamma_odc, rho, q,
+    and the meaning of the mask codes)."""
 
     def __init__(self, window=32, block=4, nu_max=100, gamma_odc=0.5, rho_decay=0.7,
-                 q_mode=0, q_table=None):
+                 q_mode=0, q_table=None, layout=LAYOUT_THREE_QUARTER):
         self.window, self.block, self.nu_max = int(window), int(block), int(nu_max)
         self.gamma_odc, self.rho_decay, self.q_mode = float(gamma_odc), float(rho_decay), int(q_mode)
         self.q_table = None if q_table is None else np.ascontiguousarray(q_table, dtype=np.float64)
+        self.layout = int(layout)
 
     def c(self):
         qp = None
         if self.q_table is not None:
             qp = self.q_table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         return _CParams(self.window, self.block, self.nu_max, self.gamma_odc, self.rho_decay,
-                        self.q_mode, qp)
+                        self.q_mode, qp, self.layout)
 
 
 def load():
@@ -78,14 +89,15 @@ def _check(st, what):
         raise RuntimeError("oracle %s failed with status %d" % (what, st))
 
 
-def measure(f: np.ndarray, mask: np.ndarray) -> np.ndarray:
-    """Eq. 1 three-quarter measurement (sum of the three transparent sub-pixels)."""
+def measure(f: np.ndarray, mask: np.ndarray, layout: int = LAYOUT_THREE_QUARTER) -> np.ndarray:
+    """Eq. 1 measurement: each L-pixel sums its transparent sub-pixels (three
+    for three-quarter sampling; the code's bit set for ``LAYOUT_APERTURE``)."""
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     lr_h, lr_w = mask.shape
     f = np.ascontiguousarray(f, dtype=np.float64)
     assert f.shape == (2 * lr_h, 2 * lr_w)
     y = np.empty((lr_h, lr_w), np.float64)
-    _check(load().orc_measure(_p(f), _p(mask), lr_h, lr_w, _p(y)), "measure")
+    _check(load().orc_measure(_p(f), _p(mask), lr_h, lr_w, int(layout), _p(y)), "measure")
     return y
 
 
@@ -154,10 +166,10 @@ def window_tables(pixels, w, W):
 
 def reconstruct(y, mask, params: Params, blocks=None, recurrent=False, n_threads=None,
                 trace=False):
-    """Reconstruct a three-quarter sampled image (or a list of its blocks).
+    """Reconstruct an image measured by Eq. 1 (or a list of its blocks).
 
-    ``y`` are the lr_h x lr_w measurements, ``mask`` the opaque-quadrant
-    codes.  ``blocks`` lists linear block indices ``bi * (2 lr_w / B) + bj``
+    ``y`` are the lr_h x lr_w measurements, ``mask`` the per-pixel codes in
+    ``params.layout`` (opaque sub-pixel 0..3, or transparent set 0..15).  ``blocks`` lists linear block indices ``bi * (2 lr_w / B) + bj``
     (default: every block); only those blocks of the returned HR image are
     written (the rest stay NaN).  With ``trace`` the per-block selection
     sequence, coefficient increments and FP64 score gaps are returned too.

@@ -10,8 +10,11 @@
  * itself never calls it and shares no code, table or helper with it.
  *
  * What it implements, in the paper's order and notation:
- *   - the sensor model, Eq. 1 (coefficients A = 1 on the three transparent
- *     sub-pixels of each L-pixel, i.e. a sum);
+ *   - the sensor model, Eq. 1 (coefficients A = 1 on the transparent
+ *     sub-pixels of each L-pixel, i.e. a sum): three-quarter sampling, where
+ *     one of the four sub-pixels is opaque, or any other per-pixel aperture
+ *     (Sec. I: arbitrary periodically repeating layouts), given as the set
+ *     of transparent sub-pixels;
  *   - the window model of Eqs. 2-3 with the Fourier basis
  *     Phi_{eta,gamma,sigma,rho} = exp(2 pi j (eta sigma + gamma rho) / W)
  *     (Sec. III prints M and N in the exponent; the sums run over the W x W
@@ -35,7 +38,13 @@
  *   - argmax (Eqs. 10, 11): evaluated on the score rounded to binary32, the
  *     precision of the paper's complex64 tables (Table I); ties go to the
  *     lowest linear index sigma * W + rho;
- *   - a window position outside the image holds no measurement;
+ *   - a window position outside the image holds no measurement, and neither
+ *     does an L-pixel whose aperture is empty;
+ *   - a candidate whose atom vanishes identically on every measurement of
+ *     the window (its sub-pixel phases cancel in antipodal pairs, e.g. the
+ *     Nyquist row or column under a full 2x2 aperture) cannot be observed:
+ *     its score is 0 and its delta 0, instead of a ratio of two rounding
+ *     residues;
  *   - the target block sits at window offset (W - B) / 2 in both axes;
  *   - the output is the real part of the back-transformed model (Eq. 18).
  *
@@ -60,7 +69,22 @@ typedef struct {
     double rho_decay;    /* base of the isotropic spatial weight, Eq. 8       */
     int q_mode;          /* 0: default q, 1: q = 1, 2: q_table                */
     const double *q_table; /* W*W entries, row-major over (sigma, rho)        */
+    int layout;          /* mask codes: 0 = index of the opaque sub-pixel of
+                            a three-quarter pixel (0..3); 1 = set of
+                            transparent sub-pixels, bit 2 * dy + dx (0..15) */
 } orc_params;
+
+/* Sub-pixel s = 2 * dy + dx of an L-pixel with mask code `code` is
+ * transparent (Eq. 1: A = 1 there). */
+static int transparent(int layout, int code, int s)
+{
+    return layout == 1 ? (code >> s) & 1 : s != code;
+}
+
+static int code_valid(int layout, int code)
+{
+    return layout == 1 ? code >= 0 && code <= 15 : code >= 0 && code <= 3;
+}
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2 };
 
@@ -143,6 +167,34 @@ static void measurement_atoms(const orc_window *win, const cplx *om, cplx *a)
     }
 }
 
+/* Exact test that a_m(k) = sum_i w^(n_i) vanishes.  For W a power of two the
+ * cyclotomic polynomial of w is x^(W/2) + 1, so 1, w, ..., w^(W/2 - 1) are
+ * linearly independent over the rationals and a sum with integer counts c_n
+ * of each power vanishes iff c_n = c_(n + W/2) for every n < W/2 (the terms
+ * cancel in antipodal pairs).  For other W this is the pairwise part of the
+ * condition only. */
+static int atom_vanishes(const orc_window *win, int m, int s, int r)
+{
+    int W = win->W, cnt[128] = {0};
+    for (int i = 0; i < win->npx[m]; ++i)
+        ++cnt[(win->eta[4 * m + i] * s + win->gam[4 * m + i] * r) % W];
+    for (int n = 0; n < W / 2; ++n)
+        if (cnt[n] != cnt[n + W / 2]) return 0;
+    return 1;
+}
+
+/* flag[k] = 1 when the atom of candidate k vanishes on every measurement. */
+static void unobservable(const orc_window *win, char *flag)
+{
+    int W = win->W;
+    for (int s = 0; s < W; ++s)
+        for (int r = 0; r < W; ++r) {
+            int all = 1;
+            for (int m = 0; m < win->nm && all; ++m) all = atom_vanishes(win, m, s, r);
+            flag[s * W + r] = (char)all;
+        }
+}
+
 /* Argmax of Eq. 10 / Eq. 11 on binary32-rounded scores, lowest index on
  * ties.  Also reports the FP64 relative gap to the best other candidate. */
 static int select_atom(int K, const double *score, double *gap_out)
@@ -178,11 +230,13 @@ static int window_direct(const orc_window *win, const orc_params *p, const cplx 
     cplx *wr = malloc(sizeof(cplx) * (size_t)(nm > 0 ? nm : 1));
     cplx *N = malloc(sizeof(cplx) * K);
     double *D = malloc(sizeof(double) * K), *score = malloc(sizeof(double) * K);
-    if (!a || !r || !wr || !N || !D || !score) {
-        free(a); free(r); free(wr); free(N); free(D); free(score);
+    char *zero = malloc(K);
+    if (!a || !r || !wr || !N || !D || !score || !zero) {
+        free(a); free(r); free(wr); free(N); free(D); free(score); free(zero);
         return ORC_ENOMEM;
     }
     measurement_atoms(win, om, a);
+    unobservable(win, zero);
     /* denominator of Eq. 10: D_k = sum_m w_m |a_m(k)|^2 */
     for (int k = 0; k < K; ++k) D[k] = 0.0;
     for (int m = 0; m < nm; ++m) {
@@ -206,10 +260,10 @@ static int window_direct(const orc_window *win, const orc_params *p, const cplx 
             for (int k = 0; k < K; ++k) N[k] += conj(am[k]) * x;
         }
         for (int k = 0; k < K; ++k)
-            score[k] = D[k] < 1e-300 ? 0.0
+            score[k] = (D[k] < 1e-300 || zero[k]) ? 0.0
                      : q[k] * (creal(N[k]) * creal(N[k]) + cimag(N[k]) * cimag(N[k])) / D[k];
         int uv = select_atom(K, score, tr->gap ? &tr->gap[nu] : NULL);
-        cplx delta = D[uv] < 1e-300 ? 0.0 : N[uv] / D[uv];      /* Eq. 16 */
+        cplx delta = (D[uv] < 1e-300 || zero[uv]) ? 0.0 : N[uv] / D[uv];      /* Eq. 16 */
         cplx step = p->gamma_odc * delta;
         tr->c[uv] += step;                                         /* Eq. 15 */
         const cplx *au = a + (size_t)uv;
@@ -219,7 +273,7 @@ static int window_direct(const orc_window *win, const orc_params *p, const cplx 
         if (tr->energy) tr->energy[nu + 1] = weighted_energy(nm, win->w, r);
     }
     if (tr->r) memcpy(tr->r, r, sizeof(cplx) * (size_t)nm);
-    free(a); free(r); free(wr); free(N); free(D); free(score);
+    free(a); free(r); free(wr); free(N); free(D); free(score); free(zero);
     return ORC_OK;
 }
 
@@ -265,7 +319,9 @@ static int window_recurrent(const orc_window *win, const orc_tables *t, const or
     int K = t->K, nm = win->nm;
     cplx *R = malloc(sizeof(cplx) * K);
     double *score = malloc(sizeof(double) * K);
-    if (!R || !score) { free(R); free(score); return ORC_ENOMEM; }
+    char *zero = malloc(K);
+    if (!R || !score || !zero) { free(R); free(score); free(zero); return ORC_ENOMEM; }
+    unobservable(win, zero);
     /* R^(0)_k = sum_m B_{m,k} y_m  (Eq. 12 with r^(0) = y) */
     for (int k = 0; k < K; ++k) R[k] = 0.0;
     for (int m = 0; m < nm; ++m) {
@@ -276,10 +332,10 @@ static int window_recurrent(const orc_window *win, const orc_tables *t, const or
     for (int k = 0; k < K; ++k) tr->c[k] = 0.0;
     for (int nu = 0; nu < p->nu_max; ++nu) {
         for (int k = 0; k < K; ++k)                                   /* Eq. 11 */
-            score[k] = t->D[k] < 1e-300 ? 0.0
+            score[k] = (t->D[k] < 1e-300 || zero[k]) ? 0.0
                      : q[k] * (creal(R[k]) * creal(R[k]) + cimag(R[k]) * cimag(R[k])) / t->D[k];
         int uv = select_atom(K, score, tr->gap ? &tr->gap[nu] : NULL);
-        cplx delta = t->D[uv] < 1e-300 ? 0.0 : R[uv] / t->D[uv];    /* Eq. 16 */
+        cplx delta = (t->D[uv] < 1e-300 || zero[uv]) ? 0.0 : R[uv] / t->D[uv];    /* Eq. 16 */
         cplx step = p->gamma_odc * delta;
         tr->c[uv] += step;                                            /* Eq. 15 */
         const cplx *Cu = t->CT + (size_t)uv * K;
@@ -287,7 +343,7 @@ static int window_recurrent(const orc_window *win, const orc_tables *t, const or
         if (tr->sel) tr->sel[nu] = uv;
         if (tr->dc) { tr->dc[2 * nu] = creal(step); tr->dc[2 * nu + 1] = cimag(step); }
     }
-    free(R); free(score);
+    free(R); free(score); free(zero);
     return ORC_OK;
 }
 
@@ -296,8 +352,9 @@ static int window_recurrent(const orc_window *win, const orc_tables *t, const or
 /* ------------------------------------------------------------------ */
 static int check_params(const orc_params *p)
 {
-    if (!p || p->window < 8 || p->window % 8 || p->nu_max < 0) return ORC_EINVAL;
+    if (!p || p->window < 8 || p->window % 8 || p->window > 128 || p->nu_max < 0) return ORC_EINVAL;
     if (p->q_mode == 2 && !p->q_table) return ORC_EINVAL;
+    if (p->layout != 0 && p->layout != 1) return ORC_EINVAL;
     return ORC_OK;
 }
 
@@ -338,7 +395,7 @@ int orc_window_solve(int recurrent, int W, int nm, const int *npx, const int *et
 int orc_window_tables(int W, int nm, const int *npx, const int *eta, const int *gam,
                       const double *w, double *B_out, double *C_out, double *D_out)
 {
-    if (W < 8 || W % 8 || nm < 0) return ORC_EINVAL;
+    if (W < 8 || W % 8 || W > 128 || nm < 0) return ORC_EINVAL;
     int K = W * W;
     cplx *om = malloc(sizeof(cplx) * W);
     if (!om) return ORC_ENOMEM;
@@ -362,35 +419,36 @@ int orc_window_tables(int W, int nm, const int *npx, const int *eta, const int *
 }
 
 /* ------------------------------------------------------------------ */
-/* Three-quarter sampling images.                                      */
+/* Images: three-quarter sampling and other per-pixel apertures.       */
 /* ------------------------------------------------------------------ */
 
-/* Eq. 1: y[p][q] = sum of the three transparent sub-pixels. */
-int orc_measure(const double *f, const uint8_t *mask, int lr_h, int lr_w, double *y)
+/* Eq. 1: y[p][q] = sum of the transparent sub-pixels of L-pixel (p, q). */
+int orc_measure(const double *f, const uint8_t *mask, int lr_h, int lr_w, int layout, double *y)
 {
-    if (!f || !mask || !y || lr_h <= 0 || lr_w <= 0) return ORC_EINVAL;
+    if (!f || !mask || !y || lr_h <= 0 || lr_w <= 0 || (layout != 0 && layout != 1)) return ORC_EINVAL;
     int N = 2 * lr_w;
     for (int p = 0; p < lr_h; ++p)
         for (int q = 0; q < lr_w; ++q) {
             int code = mask[p * lr_w + q];
-            if (code > 3) return ORC_EINVAL;
+            if (!code_valid(layout, code)) return ORC_EINVAL;
             double s = 0.0;
             for (int de = 0; de < 2; ++de)
                 for (int dg = 0; dg < 2; ++dg)
-                    if (de * 2 + dg != code) s += f[(2 * p + de) * N + 2 * q + dg];
+                    if (transparent(layout, code, de * 2 + dg)) s += f[(2 * p + de) * N + 2 * q + dg];
             y[p * lr_w + q] = s;
         }
     return ORC_OK;
 }
 
 /* The measurements of the model window of block (bi, bj): every L-pixel
- * whose 2x2 footprint lies in both the window and the image. */
+ * whose 2x2 footprint lies in both the window and the image and whose
+ * aperture is not empty. */
 typedef struct {
     int nm;
     int npx[4096];
     int eta[4 * 4096], gam[4 * 4096];
     double w[4096], y[4096];
-    uint8_t key[4096];   /* opaque code per window L-pixel, 255 = absent */
+    uint8_t key[4096];   /* mask code per window L-pixel, 255 = absent */
 } block_window;
 
 static void gather_block(const double *y, const uint8_t *mask, int lr_h, int lr_w,
@@ -406,14 +464,16 @@ static void gather_block(const double *y, const uint8_t *mask, int lr_h, int lr_
             if (P < 0 || P >= lr_h || Q < 0 || Q >= lr_w) { bw->key[pm * L + qm] = 255; continue; }
             int code = mask[P * lr_w + Q];
             bw->key[pm * L + qm] = (uint8_t)code;
-            int m = bw->nm++, n = 0;
+            int m = bw->nm, n = 0;
             for (int de = 0; de < 2; ++de)
                 for (int dg = 0; dg < 2; ++dg) {
-                    if (de * 2 + dg == code) continue;
+                    if (!transparent(p->layout, code, de * 2 + dg)) continue;
                     bw->eta[4 * m + n] = 2 * pm + de;
                     bw->gam[4 * m + n] = 2 * qm + dg;
                     ++n;
                 }
+            if (n == 0) continue;          /* empty aperture: no measurement */
+            bw->nm++;
             bw->npx[m] = n;
             double dy = 2 * pm + 0.5 - centre, dx = 2 * qm + 0.5 - centre;
             bw->w[m] = pow(p->rho_decay, sqrt(dy * dy + dx * dx));
@@ -449,9 +509,10 @@ static int cmp_block_keys(const void *x, const void *y)
 }
 
 /*
- * Reconstruct the listed target blocks of a three-quarter sampled image.
+ * Reconstruct the listed target blocks of an image measured by Eq. 1.
  *   y:      lr_h x lr_w measurements (row-major)
- *   mask:   lr_h x lr_w opaque-quadrant codes 0..3
+ *   mask:   lr_h x lr_w codes in p->layout (opaque sub-pixel 0..3, or the
+ *           set of transparent sub-pixels 0..15)
  *   blocks: n_blocks linear block indices bi * (N/B) + bj, or NULL for all
  *   hr:     (2 lr_h) x (2 lr_w) output; only the listed blocks are written
  *   sel, dc, gap: per listed block nu_max entries (dc: 2 per entry); may be NULL
@@ -465,7 +526,7 @@ int orc_reconstruct(int recurrent, const double *y, const uint8_t *mask, int lr_
     if (check_params(p) || !y || !mask || !hr || lr_h <= 0 || lr_w <= 0) return ORC_EINVAL;
     int W = p->window, Bk = p->block;
     if (Bk != 4 || (W - Bk) % 4 != 0 || (2 * lr_h) % Bk || (2 * lr_w) % Bk || W / 2 > 64) return ORC_EINVAL;
-    for (size_t i = 0; i < (size_t)lr_h * lr_w; ++i) if (mask[i] > 3) return ORC_EINVAL;
+    for (size_t i = 0; i < (size_t)lr_h * lr_w; ++i) if (!code_valid(p->layout, mask[i])) return ORC_EINVAL;
     int nbh = 2 * lr_h / Bk, nbw = 2 * lr_w / Bk, N = 2 * lr_w, K = W * W, L2 = (W / 2) * (W / 2);
     int total = nbh * nbw;
     if (!blocks) n_blocks = total;

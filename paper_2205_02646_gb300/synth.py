@@ -24,6 +24,12 @@ mask tiles a ``T x T`` LR tile drawn uniformly from {0..3} (Sec. V-A uses a
 random pattern repeating every 32 HR pixels, i.e. T = 16); a non-recurrent
 mask draws every LR pixel independently.
 
+Other sensor layouts (Sec. I: any periodically repeating layout) use
+aperture codes instead: the set of transparent sub-pixels of each L-pixel,
+bit ``2 * dy + dx`` for the sub-pixel at row offset dy, column offset dx.
+Three-quarter sampling is the aperture ``15 ^ (1 << opaque)``, quarter
+sampling a single bit, a regular LR sensor the full aperture 15.
+
 All randomness comes from numpy's PCG64 generator, whose streams are the same
 on every platform.
 """
@@ -34,7 +40,18 @@ import numpy as np
 __all__ = [
     "image", "recurrent_mask", "random_mask", "measure", "workload",
     "batch_sizes", "OPAQUE_OFFSETS", "image_torch", "measure_torch",
+    "APERTURE_SETS", "aperture_mask", "apertures_of",
 ]
+
+# Named aperture sets for recurrent layouts other than three-quarter
+# sampling (codes: bit 2 * dy + dx = transparent sub-pixel).
+APERTURE_SETS = {
+    "three_quarter": (14, 13, 11, 7),
+    "quarter": (1, 2, 4, 8),
+    "pairs": (3, 12, 5, 10),            # horizontal and vertical sub-pixel pairs
+    "mixed": (1, 6, 14, 15),            # quarter, diagonal pair, three-quarter, full
+    "all": tuple(range(1, 16)),         # every non-empty aperture
+}
 
 # (row, col) offset of the opaque sub-pixel inside the 2x2 footprint, by code.
 OPAQUE_OFFSETS = ((0, 0), (0, 1), (1, 0), (1, 1))
@@ -125,15 +142,36 @@ def random_mask(lr_h: int, lr_w: int, seed: int) -> np.ndarray:
     return rng.integers(0, 4, (lr_h, lr_w), dtype=np.uint8)
 
 
-def measure(f: np.ndarray, mask: np.ndarray) -> np.ndarray:
-    """Simulate the three-quarter sensor of Eq. 1 (coefficients 1, a sum).
+def aperture_mask(lr_h: int, lr_w: int, tile: int, seed: int, codes) -> np.ndarray:
+    """Aperture codes of a ``tile x tile`` LR tile, each drawn uniformly from
+    ``codes``, repeated periodically (``tile=0``: no repetition)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    codes = np.asarray(codes, dtype=np.uint8)
+    if tile <= 0:
+        return np.ascontiguousarray(codes[rng.integers(0, len(codes), (lr_h, lr_w))])
+    t = codes[rng.integers(0, len(codes), (tile, tile))]
+    reps = (-(-lr_h // tile), -(-lr_w // tile))
+    return np.ascontiguousarray(np.tile(t, reps)[:lr_h, :lr_w])
 
-    ``y[p, q]`` is the sum of the three transparent HR sub-pixels of the
-    footprint ``f[2p:2p+2, 2q:2q+2]``; ``mask[p, q]`` names the opaque one.
+
+def apertures_of(mask: np.ndarray) -> np.ndarray:
+    """Aperture codes of an opaque-quadrant mask."""
+    return (15 ^ (1 << mask.astype(np.uint8))).astype(np.uint8)
+
+
+def measure(f: np.ndarray, mask: np.ndarray, layout: int = 0) -> np.ndarray:
+    """Simulate the sensor of Eq. 1 (coefficients 1, a sum).
+
+    ``y[p, q]`` is the sum of the transparent HR sub-pixels of the footprint
+    ``f[2p:2p+2, 2q:2q+2]``: with ``layout=0`` ``mask[p, q]`` names the one
+    opaque sub-pixel, with ``layout=1`` it is the aperture bit set.
     """
     lr_h, lr_w = mask.shape
     f = np.asarray(f, dtype=np.float64)[: 2 * lr_h, : 2 * lr_w]
     quad = f.reshape(lr_h, 2, lr_w, 2).transpose(0, 2, 1, 3).reshape(lr_h, lr_w, 4)
+    if layout == 1:
+        bits = (mask[..., None].astype(np.int64) >> np.arange(4)) & 1
+        return (quad * bits).sum(axis=2)
     total = quad.sum(axis=2)
     opaque = np.take_along_axis(quad, mask[..., None].astype(np.int64), axis=2)[..., 0]
     return total - opaque

@@ -316,3 +316,126 @@ def test_frequency_weight_reading_properties():
         zero = np.argwhere(q < 1e-12)
         assert zero.tolist() == [[W // 2, W // 2]]
         assert np.all(q >= 0.0)
+
+
+# --- other sensor layouts: per-pixel apertures (Sec. I) ----------------------
+def aperture_pixels(codes):
+    """Window coordinates of the transparent sub-pixels of each L-pixel with
+    aperture code in 1..15 (bit 2 * dy + dx); 0 and 255 hold no measurement."""
+    L = codes.shape[0]
+    pix = []
+    for pm in range(L):
+        for qm in range(L):
+            c = int(codes[pm, qm])
+            if c == 255 or c == 0:
+                continue
+            pix.append([(2 * pm + a, 2 * qm + b) for a in (0, 1) for b in (0, 1) if (c >> (2 * a + b)) & 1])
+    return pix
+
+
+def test_measure_aperture_layout():
+    f = np.arange(16, dtype=float).reshape(4, 4)
+    mask = np.array([[1, 6], [15, 0]], np.uint8)
+    # (0,0): TL only = 0; (0,1): TR 3 + BL 6; (1,0): all four; (1,1): nothing
+    assert oracle.measure(f, mask, oracle.LAYOUT_APERTURE).tolist() == [[0.0, 9.0], [42.0, 0.0]]
+    g = rng(2).random((64, 48))
+    m = synth.random_mask(32, 24, 4)
+    np.testing.assert_array_equal(oracle.measure(g, synth.apertures_of(m), 1), oracle.measure(g, m))
+    a = synth.aperture_mask(32, 24, 0, 5, synth.APERTURE_SETS["all"])
+    np.testing.assert_allclose(oracle.measure(g, a, 1), synth.measure(g, a, 1), rtol=0, atol=1e-13)
+    with pytest.raises(RuntimeError):
+        oracle.measure(g, np.full((32, 24), 4, np.uint8))
+    with pytest.raises(RuntimeError):
+        oracle.measure(g, np.full((32, 24), 16, np.uint8), 1)
+
+
+def test_three_quarter_apertures_equal_opaque_codes():
+    f, mask, y = synth.workload("rljsde_64x64")
+    y = y.astype(np.float64)
+    for rec in (False, True):
+        p0 = oracle.Params(window=16, nu_max=40)
+        p1 = oracle.Params(window=16, nu_max=40, layout=oracle.LAYOUT_APERTURE)
+        a, ta = oracle.reconstruct(y, mask, p0, recurrent=rec, trace=True)
+        b, tb = oracle.reconstruct(y, synth.apertures_of(mask), p1, recurrent=rec, trace=True)
+        assert np.array_equal(ta["sel"], tb["sel"])
+        assert np.array_equal(a, b)
+
+
+def _uniform_window_case(code, seed):
+    """24 x 24 LR image with one aperture code everywhere, block (5, 5) whose
+    window (LR rows / cols 3..18) lies inside; w = 1, q = 1, gamma = 1."""
+    y = rng(seed).uniform(0.0, 2.0, (24, 24))
+    mask = np.full((24, 24), code, np.uint8)
+    p = oracle.Params(nu_max=256, gamma_odc=1.0, rho_decay=1.0, q_mode=1, layout=oracle.LAYOUT_APERTURE)
+    F = np.fft.fft2(y[3:19, 3:19])           # F[kap] = sum y exp(-2 pi i (p kap1 + q kap2) / 16)
+    return y, mask, p, F, 5 * 12 + 5
+
+
+def _check_fft_closed_form(hr, tr, F, h):
+    """Quarter sampling (h = 1) and the full aperture: every candidate
+    aliases with k mod 16 and, with w = q = 1, ties with its aliases; the
+    lowest index kap in [0, 16)^2 wins, delta = F[kap] / (256 h(kap)), and
+    after 256 iterations the model is sum_kap F[kap] / (256 h(kap)) Phi_kap."""
+    sel = tr["sel"][0]
+    kap = np.stack([sel // 32, sel % 32], 1)
+    assert np.all(kap < 16)
+    assert sorted((kap[:, 0] * 16 + kap[:, 1]).tolist()) == list(range(256))
+    A = np.abs(F) ** 2
+    k0 = kap[0]
+    assert A[k0[0], k0[1]] >= A.max() * (1 - 1e-12)
+    np.testing.assert_allclose(tr["dc"][0][0], F[k0[0], k0[1]] / (256 * h[k0[0], k0[1]]), rtol=1e-12)
+    c = F / (256 * h)
+    e = np.arange(14, 18)
+    k = np.arange(16)
+    ph = np.exp(2j * np.pi * np.outer(e, k) / 32)            # exp(2 pi i eta kap / 32)
+    model = (ph @ c @ ph.T).real                             # Eq. 18 on the block
+    np.testing.assert_allclose(hr[20:24, 20:24], model, atol=1e-10)
+
+
+@pytest.mark.parametrize("recurrent", [False, True])
+def test_quarter_sampling_reduces_to_fft2(recurrent):
+    y, mask, p, F, b = _uniform_window_case(1, 61)
+    hr, tr = oracle.reconstruct(y, mask, p, blocks=[b], recurrent=recurrent, trace=True)
+    _check_fft_closed_form(hr, tr, F, np.ones((16, 16)))
+    # the model interpolates the measured sub-pixels exactly
+    np.testing.assert_allclose(hr[20:24:2, 20:24:2], y[10:12, 10:12], atol=1e-10)
+
+
+def test_full_aperture_reduces_to_fft2_and_hides_nyquist():
+    y, mask, p, F, b = _uniform_window_case(15, 62)
+    hr, tr = oracle.reconstruct(y, mask, p, blocks=[b], trace=True)
+    k = np.arange(16)
+    e = np.exp(2j * np.pi * k / 32)
+    h = np.outer(1 + e, 1 + e)                               # (1 + w^k1)(1 + w^k2)
+    _check_fft_closed_form(hr, tr, F, h)
+    # the 2x2 box sums of the model reproduce the measurements
+    blk = hr[20:24, 20:24]
+    np.testing.assert_allclose(blk.reshape(2, 2, 2, 2).sum(axis=(1, 3)), y[10:12, 10:12], atol=1e-10)
+
+
+def test_mixed_apertures_direct_equals_recurrent_and_skip_unobservable():
+    W = 16
+    f = synth.image(64, 64, 32, 4, 70)
+    mask = synth.aperture_mask(32, 32, 4, 71, synth.APERTURE_SETS["all"])
+    y = synth.measure(f, mask, 1)
+    p = oracle.Params(window=W, nu_max=40, layout=oracle.LAYOUT_APERTURE)
+    a, ta = oracle.reconstruct(y, mask, p, trace=True)
+    b, tb = oracle.reconstruct(y, mask, p, recurrent=True, trace=True)
+    assert np.array_equal(ta["sel"], tb["sel"])
+    assert np.max(np.abs(a - b)) <= 1e-10
+    # one window of vertical-pair and full apertures: the candidates whose
+    # atom is zero on all measurements (k1 = W/2; dense numpy check) are never
+    # selected, and the residual stays consistent with the model (Eq. 7)
+    codes = synth.aperture_mask(8, 8, 0, 72, (5, 15))
+    pix = aperture_pixels(codes)
+    M = dense_M(pix, W)
+    dead = np.all(np.abs(M) < 1e-9, axis=0)
+    assert dead.sum() > 0
+    ym = rng(73).uniform(0.0, 2.0, len(pix))
+    wm = rng(74).uniform(0.1, 1.0, len(pix))
+    out = oracle.window_solve(pix, wm, ym, oracle.Params(window=W, nu_max=60))
+    assert not dead[out["sel"]].any()
+    model = dense_M([[(e, g)] for e in range(W) for g in range(W)], W) @ out["c"].ravel()
+    re_int = np.array([sum(model[e * W + g].real for e, g in px) for px in pix])
+    np.testing.assert_allclose(out["r"].real, ym - re_int, atol=1e-10)
+    assert np.all(np.diff(out["energy"]) <= 1e-12)
