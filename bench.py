@@ -474,6 +474,48 @@ def run_random_mask(args):
     print(json.dumps(out), flush=True)
 
 
+def run_layouts(args):
+    """The 1024x1024 image behind other sensor layouts (Sec. I): aperture
+    masks tiled with a random 4x4 LR tile, each layout on the recurrent path
+    with host tables; 15 apertures on the direct path (128x128 crop)."""
+    import torch
+    from paper_2205_02646_gb300 import build, rljsde, synth
+    build.build()
+    torch.cuda.set_device(0)
+    f, _, _ = synth.workload("rljsde_1024x1024")
+    out = {"study": "layouts", "workload": "rljsde_1024x1024", "nu_max": args.nu_max, "tile_lr": 4}
+
+    def timed(plan, lr, hr, reps):
+        plan.reconstruct(lr, hr)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.reconstruct(lr, hr)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        plan.check()
+        return best
+
+    for name in ("three_quarter", "quarter", "pairs", "mixed", "all"):
+        mask = synth.aperture_mask(512, 512, 4, 9, synth.APERTURE_SETS[name])
+        y = synth.measure(f, mask, 1).astype(np.float32)
+        if name == "all":
+            mask, y = np.ascontiguousarray(mask[:64, :64]), np.ascontiguousarray(y[:64, :64])
+        plan = rljsde.Plan(mask, rljsde.default_params(nu_max=args.nu_max, layout=1))
+        lr = torch.from_numpy(y).cuda()
+        hr = torch.empty((2 * mask.shape[0], 2 * mask.shape[1]), device="cuda")
+        ms = timed(plan, lr, hr, args.steps if name != "all" else 1)
+        info = plan.info()
+        mp = 4 * mask.size / 1e6
+        out[name] = {"apertures": list(synth.APERTURE_SETS[name]), "path": info["path"],
+                     "mp_per_s": mp / (ms / 1e3), "ms": ms, "hr": [2 * mask.shape[0], 2 * mask.shape[1]],
+                     "tables": info["n_tables"]}
+    print(json.dumps(out), flush=True)
+
+
 def run_learned_launch(args):
     """The learned inference path (whole-image proposal, shortlist loop,
     fallback pass) run twice with a seeded untrained network: the launch
@@ -505,7 +547,8 @@ def main():
     ap.add_argument("--nu-max", type=int, default=100)
     ap.add_argument("--ref-blocks", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "precision", "learned-launch", "random-mask"])
+    ap.add_argument("--study", default=None,
+                    choices=[None, "precision", "learned-launch", "random-mask", "layouts"])
     ap.add_argument("--sample", type=int, default=3072)
     ap.add_argument("--train-images", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=6)
@@ -527,6 +570,9 @@ def main():
         return
     if args.study == "random-mask":
         run_random_mask(args)
+        return
+    if args.study == "layouts":
+        run_layouts(args)
         return
     if args.workload == "rljsde_learned":
         run_learned(args)

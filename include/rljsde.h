@@ -10,6 +10,10 @@
  *     transparent HR sub-pixels of its 2x2 footprint; mask[p][q] in 0..3 names
  *     the opaque one (0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right).
  *     lr_h x lr_w measurements give a (2 lr_h) x (2 lr_w) HR image.
+ *     Sec. I extends the method to any periodically repeating sensor layout:
+ *     with params.layout = RLJSDE_LAYOUT_APERTURE, mask[p][q] in 0..15 is
+ *     instead the set of transparent sub-pixels (bit 2 * dy + dx), e.g.
+ *     quarter sampling (one bit), pairs, or the full 2x2 aperture.
  *   - Sec. III: every B x B = 4 x 4 HR target block is rebuilt from a
  *     W x W = 32 x 32 model window of DFT atoms centred on it; only the
  *     central block is kept.
@@ -42,13 +46,20 @@ typedef enum {
     RLJSDE_OK = 0,
     RLJSDE_ERR_INVALID_ARG = 1,     /* NULL pointer, bad parameter value        */
     RLJSDE_ERR_BAD_SHAPE = 2,       /* lr_h / lr_w not even, or too large        */
-    RLJSDE_ERR_BAD_MASK = 3,        /* a mask code outside 0..3                  */
+    RLJSDE_ERR_BAD_MASK = 3,        /* a mask code outside 0..3 (0..15 apertures) */
     RLJSDE_ERR_OUT_OF_MEMORY = 4,   /* host or device allocation failed          */
     RLJSDE_ERR_CUDA = 5,            /* a CUDA runtime call failed                */
     RLJSDE_ERR_TIMEOUT = 6,         /* a bounded device wait gave up             */
     RLJSDE_ERR_NONFINITE_INPUT = 7, /* NaN/Inf measurement (treated as absent)   */
     RLJSDE_ERR_UNSUPPORTED = 8      /* valid request this build does not offer   */
 } rljsde_status;
+
+/* Meaning of the mask codes (rljsde_params.layout). */
+enum {
+    RLJSDE_LAYOUT_THREE_QUARTER = 0,   /* code 0..3: the one opaque sub-pixel     */
+    RLJSDE_LAYOUT_APERTURE = 1         /* code 0..15: bit 2*dy+dx set = sub-pixel
+                                          (dy, dx) transparent; 0 = no measurement */
+};
 
 /* Reconstruction parameters.  The paper fixes B and W (Sec. III); it names
  * nu_max, gamma_odc, the spatial weight w_m and the frequency weight q but
@@ -73,7 +84,15 @@ typedef struct {
                              (for non-recurrent sensors, FP32 loops only);
                              0 = auto: 3 if precision is 0 and there are more than
                              4096 distinct local matrices, more than a quarter of
-                             the blocks, else 1                                    */
+                             the blocks, else 1.  Aperture layouts: path 1 holds
+                             up to four distinct non-empty apertures per mask;
+                             with more, auto runs path 2 and path 1 is refused
+                             (RLJSDE_ERR_UNSUPPORTED); path 3 and auto's choice
+                             of it need three-quarter apertures               */
+    int layout;           /* RLJSDE_LAYOUT_*: meaning of the mask codes; default
+                             three-quarter.  A candidate whose atom cancels on
+                             every measurement of its window (e.g. the Nyquist
+                             row under full 2x2 apertures) is never selected   */
 } rljsde_params;
 
 /* Fill *p with the defaults above.  Returns RLJSDE_ERR_INVALID_ARG on NULL. */
@@ -84,7 +103,8 @@ typedef struct rljsde_plan rljsde_plan_t;   /* opaque; owns all its device memor
 /*
  * Build a plan for one image size and sensor mask (Sec. IV: "pre-computed and
  * re-used for all model windows with the same measurement matrix").
- *   mask: host, lr_h x lr_w codes 0..3, row-major, contiguous.
+ *   mask: host, lr_h x lr_w codes (0..3, or 0..15 for aperture layouts),
+ *         row-major, contiguous.
  *   lr_h, lr_w: even, 4 .. 32768.
  * Every target block's local measurement matrix (the window's codes, with
  * positions outside the image absent) is classified; tables are built in FP64
@@ -214,7 +234,8 @@ size_t rljsde_propose_workspace(const rljsde_plan_t *plan);
 /* Run the network over the whole image (convolutions, then the head as one
  * BF16 GEMM per chunk of blocks) and write one rljsde_shortlist per block
  * (device, n_blocks entries, block order bi * (2 lr_w / 4) + bj).
- * Asynchronous; the caller owns shortlists and workspace. */
+ * Asynchronous; the caller owns shortlists and workspace.  The network reads
+ * opaque-sub-pixel codes: plans of the three-quarter layout only. */
 int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
                    void *shortlists, void *workspace, size_t workspace_bytes, void *stream);
 /*
@@ -245,7 +266,8 @@ int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, c
  * the greedy loop over its 64 candidates (nu_max iterations, or the
  * network's iteration output if use_nu_hat), every other block the full
  * loop.  sel/dc as for rljsde_reconstruct_trace (unused iterations get
- * 0xFFFF), n_restricted (device int, added to) may be NULL.  FP32 plans. */
+ * 0xFFFF), n_restricted (device int, added to) may be NULL.  FP32 plans of
+ * the three-quarter layout on the recurrent host-table path. */
 int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_t lr_pitch, float *hr,
                                size_t hr_pitch, const void *shortlists, float max_missing, int use_nu_hat,
                                uint16_t *sel, float *dc, int *n_restricted, void *stream);
@@ -261,6 +283,8 @@ typedef struct {
     int64_t paper_B_bytes;        /* Table I equivalent: n_tables x 256 x 1024 x 8 B */
     int64_t paper_C_bytes;        /* n_tables x 1024^2 x 8 B                  */
     int64_t paper_D_bytes;        /* n_tables x 1024 x 8 B                    */
+    int path;                     /* path in effect: 1, 2 or 3 (rljsde_params) */
+    int n_apertures;              /* distinct non-empty apertures in the masks  */
 } rljsde_plan_info_t;
 
 int rljsde_plan_info(const rljsde_plan_t *plan, rljsde_plan_info_t *out);

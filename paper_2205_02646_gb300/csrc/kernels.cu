@@ -141,6 +141,10 @@ struct Args {
     float max_missing;             // restrict a block iff its left-out mass <= this
     int use_nu_hat;                // iterations from the network's output
     int *n_restricted;             // optional count of restricted blocks
+    // sensor layout: aperture code of slot t in bits 4t..4t+3 (MODE 3 loops)
+    // and the meaning of the mask codes (direct path)
+    uint32_t slot_ap;
+    int layout;
     // direct path only
     const uint8_t *masks;
     const long long *mask_offset;
@@ -295,6 +299,12 @@ __device__ __forceinline__ void keep_best(T s, int k, T re, T im, T &bs, int &bk
     if (s > bs) { bs = s; bk = k; bre = re; bim = im; }
 }
 
+// The argmax of Eqs. 10-11 compares scores rounded to binary32 (the precision
+// of the paper's complex64 tables), so the FP64 loop rounds its scores too:
+// candidates whose FP64 scores differ only by rounding tie, and the lowest
+// index wins, as in the FP32 loop.
+template <typename T> __device__ __forceinline__ T key32(T s) { return (T)(float)s; }
+
 // Warp argmax over (score, index), ties to the lowest index.
 template <typename T>
 __device__ __forceinline__ void warp_argmax(T &bs, int &bk)
@@ -309,7 +319,9 @@ __device__ __forceinline__ void warp_argmax(T &bs, int &bk)
 
 // Per-iteration bookkeeping shared by both loops: delta, the update
 // coefficients g_t = gamma delta h_t(uv) and the synthesis of Eq. 18.
-template <typename T>
+// GENERAL selects slot apertures from a.slot_ap instead of the three-quarter
+// ones (slot t = everything but sub-pixel t).
+template <typename T, bool GENERAL = false>
 __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, const T invD, const T gamma,
                                             const int bk, const T Rre, const T Rim, const int eta, const int gam,
                                             const int lane, const long long trow, const int it, int &u, int &v,
@@ -318,13 +330,26 @@ __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, cons
     const C2<T> gd = {gamma * (Rre * invD), gamma * (Rim * invD)};   // gamma * delta (Eqs. 15, 16)
     u = bk >> 5;
     v = bk & 31;
-    // h_t(uv) = P - e_t with P = 1 + w^v + w^u + w^(u+v)
     const C2<T> ev = om[v], eu = om[u], euv = om[(u + v) & 31];
-    const C2<T> P = cadd(cadd(cadd(C2<T>{1, 0}, ev), eu), euv);
-    g[0] = cmul(gd, csub(P, C2<T>{1, 0}));
-    g[1] = cmul(gd, csub(P, ev));
-    g[2] = cmul(gd, csub(P, eu));
-    g[3] = cmul(gd, csub(P, euv));
+    if constexpr (GENERAL) {
+        // h_t(uv) = sum over slot t's sub-pixels s of e_s, e = (1, w^v, w^u, w^(u+v))
+        const C2<T> e[4] = {C2<T>{1, 0}, ev, eu, euv};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            C2<T> h = {0, 0};
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+                if ((a.slot_ap >> (4 * t + sp)) & 1u) h = cadd(h, e[sp]);
+            g[t] = cmul(gd, h);
+        }
+    } else {
+        // h_t(uv) = P - e_t with P = 1 + w^v + w^u + w^(u+v)
+        const C2<T> P = cadd(cadd(cadd(C2<T>{1, 0}, ev), eu), euv);
+        g[0] = cmul(gd, csub(P, C2<T>{1, 0}));
+        g[1] = cmul(gd, csub(P, ev));
+        g[2] = cmul(gd, csub(P, eu));
+        g[3] = cmul(gd, csub(P, euv));
+    }
     const C2<T> ph = om[(eta * u + gam * v) & 31];
     fpix += gd.re * ph.re - gd.im * ph.im;
     if (a.trace_sel != nullptr && lane == 0) {
@@ -335,7 +360,7 @@ __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, cons
 }
 
 // ------------------------------------------------------ FP64 (scalar) loop --
-template <typename T>
+template <typename T, bool GENERAL = false>
 __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec, const C2<T> *om,
                                             const C2<T> *omc, const WorkEntry we, const int lane,
                                             C2<T> (&Y)[8][4])
@@ -364,20 +389,35 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
                 Y[i][2] = csub(Y[i][2], cmul(g[2], C2<T>{G23.x, G23.y}));
                 Y[i][3] = csub(Y[i][3], cmul(g[3], C2<T>{G23.z, G23.w}));
             }
-            // R_k = sum_s conj(e_s(k)) Z_s, Z_s = S - Y_s, e = (1, w^k2, w^k1, w^(k1+k2))
-            const C2<T> S = cadd(cadd(cadd(Y[i][0], Y[i][1]), Y[i][2]), Y[i][3]);
-            const C2<T> Z0 = csub(S, Y[i][0]);
-            const C2<T> U = cmul(e1, csub(S, Y[i][1]));
-            const C2<T> V = cmul(omc[k1], csub(S, Y[i][2]));
-            const C2<T> X = cmul(omc[(k1 + k2) & 31], csub(S, Y[i][3]));
+            // R_k = sum_s conj(e_s(k)) Z_s, e = (1, w^k2, w^k1, w^(k1+k2)), with Z_s the
+            // sum of Y_t over the slots t whose aperture holds sub-pixel s
+            // (three-quarter: Z_s = S - Y_s, S = sum_t Y_t)
+            C2<T> Z[4];
+            if constexpr (GENERAL) {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) {
+                    Z[sp] = {0, 0};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if ((a.slot_ap >> (4 * t + sp)) & 1u) Z[sp] = cadd(Z[sp], Y[i][t]);
+                }
+            } else {
+                const C2<T> S = cadd(cadd(cadd(Y[i][0], Y[i][1]), Y[i][2]), Y[i][3]);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) Z[sp] = csub(S, Y[i][sp]);
+            }
+            const C2<T> Z0 = Z[0];
+            const C2<T> U = cmul(e1, Z[1]);
+            const C2<T> V = cmul(omc[k1], Z[2]);
+            const C2<T> X = cmul(omc[(k1 + k2) & 31], Z[3]);
             const C2<T> pp = cadd(Z0, U), mm = csub(Z0, U), ss = cadd(V, X), dd = csub(V, X);
             const C2<T> R00 = cadd(pp, ss), R01 = cadd(mm, dd), R10 = csub(pp, ss), R11 = csub(mm, dd);
             const Vec4<T> qd = ld4(&rec.qD[k1 * 16 + k2]);
             const int k = k1 * kW + k2;
-            keep_best(qd.x * (R00.re * R00.re + R00.im * R00.im), k, R00.re, R00.im, bs0, bk0, b0re, b0im);
-            keep_best(qd.y * (R01.re * R01.re + R01.im * R01.im), k + 16, R01.re, R01.im, bs0, bk0, b0re, b0im);
-            keep_best(qd.z * (R10.re * R10.re + R10.im * R10.im), k + 512, R10.re, R10.im, bs1, bk1, b1re, b1im);
-            keep_best(qd.w * (R11.re * R11.re + R11.im * R11.im), k + 528, R11.re, R11.im, bs1, bk1, b1re, b1im);
+            keep_best(key32(qd.x * (R00.re * R00.re + R00.im * R00.im)), k, R00.re, R00.im, bs0, bk0, b0re, b0im);
+            keep_best(key32(qd.y * (R01.re * R01.re + R01.im * R01.im)), k + 16, R01.re, R01.im, bs0, bk0, b0re, b0im);
+            keep_best(key32(qd.z * (R10.re * R10.re + R10.im * R10.im)), k + 512, R10.re, R10.im, bs1, bk1, b1re, b1im);
+            keep_best(key32(qd.w * (R11.re * R11.re + R11.im * R11.im)), k + 528, R11.re, R11.im, bs1, bk1, b1re, b1im);
         }
         if (bs1 > bs0) { bs0 = bs1; bk0 = bk1; b0re = b1re; b0im = b1im; }
         T bs = bs0;
@@ -386,7 +426,7 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;    // lane owning kap = (k1 & 15, k2 & 15)
         const T Rre = __shfl_sync(0xffffffffu, b0re, wl);
         const T Rim = __shfl_sync(0xffffffffu, b0im, wl);
-        select_step<T>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
+        select_step<T, GENERAL>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
     }
     if (lane < 16) {
         const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
@@ -431,6 +471,7 @@ __device__ __forceinline__ CP rot(float2 c, float2 s, float2 ns, CP z)
 }
 __device__ __forceinline__ float2 energy(float2 q, CP r) { return mul2(q, fma2(r.im, r.im, mul2(r.re, r.re))); }
 
+template <bool GENERAL = false>
 __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &rec, const C2<float> *om,
                                                 const C2<float> *omc, const PairTables &pt, const WorkEntry we,
                                                 const int lane, C2<float> (&Y0)[8][4])
@@ -476,13 +517,27 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
                     Y[jj][t].im = fma2(Gre, ngim[t], fma2(Gim, ngre[t], Y[jj][t].im));
                 }
             }
-            const CP S = addc(addc(Y[jj][0], Y[jj][1]), addc(Y[jj][2], Y[jj][3]));
-            const CP Z0 = subc(S, Y[jj][0]);
-            const CP U = rot(e1c, e1s, e1n, subc(S, Y[jj][1]));
+            // Z_s = sum of Y_t over the slots holding sub-pixel s (three-quarter: S - Y_s)
+            CP Z[4];
+            if constexpr (GENERAL) {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) {
+                    Z[sp] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if ((a.slot_ap >> (4 * t + sp)) & 1u) Z[sp] = addc(Z[sp], Y[jj][t]);
+                }
+            } else {
+                const CP S = addc(addc(Y[jj][0], Y[jj][1]), addc(Y[jj][2], Y[jj][3]));
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) Z[sp] = subc(S, Y[jj][sp]);
+            }
+            const CP Z0 = Z[0];
+            const CP U = rot(e1c, e1s, e1n, Z[1]);
             const float4 e2 = lds4(&pt.e2[4 * h + jj]);
-            const CP V = rot(f2(e2.x, e2.y), f2(e2.z, e2.w), lds2(&pt.e2n[4 * h + jj]), subc(S, Y[jj][2]));
+            const CP V = rot(f2(e2.x, e2.y), f2(e2.z, e2.w), lds2(&pt.e2n[4 * h + jj]), Z[2]);
             const float4 e12 = lds4(&pt.e12[k1 + k2]);
-            const CP X = rot(f2(e12.x, e12.y), f2(e12.z, e12.w), lds2(&pt.e12n[k1 + k2]), subc(S, Y[jj][3]));
+            const CP X = rot(f2(e12.x, e12.y), f2(e12.z, e12.w), lds2(&pt.e12n[k1 + k2]), Z[3]);
             const CP pp = addc(Z0, U), mm = subc(Z0, U), ss = addc(V, X), dd = subc(V, X);
             const CP R00 = addc(pp, ss), R01 = addc(mm, dd), R10 = subc(pp, ss), R11 = subc(mm, dd);
             const float4 q0 = lds4(rec.qDP[4 * h + jj][0][k2]);
@@ -506,7 +561,8 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;
         const float Rre = __shfl_sync(0xffffffffu, b0re, wl);
         const float Rim = __shfl_sync(0xffffffffu, b0im, wl);
-        select_step<float>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
+        select_step<float, GENERAL>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g,
+                                    fpix);
     }
     if (lane < 16) {
         const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
@@ -702,7 +758,8 @@ __device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortli
 // blocks whose left-out mass is <= max_missing, other blocks untouched;
 // 2 = full loop on the other blocks only.  Modes 1 and 2 together cover
 // every block once; each is its own instantiation, so the register budget
-// of one does not constrain the other.
+// of one does not constrain the other.  3 = mode 0 for sensor layouts
+// other than three-quarter sampling (slot apertures from a.slot_ap).
 template <typename T, int MODE> struct Loop;
 template <int MODE> struct Loop<float, MODE> {
     using Rec = typename RecOf<float, MODE>::type;
@@ -710,10 +767,10 @@ template <int MODE> struct Loop<float, MODE> {
                                                const C2<float> *om, const C2<float> *omc, const PairTables &pt,
                                                const float *wt, const WorkEntry we, const int lane)
     {
-        if constexpr (MODE == 0) {
+        if constexpr (MODE == 0 || MODE == 3) {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
+            greedy_loop_f32<MODE == 3>(a, rec, om, omc, pt, we, lane, Y);
         } else if constexpr (MODE == 1) {
             const Shortlist &sl = a.shortlists[we.ord];
             if (!(sl.missing <= a.max_missing)) return;
@@ -727,7 +784,7 @@ template <int MODE> struct Loop<float, MODE> {
             if (sl.missing <= a.max_missing) return;
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            greedy_loop_f32(a, rec, om, omc, pt, we, lane, Y);
+            greedy_loop_f32<false>(a, rec, om, omc, pt, we, lane, Y);
         }
     }
 
@@ -759,7 +816,7 @@ template <int MODE> struct Loop<double, MODE> {
     {
         C2<double> Y[8][4];
         initial_projection<double>(a, rec, scratch, omc, wt, we, lane, Y);
-        greedy_loop<double>(a, rec, om, omc, we, lane, Y);
+        greedy_loop<double, MODE == 3>(a, rec, om, omc, we, lane, Y);
     }
     static __device__ __forceinline__ void run_pair(const Args &a, const Record<double> &rec, C2<double> *scratch,
                                                     const C2<double> *om, const C2<double> *omc,
@@ -1000,7 +1057,7 @@ __global__ void __launch_bounds__(kFlyWarps * 32, 2) onthefly_kernel(const Args 
 #pragma unroll
                 for (int B = 0; B < 2; ++B) rec.invD[(8 * h + i + 16 * A) * kW + k2 + 16 * B] = invd[i][2 * A + B];
         __syncwarp();
-        greedy_loop_f32(a, rec, om, omc, *pt, we, lane, Y);
+        greedy_loop_f32<false>(a, rec, om, omc, *pt, we, lane, Y);
     }
 }
 
@@ -1008,11 +1065,14 @@ __global__ void __launch_bounds__(kFlyWarps * 32, 2) onthefly_kernel(const Args 
 // Direct L-JSDE (Eqs. 4-10): per block the residual r (256 complex, in the
 // warp's scratch) and, every iteration, N_k = sum_m conj(a_m(k)) w_m r_m for
 // all 1024 k with a_m(k) evaluated from the roots-of-unity table (O(W^4)).
+// Any per-pixel aperture: a_m(k) sums the phases of m's transparent
+// sub-pixels; a candidate whose phase sum cancels exactly for every aperture
+// in the window is not observed by any measurement and scores 0.
 constexpr int kDirectWarps = 4;
 struct DirectSmem {
     float2 r[kDirectWarps][256];
     float wr[kDirectWarps][256][2];
-    uint8_t type[kDirectWarps][256];
+    uint8_t type[kDirectWarps][256];     // aperture code, 0 = no measurement
     float2 om[32];
     float w[256];
 };
@@ -1032,26 +1092,32 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
         const uint8_t *mask = a.masks + a.mask_offset[we.img];
         const int p0 = 2 * we.bi - kOff / 2, q0 = 2 * we.bj - kOff / 2;
         bool bad = false;
+        uint32_t present = 0;                // bit a: aperture a occurs in the window
         for (int m = lane; m < 256; m += 32) {
             const int p = m >> 4, q = m & 15, P = p0 + p, Q = q0 + q;
-            uint8_t t = 255;
+            int t = 0;
             float y = 0.f;
             if (P >= 0 && P < img.lr_h && Q >= 0 && Q < img.lr_w) {
-                t = mask[(long long)P * img.lr_w + Q];
-                y = img.lr[(long long)P * img.lr_pitch + Q];
-                if (!isfinite(y)) { bad = true; y = 0.f; }
+                const int code = mask[(long long)P * img.lr_w + Q];
+                t = a.layout == RLJSDE_LAYOUT_APERTURE ? code & 15 : 15 ^ (1 << (code & 3));
+                if (t != 0) {
+                    y = img.lr[(long long)P * img.lr_pitch + Q];
+                    if (!isfinite(y)) { bad = true; y = 0.f; }
+                }
             }
-            sm.type[warp][m] = t;
-            sm.r[warp][m] = make_float2(t < 4 ? y : 0.f, 0.f);
+            present |= 1u << t;
+            sm.type[warp][m] = (uint8_t)t;
+            sm.r[warp][m] = make_float2(y, 0.f);
         }
         if (bad) atomicOr(a.status, kStatusNonfinite);
+        present = __reduce_or_sync(0xffffffffu, present) & ~1u;
         __syncwarp();
         // D_k = sum_m w_m |a_m(k)|^2 for this lane's 32 candidates k = lane + 32 j
         float D[32];
         for (int j = 0; j < 32; ++j) D[j] = 0.f;
         for (int m = 0; m < 256; ++m) {
             const int t = sm.type[warp][m];
-            if (t > 3) continue;
+            if (t == 0) continue;
             const int p = m >> 4, q = m & 15;
             const float wm = sm.w[m];
 #pragma unroll
@@ -1060,7 +1126,7 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
                 float are = 0.f, aim = 0.f;
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
-                    if (s == t) continue;
+                    if (!((t >> s) & 1)) continue;
                     const float2 z = sm.om[((2 * p + (s >> 1)) * k1 + (2 * q + (s & 1)) * k2) & 31];
                     are += z.x;
                     aim += z.y;
@@ -1068,12 +1134,16 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
                 D[j] += wm * (are * are + aim * aim);
             }
         }
+        // candidates no aperture of the window observes
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if ((present & ~(uint32_t)a.consts->vanish[j * kW + lane]) == 0) D[j] = 0.f;
         float fpix = 0.f;
         const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
         const long long trow = (long long)we.ord * a.nu_max;
         for (int it = 0; it < a.nu_max; ++it) {
             for (int m = lane; m < 256; m += 32) {
-                const float wm = sm.type[warp][m] < 4 ? sm.w[m] : 0.f;
+                const float wm = sm.type[warp][m] != 0 ? sm.w[m] : 0.f;
                 sm.wr[warp][m][0] = wm * sm.r[warp][m].x;
                 sm.wr[warp][m][1] = wm * sm.r[warp][m].y;
             }
@@ -1082,7 +1152,7 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
             for (int j = 0; j < 32; ++j) Nre[j] = Nim[j] = 0.f;
             for (int m = 0; m < 256; ++m) {
                 const int t = sm.type[warp][m];
-                if (t > 3) continue;
+                if (t == 0) continue;
                 const int p = m >> 4, q = m & 15;
                 const float xr = sm.wr[warp][m][0], xi = sm.wr[warp][m][1];
 #pragma unroll
@@ -1090,7 +1160,7 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
                     float are = 0.f, aim = 0.f;
 #pragma unroll
                     for (int s = 0; s < 4; ++s) {
-                        if (s == t) continue;
+                        if (!((t >> s) & 1)) continue;
                         const float2 z = sm.om[((2 * p + (s >> 1)) * j + (2 * q + (s & 1)) * lane) & 31];
                         are += z.x;
                         aim += z.y;
@@ -1107,7 +1177,12 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
             for (int j = 0; j < 32; ++j) {
                 const int k = j * kW + lane;
                 const float s = D[j] > 0.f ? a.q[k] * (Nre[j] * Nre[j] + Nim[j] * Nim[j]) / D[j] : 0.f;
-                if (s > bs) { bs = s; bk = k; bre = Nre[j] / D[j]; bim = Nim[j] / D[j]; }
+                if (s > bs) {
+                    bs = s;
+                    bk = k;
+                    bre = D[j] > 0.f ? Nre[j] / D[j] : 0.f;
+                    bim = D[j] > 0.f ? Nim[j] / D[j] : 0.f;
+                }
             }
 #pragma unroll
             for (int m = 16; m >= 1; m >>= 1) {
@@ -1122,11 +1197,11 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
             // r_m -= gamma delta a_m(uv)   (Eq. 7)
             for (int m = lane; m < 256; m += 32) {
                 const int t = sm.type[warp][m];
-                if (t > 3) continue;
+                if (t == 0) continue;
                 const int p = m >> 4, q = m & 15;
                 float are = 0.f, aim = 0.f;
                 for (int s = 0; s < 4; ++s) {
-                    if (s == t) continue;
+                    if (!((t >> s) & 1)) continue;
                     const float2 z = sm.om[((2 * p + (s >> 1)) * u + (2 * q + (s & 1)) * v) & 31];
                     are += z.x;
                     aim += z.y;
@@ -1167,6 +1242,7 @@ const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 0), RLJSDE_VARIANT(float, 4, 4, 0), RLJSDE_VARIANT(float, 8, 2, 0),
     RLJSDE_VARIANT(float, 8, 1, 0), RLJSDE_VARIANT(double, 4, 1, 0), RLJSDE_VARIANT(double, 8, 1, 0),
     RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 3, 2),
+    RLJSDE_VARIANT(float, 4, 3, 3), RLJSDE_VARIANT(float, 8, 2, 3), RLJSDE_VARIANT(double, 4, 1, 3),
 };
 #undef RLJSDE_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -1197,6 +1273,8 @@ Args make_args(const rljsde_plan *p)
     a.masks = p->d_masks;
     a.mask_offset = p->d_mask_offset;
     a.q = p->d_qD;
+    a.slot_ap = p->slot_ap;
+    a.layout = p->params.layout;
     return a;
 }
 
@@ -1263,13 +1341,14 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
     // Default: 4 warps per CTA, as many CTAs as the 168-register variant fits.
     if (warps == 0) { warps = 4; if (ctas_per_sm == 0) ctas_per_sm = 3; }
     const int fp64 = p->params.precision == 1;
+    const int mode = p->kind == 1 ? 3 : 0;
     // The variant with this precision and warp count whose register budget
     // admits the requested CTAs per SM (the largest one not above it).
     int best = -1, best_occ = 0;
     for (int pass = 0; pass < 2 && best < 0; ++pass)    // second pass: smallest budget above the request
         for (int i = 0; i < kNumVariants; ++i) {
             const Variant &v = kVariants[i];
-                if (v.fp64 != fp64 || v.warps != warps || v.mode != 0) continue;
+            if (v.fp64 != fp64 || v.warps != warps || v.mode != mode) continue;
             if (pass == 0 && ctas_per_sm > 0 && v.minb > ctas_per_sm) continue;
             const int occ = occupancy(v);
             if (occ < 0) return RLJSDE_ERR_CUDA;
@@ -1318,7 +1397,8 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
                                uint16_t *sel, float *dc, int *n_restricted, void *stream)
 {
     if (!plan || !lr || !hr || !shortlists) return RLJSDE_ERR_INVALID_ARG;
-    if (plan->n_images != 1 || plan->direct || plan->onthefly || plan->params.precision != 0)
+    if (plan->n_images != 1 || plan->direct || plan->onthefly || plan->params.precision != 0 || plan->kind != 0 ||
+        plan->params.layout != RLJSDE_LAYOUT_THREE_QUARTER)
         return RLJSDE_ERR_UNSUPPORTED;
     if (lr_pitch < (size_t)plan->lr_w[0] || hr_pitch < (size_t)(2 * plan->lr_w[0])) return RLJSDE_ERR_INVALID_ARG;
     if ((sel == nullptr) != (dc == nullptr)) return RLJSDE_ERR_INVALID_ARG;

@@ -58,15 +58,35 @@ void frequency_weight(const rljsde_params &p, std::vector<double> &q)
         }
 }
 
-// The window's codes: opaque quadrant per L-pixel, 255 outside the image.
-void window_key(const uint8_t *mask, int lr_h, int lr_w, int bi, int bj, uint8_t *key)
+// Aperture (set of transparent sub-pixels, bit 2 * dy + dx) of a mask code.
+inline int aperture_of(int layout, int code) { return layout == RLJSDE_LAYOUT_APERTURE ? code : 15 ^ (1 << code); }
+
+// Exact test that h(k) = sum over the aperture's sub-pixels (dy, dx) of
+// w32^(dy k1 + dx k2) is zero: w32's minimal polynomial is x^16 + 1, so
+// w32^0..w32^15 are independent over the rationals and a sum of powers with
+// integer counts c_n vanishes iff c_n = c_(n+16) for every n < 16.
+bool aperture_vanishes(int ap, int k1, int k2)
+{
+    int c[32] = {0};
+    for (int s = 0; s < 4; ++s)
+        if ((ap >> s) & 1) ++c[((s >> 1) * k1 + (s & 1) * k2) & 31];
+    for (int n = 0; n < 16; ++n)
+        if (c[n] != c[n + 16]) return false;
+    return true;
+}
+
+// The window's key: aperture slot per L-pixel, 255 outside the image or
+// where the aperture is empty.
+void window_key(const uint8_t *mask, int lr_h, int lr_w, int bi, int bj, const uint8_t *slot_of_code,
+                uint8_t *key)
 {
     int p0 = 2 * bi - kOff / 2, q0 = 2 * bj - kOff / 2;
     for (int p = 0; p < kL; ++p) {
         int P = p0 + p;
         for (int q = 0; q < kL; ++q) {
             int Q = q0 + q;
-            key[p * kL + q] = (P < 0 || P >= lr_h || Q < 0 || Q >= lr_w) ? 255 : mask[(size_t)P * lr_w + Q];
+            key[p * kL + q] =
+                (P < 0 || P >= lr_h || Q < 0 || Q >= lr_w) ? 255 : slot_of_code[mask[(size_t)P * lr_w + Q]];
         }
     }
 }
@@ -74,13 +94,17 @@ void window_key(const uint8_t *mask, int lr_h, int lr_w, int bi, int bj, uint8_t
 // FP64 factored tables of one local measurement matrix:
 //   G_t(d) = sum_{m: t(m) = t} w_m w16^(p d1 + q d2),  w16^n = w32^(2n),
 //   D_k    = sum_t |h_t(k)|^2 G_t(0)  (= C_{k,k}, Eq. 13),
-//   h_t(k) = sum over the three transparent offsets of w32^(e k1 + g k2).
+//   h_t(k) = sum over the transparent offsets (e, g) of slot t's aperture
+//            (bits 4t..4t+3 of slot_ap) of w32^(e k1 + g k2).
+// A candidate whose h_t vanishes exactly for every slot present in the
+// window has no measurement that sees it: D_k is set to 0 (score 0) rather
+// than left at the rounding residue of a cancelled sum.
 struct Tables {
     double Gre[4][256], Gim[4][256];
     double D[kK];
 };
 
-void build_tables(const uint8_t *key, const double *w, const Cd *r32, Tables &T)
+void build_tables(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap, Tables &T)
 {
     for (int t = 0; t < 4; ++t)
         for (int d = 0; d < 256; ++d) T.Gre[t][d] = T.Gim[t][d] = 0.0;
@@ -99,28 +123,31 @@ void build_tables(const uint8_t *key, const double *w, const Cd *r32, Tables &T)
     for (int k1 = 0; k1 < kW; ++k1)
         for (int k2 = 0; k2 < kW; ++k2) {
             double dk = 0.0;
+            bool seen = false;
             for (int t = 0; t < 4; ++t) {
+                const int ap = (slot_ap >> (4 * t)) & 15;
                 double hre = 0.0, him = 0.0;
                 for (int e = 0; e < 2; ++e)
                     for (int g = 0; g < 2; ++g) {
-                        if (2 * e + g == t) continue;
+                        if (!((ap >> (2 * e + g)) & 1)) continue;
                         const Cd &z = r32[(e * k1 + g * k2) & 31];
                         hre += z.re;
                         him += z.im;
                     }
                 dk += (hre * hre + him * him) * T.Gre[t][0];
+                if (T.Gre[t][0] > 0.0 && !aperture_vanishes(ap, k1, k2)) seen = true;
             }
-            T.D[k1 * kW + k2] = dk;
+            T.D[k1 * kW + k2] = seen ? dk : 0.0;
         }
 }
 
 inline double inv_or_zero(double num, double den) { return den > 1e-300 ? num / den : 0.0; }
 
-void build_record64(const uint8_t *key, const double *w, const Cd *r32, const std::vector<double> &q,
-                    Record<double> *rec)
+void build_record64(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap,
+                    const std::vector<double> &q, Record<double> *rec)
 {
     static thread_local Tables T;
-    build_tables(key, w, r32, T);
+    build_tables(key, w, r32, slot_ap, T);
     for (int d = 0; d < 256; ++d) {
         rec->G01[d] = {T.Gre[0][d], T.Gim[0][d], T.Gre[1][d], T.Gim[1][d]};
         rec->G23[d] = {T.Gre[2][d], T.Gim[2][d], T.Gre[3][d], T.Gim[3][d]};
@@ -139,11 +166,11 @@ void build_record64(const uint8_t *key, const double *w, const Cd *r32, const st
     std::memcpy(rec->types, key, 256);
 }
 
-void build_record32(const uint8_t *key, const double *w, const Cd *r32, const std::vector<double> &q,
-                    RecordF32 *rec, RecordShortF32 *sh)
+void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap,
+                    const std::vector<double> &q, RecordF32 *rec, RecordShortF32 *sh)
 {
     static thread_local Tables T;
-    build_tables(key, w, r32, T);
+    build_tables(key, w, r32, slot_ap, T);
     for (int d = 0; d < 256; ++d) {
         float *a = sh->G01[d], *b = sh->G23[d];
         a[0] = (float)T.Gre[0][d]; a[1] = (float)T.Gim[0][d]; a[2] = (float)T.Gre[1][d]; a[3] = (float)T.Gim[1][d];
@@ -209,6 +236,8 @@ int check_params(const rljsde_params *p)
             if (!(p->q_table[k] >= 0.0) || !std::isfinite(p->q_table[k])) return RLJSDE_ERR_INVALID_ARG;
     if (p->precision != 0 && p->precision != 1) return RLJSDE_ERR_INVALID_ARG;
     if (p->path < 0 || p->path > 3) return RLJSDE_ERR_INVALID_ARG;
+    if (p->layout != RLJSDE_LAYOUT_THREE_QUARTER && p->layout != RLJSDE_LAYOUT_APERTURE)
+        return RLJSDE_ERR_INVALID_ARG;
     if ((p->path == 2 || p->path == 3) && p->precision != 0) return RLJSDE_ERR_UNSUPPORTED;
     return RLJSDE_OK;
 }
@@ -240,15 +269,51 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     if (st) return st;
     if (n_images < 1 || !masks || !lr_h || !lr_w) return RLJSDE_ERR_INVALID_ARG;
     long long total_blocks = 0;
+    const int max_code = prm->layout == RLJSDE_LAYOUT_APERTURE ? 15 : 3;
+    uint32_t present = 0;                       // bit a: aperture a occurs
     for (int i = 0; i < n_images; ++i) {
         if (!masks[i]) return RLJSDE_ERR_INVALID_ARG;
         if (lr_h[i] < 4 || lr_w[i] < 4 || lr_h[i] > 32768 || lr_w[i] > 32768 || (lr_h[i] & 1) || (lr_w[i] & 1))
             return RLJSDE_ERR_BAD_SHAPE;
-        for (size_t j = 0; j < (size_t)lr_h[i] * lr_w[i]; ++j)
-            if (masks[i][j] > 3) return RLJSDE_ERR_BAD_MASK;
+        uint32_t seen = 0;
+        for (size_t j = 0; j < (size_t)lr_h[i] * lr_w[i]; ++j) {
+            if (masks[i][j] > max_code) return RLJSDE_ERR_BAD_MASK;
+            seen |= 1u << masks[i][j];
+        }
+        for (int c = 0; c <= max_code; ++c)
+            if ((seen >> c) & 1) present |= 1u << aperture_of(prm->layout, c);
         total_blocks += (long long)(lr_h[i] / 2) * (lr_w[i] / 2);
     }
     if (total_blocks > (1ll << 30)) return RLJSDE_ERR_BAD_SHAPE;
+
+    // Aperture slots of the factored tables (Sec. I layouts).  Three-quarter
+    // apertures keep slot t = opaque quadrant t; up to four other apertures
+    // take slots in increasing code order; more need the direct path.
+    present &= ~1u;                             // an empty aperture measures nothing
+    int n_ap = 0;
+    for (int a = 1; a < 16; ++a) n_ap += (present >> a) & 1;
+    const uint32_t tq = (1u << 14) | (1u << 13) | (1u << 11) | (1u << 7);
+    int kind;
+    uint32_t slot_ap = 0;
+    uint8_t slot_of_ap[16];
+    std::memset(slot_of_ap, 255, sizeof(slot_of_ap));
+    if ((present & ~tq) == 0) {
+        kind = 0;
+        for (int t = 0; t < 4; ++t) { slot_of_ap[15 ^ (1 << t)] = (uint8_t)t; slot_ap |= (uint32_t)(15 ^ (1 << t)) << (4 * t); }
+    } else if (n_ap <= 4) {
+        kind = 1;
+        int t = 0;
+        for (int a = 1; a < 16; ++a)
+            if ((present >> a) & 1) { slot_of_ap[a] = (uint8_t)t; slot_ap |= (uint32_t)a << (4 * t); ++t; }
+    } else {
+        kind = 2;
+    }
+    if (kind == 2 && (prm->path == 1 || prm->path == 3)) return RLJSDE_ERR_UNSUPPORTED;
+    if (kind == 2 && prm->precision != 0) return RLJSDE_ERR_UNSUPPORTED;
+    if (kind != 0 && prm->path == 3) return RLJSDE_ERR_UNSUPPORTED;
+    uint8_t slot_of_code[256];
+    std::memset(slot_of_code, 255, sizeof(slot_of_code));
+    for (int c = 0; c <= max_code; ++c) slot_of_code[c] = slot_of_ap[aperture_of(prm->layout, c)];
 
     rljsde_plan *p = new (std::nothrow) rljsde_plan();
     if (!p) return RLJSDE_ERR_OUT_OF_MEMORY;
@@ -257,7 +322,10 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     p->n_images = n_images;
     p->lr_h.assign(lr_h, lr_h + n_images);
     p->lr_w.assign(lr_w, lr_w + n_images);
-    p->direct = prm->path == 2;
+    p->direct = prm->path == 2 || kind == 2;
+    p->kind = kind;
+    p->slot_ap = slot_ap;
+    p->n_apertures = n_ap;
     frequency_weight(*prm, p->q);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
@@ -292,7 +360,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             int nbh = lr_h[i] / 2, nbw = lr_w[i] / 2;
             for (int bi = 0; bi < nbh; ++bi)
                 for (int bj = 0; bj < nbw; ++bj) {
-                    window_key(masks[i], lr_h[i], lr_w[i], bi, bj, (uint8_t *)&key[0]);
+                    window_key(masks[i], lr_h[i], lr_w[i], bi, bj, slot_of_code, (uint8_t *)&key[0]);
                     auto it = ids.find(key);
                     int id;
                     if (it == ids.end()) {
@@ -313,8 +381,8 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         // Mostly unique windows (a non-recurrent sensor): build each block's
         // tables in the kernel instead of one host table set per block.
         // (Small images keep host tables: their build is cheap.)
-        p->onthefly = prm->path == 3 ||
-                      (prm->path == 0 && prm->precision == 0 && 4ll * p->n_tables > ord && p->n_tables > 4096);
+        p->onthefly = prm->path == 3 || (prm->path == 0 && prm->precision == 0 && kind == 0 &&
+                                         4ll * p->n_tables > ord && p->n_tables > 4096);
         if (p->onthefly)
             for (auto &t : table_of) t = 0;
     } else {
@@ -355,6 +423,12 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             c.om64[2 * n] = r32[n].re;
             c.om64[2 * n + 1] = r32[n].im;
         }
+        for (int k = 0; k < kK; ++k) {
+            uint16_t v = 0;
+            for (int a = 1; a < 16; ++a)
+                if (aperture_vanishes(a, k / kW, k % kW)) v |= (uint16_t)(1u << a);
+            c.vanish[k] = v;
+        }
         st = upload(&p->d_consts, &c, sizeof(c));
     }
     if (!st && (cudaMalloc((void **)&p->d_status, sizeof(int)) != cudaSuccess ||
@@ -380,9 +454,10 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             for (int t = 0; t < p->n_tables; ++t) {
                 const uint8_t *key = (const uint8_t *)keys[t].data();
                 if (prm->precision)
-                    build_record64(key, w64, r32, p->q, (Record<double> *)(host.data() + p->record_bytes * t));
+                    build_record64(key, w64, r32, slot_ap, p->q,
+                                   (Record<double> *)(host.data() + p->record_bytes * t));
                 else
-                    build_record32(key, w64, r32, p->q, (RecordF32 *)(host.data() + p->record_bytes * t),
+                    build_record32(key, w64, r32, slot_ap, p->q, (RecordF32 *)(host.data() + p->record_bytes * t),
                                    (RecordShortF32 *)(host_short.data() + sizeof(RecordShortF32) * t));
             }
             st = upload(&p->d_records, host.data(), host.size());
@@ -431,6 +506,7 @@ int rljsde_default_params(rljsde_params *p)
     p->q_table = nullptr;
     p->precision = 0;
     p->path = 0;
+    p->layout = RLJSDE_LAYOUT_THREE_QUARTER;
     return RLJSDE_OK;
 }
 
@@ -476,6 +552,8 @@ int rljsde_plan_info(const rljsde_plan_t *p, rljsde_plan_info_t *out)
     out->paper_B_bytes = (int64_t)p->n_tables * 256 * kK * 8;
     out->paper_C_bytes = (int64_t)p->n_tables * kK * kK * 8;
     out->paper_D_bytes = (int64_t)p->n_tables * kK * 8;
+    out->path = p->direct ? 2 : p->onthefly ? 3 : 1;
+    out->n_apertures = p->n_apertures;
     return RLJSDE_OK;
 }
 

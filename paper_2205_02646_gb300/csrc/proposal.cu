@@ -800,6 +800,7 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
 {
     if (!plan || !net || !lr || !shortlists || !workspace) return RLJSDE_ERR_INVALID_ARG;
     if (plan->n_images != 1 || lr_pitch < (size_t)plan->lr_w[0]) return RLJSDE_ERR_INVALID_ARG;
+    if (plan->params.layout != RLJSDE_LAYOUT_THREE_QUARTER) return RLJSDE_ERR_UNSUPPORTED;   // opaque-code input
     if (ws_bytes < rljsde_propose_workspace(plan)) return RLJSDE_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int lr_h = plan->lr_h[0], lr_w = plan->lr_w[0], nbh = lr_h / 2, nbw = lr_w / 2;
@@ -846,6 +847,7 @@ int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, c
 {
     if (!plan || !net || !lr || !shortlists) return RLJSDE_ERR_INVALID_ARG;
     if (plan->n_images != 1 || lr_pitch < (size_t)plan->lr_w[0]) return RLJSDE_ERR_INVALID_ARG;
+    if (plan->params.layout != RLJSDE_LAYOUT_THREE_QUARTER) return RLJSDE_ERR_UNSUPPORTED;   // opaque-code input
     const int lr_h = plan->lr_h[0], lr_w = plan->lr_w[0], nbh = lr_h / 2, nbw = lr_w / 2;
     const size_t P = (size_t)lr_h * lr_w, nb = (size_t)plan->n_blocks;
     const size_t chunk = nb < (size_t)kStaticChunk ? nb : (size_t)kStaticChunk;

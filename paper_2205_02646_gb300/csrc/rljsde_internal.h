@@ -31,12 +31,15 @@ struct WorkEntry {
 };
 
 // Plan-independent constants: spatial weights w(p, q) of the window's
-// L-pixels and exp(2 pi i n / 32), each in FP32 and FP64.
+// L-pixels and exp(2 pi i n / 32), each in FP32 and FP64; per candidate k,
+// the apertures whose sub-pixel phase sum h(k) is exactly zero (bit a set:
+// aperture code a, sub-pixel bit 2 * dy + dx).
 struct Consts {
     float w32[256];
     float om32[64];     // (re, im) for n = 0..31
     double w64[256];
     double om64[64];
+    uint16_t vanish[kK];
 };
 
 template <typename T>
@@ -46,10 +49,11 @@ struct alignas(16) Vec4 {
 
 // Tables of one local measurement matrix in the factored form.
 //
-// With t(m) the opaque quadrant of L-pixel m at window LR position (p, q),
-// the integrated atom of Eq. 4 factors as
+// With t(m) the aperture type (slot 0..3) of L-pixel m at window LR position
+// (p, q) -- for three-quarter sampling, its opaque quadrant -- the integrated
+// atom of Eq. 4 factors as
 //     a_m(k) = w32^(2 p k1 + 2 q k2) h_t(k),
-//     h_t(k) = sum over the three transparent offsets (e, g) of w32^(e k1 + g k2),
+//     h_t(k) = sum over the transparent offsets (e, g) of type t of w32^(e k1 + g k2),
 // so the Gram matrix of Eq. 14 is
 //     C_{k,l} = sum_t conj(h_t(k)) h_t(l) G_t((l - k) mod 16),
 //     G_t(d) = sum_{m: t(m) = t} w_m w16^(p d1 + q d2),
@@ -60,7 +64,7 @@ struct Record {
     Vec4<T> G23[256];     // (G_2(d), G_3(d))
     Vec4<T> qD[256];      // q_k / D_k at k = (kap1 + 16a, kap2 + 16b), entry 2a + b
     T invD[kK];           // 1 / D_k, k = k1 * 32 + k2
-    uint8_t types[256];   // opaque code per window L-pixel (p * 16 + q), 255 = absent
+    uint8_t types[256];   // aperture slot per window L-pixel (p * 16 + q), 255 = absent
 };
 static_assert(sizeof(Record<double>) % 16 == 0, "record size must allow bulk copies");
 
@@ -115,6 +119,10 @@ struct rljsde_plan {
     int n_entries = 0, n_chunks = 0;
     int direct = 0;                   // path == 2
     int onthefly = 0;                 // tables built per block in the kernel (path 3, or auto)
+    int kind = 0;                     // 0: three-quarter apertures (slot t = opaque quadrant t);
+                                      // 1: up to four other apertures; 2: more (direct path only)
+    uint32_t slot_ap = 0;             // aperture code of slot t in bits 4t..4t+3
+    int n_apertures = 0;              // distinct non-empty apertures in the masks
     int device = 0, sm_count = 0;
     int warps = 4, ctas_per_sm = 0, grid = 0, variant = 0;
     int learned_warps = 4;            // warps per CTA of the shortlist-loop kernel (4: two blocks per warp)

@@ -28,11 +28,15 @@ class RljsdeError(RuntimeError):
 
 class Params(ctypes.Structure):
     """``rljsde_params``: B, W, nu_max, gamma_odc, rho_decay, q_mode, q_table,
-    precision, path (see the header for meanings and defaults)."""
+    precision, path, layout (see the header for meanings and defaults)."""
     _fields_ = [("block", ctypes.c_int), ("window", ctypes.c_int), ("nu_max", ctypes.c_int),
                 ("gamma_odc", ctypes.c_double), ("rho_decay", ctypes.c_double),
                 ("q_mode", ctypes.c_int), ("q_table", ctypes.POINTER(ctypes.c_double)),
-                ("precision", ctypes.c_int), ("path", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("path", ctypes.c_int), ("layout", ctypes.c_int)]
+
+
+LAYOUT_THREE_QUARTER = 0   # mask code = opaque sub-pixel 2 * dy + dx
+LAYOUT_APERTURE = 1        # mask code = bit set of transparent sub-pixels
 
 
 class PlanInfo(ctypes.Structure):
@@ -40,7 +44,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_interior_tables", ctypes.c_int), ("n_work_entries", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("grid", ctypes.c_int),
                 ("device_table_bytes", ctypes.c_int64), ("paper_B_bytes", ctypes.c_int64),
-                ("paper_C_bytes", ctypes.c_int64), ("paper_D_bytes", ctypes.c_int64)]
+                ("paper_C_bytes", ctypes.c_int64), ("paper_D_bytes", ctypes.c_int64),
+                ("path", ctypes.c_int), ("n_apertures", ctypes.c_int)]
 
 
 class Image(ctypes.Structure):

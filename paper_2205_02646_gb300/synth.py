@@ -49,7 +49,11 @@ APERTURE_SETS = {
     "three_quarter": (14, 13, 11, 7),
     "quarter": (1, 2, 4, 8),
     "pairs": (3, 12, 5, 10),            # horizontal and vertical sub-pixel pairs
-    "mixed": (1, 6, 14, 15),            # quarter, diagonal pair, three-quarter, full
+    "mixed": (1, 6, 13, 15),            # quarter, diagonal pair, three-quarter, full
+    # every aperture symmetric under transposition: the atoms of (k1, k2) and
+    # (k2, k1) coincide on every measurement when k1 - k2 = 16 (mod 32), so
+    # those candidates tie exactly and only the tie rule separates them
+    "symmetric": (1, 6, 14, 15),
     "all": tuple(range(1, 16)),         # every non-empty aperture
 }
 

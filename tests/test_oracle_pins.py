@@ -439,3 +439,18 @@ def test_mixed_apertures_direct_equals_recurrent_and_skip_unobservable():
     re_int = np.array([sum(model[e * W + g].real for e, g in px) for px in pix])
     np.testing.assert_allclose(out["r"].real, ym - re_int, atol=1e-10)
     assert np.all(np.diff(out["energy"]) <= 1e-12)
+
+
+def test_transpose_symmetric_apertures_make_identical_atoms():
+    """Apertures symmetric under transposition see candidates (k1, k2) and
+    (k2, k1) with k1 - k2 = 16 through identical atoms (dense numpy check);
+    the oracle then meets exact ties, which it breaks to the lower index."""
+    W = 32
+    codes = synth.aperture_mask(16, 16, 4, 80, synth.APERTURE_SETS["symmetric"])
+    M = dense_M(aperture_pixels(codes), W)
+    for k1 in range(W):
+        k2 = (k1 - 16) % W
+        np.testing.assert_allclose(M[:, k1 * W + k2], M[:, k2 * W + k1], atol=1e-9)
+    codes = synth.aperture_mask(16, 16, 4, 81, synth.APERTURE_SETS["mixed"])
+    M = dense_M(aperture_pixels(codes), W)
+    assert np.abs(M[:, 26 * W + 10] - M[:, 10 * W + 26]).max() > 1e-3
