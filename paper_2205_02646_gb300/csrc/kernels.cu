@@ -317,11 +317,15 @@ __device__ __forceinline__ void warp_argmax(T &bs, int &bk)
     }
 }
 
+// Aperture structure of the table slots, fixed per plan:
+//   kLayThreeQuarter: slot t holds every sub-pixel but t (three-quarter sampling);
+//   kLaySingle:       slot t holds sub-pixel t only (quarter sampling);
+//   kLayGeneral:      slot t holds the sub-pixels in bits 4t..4t+3 of a.slot_ap.
+constexpr int kLayThreeQuarter = 0, kLayGeneral = 1, kLaySingle = 2;
+
 // Per-iteration bookkeeping shared by both loops: delta, the update
 // coefficients g_t = gamma delta h_t(uv) and the synthesis of Eq. 18.
-// GENERAL selects slot apertures from a.slot_ap instead of the three-quarter
-// ones (slot t = everything but sub-pixel t).
-template <typename T, bool GENERAL = false>
+template <typename T, int LAY = kLayThreeQuarter>
 __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, const T invD, const T gamma,
                                             const int bk, const T Rre, const T Rim, const int eta, const int gam,
                                             const int lane, const long long trow, const int it, int &u, int &v,
@@ -331,7 +335,13 @@ __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, cons
     u = bk >> 5;
     v = bk & 31;
     const C2<T> ev = om[v], eu = om[u], euv = om[(u + v) & 31];
-    if constexpr (GENERAL) {
+    if constexpr (LAY == kLaySingle) {
+        // h_t(uv) = e_t, e = (1, w^v, w^u, w^(u+v))
+        g[0] = gd;
+        g[1] = cmul(gd, ev);
+        g[2] = cmul(gd, eu);
+        g[3] = cmul(gd, euv);
+    } else if constexpr (LAY == kLayGeneral) {
         // h_t(uv) = sum over slot t's sub-pixels s of e_s, e = (1, w^v, w^u, w^(u+v))
         const C2<T> e[4] = {C2<T>{1, 0}, ev, eu, euv};
 #pragma unroll
@@ -360,7 +370,7 @@ __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, cons
 }
 
 // ------------------------------------------------------ FP64 (scalar) loop --
-template <typename T, bool GENERAL = false>
+template <typename T, int LAY = kLayThreeQuarter>
 __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec, const C2<T> *om,
                                             const C2<T> *omc, const WorkEntry we, const int lane,
                                             C2<T> (&Y)[8][4])
@@ -391,9 +401,12 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
             }
             // R_k = sum_s conj(e_s(k)) Z_s, e = (1, w^k2, w^k1, w^(k1+k2)), with Z_s the
             // sum of Y_t over the slots t whose aperture holds sub-pixel s
-            // (three-quarter: Z_s = S - Y_s, S = sum_t Y_t)
+            // (three-quarter: Z_s = S - Y_s, S = sum_t Y_t; single: Z_s = Y_s)
             C2<T> Z[4];
-            if constexpr (GENERAL) {
+            if constexpr (LAY == kLaySingle) {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) Z[sp] = Y[i][sp];
+            } else if constexpr (LAY == kLayGeneral) {
 #pragma unroll
                 for (int sp = 0; sp < 4; ++sp) {
                     Z[sp] = {0, 0};
@@ -426,7 +439,7 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;    // lane owning kap = (k1 & 15, k2 & 15)
         const T Rre = __shfl_sync(0xffffffffu, b0re, wl);
         const T Rim = __shfl_sync(0xffffffffu, b0im, wl);
-        select_step<T, GENERAL>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
+        select_step<T, LAY>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
     }
     if (lane < 16) {
         const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
@@ -471,7 +484,7 @@ __device__ __forceinline__ CP rot(float2 c, float2 s, float2 ns, CP z)
 }
 __device__ __forceinline__ float2 energy(float2 q, CP r) { return mul2(q, fma2(r.im, r.im, mul2(r.re, r.re))); }
 
-template <bool GENERAL = false>
+template <int LAY = kLayThreeQuarter>
 __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &rec, const C2<float> *om,
                                                 const C2<float> *omc, const PairTables &pt, const WorkEntry we,
                                                 const int lane, C2<float> (&Y0)[8][4])
@@ -519,7 +532,10 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
             }
             // Z_s = sum of Y_t over the slots holding sub-pixel s (three-quarter: S - Y_s)
             CP Z[4];
-            if constexpr (GENERAL) {
+            if constexpr (LAY == kLaySingle) {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) Z[sp] = Y[jj][sp];
+            } else if constexpr (LAY == kLayGeneral) {
 #pragma unroll
                 for (int sp = 0; sp < 4; ++sp) {
                     Z[sp] = {f2(0.f, 0.f), f2(0.f, 0.f)};
@@ -561,8 +577,7 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;
         const float Rre = __shfl_sync(0xffffffffu, b0re, wl);
         const float Rim = __shfl_sync(0xffffffffu, b0im, wl);
-        select_step<float, GENERAL>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g,
-                                    fpix);
+        select_step<float, LAY>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
     }
     if (lane < 16) {
         const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
@@ -758,8 +773,10 @@ __device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortli
 // blocks whose left-out mass is <= max_missing, other blocks untouched;
 // 2 = full loop on the other blocks only.  Modes 1 and 2 together cover
 // every block once; each is its own instantiation, so the register budget
-// of one does not constrain the other.  3 = mode 0 for sensor layouts
-// other than three-quarter sampling (slot apertures from a.slot_ap).
+// of one does not constrain the other.  3 and 4 = mode 0 for other sensor
+// layouts: slot apertures from a.slot_ap (3), or one sub-pixel per slot (4).
+__host__ __device__ constexpr int lay_of(int mode) { return mode == 3 ? kLayGeneral : mode == 4 ? kLaySingle : kLayThreeQuarter; }
+
 template <typename T, int MODE> struct Loop;
 template <int MODE> struct Loop<float, MODE> {
     using Rec = typename RecOf<float, MODE>::type;
@@ -767,10 +784,10 @@ template <int MODE> struct Loop<float, MODE> {
                                                const C2<float> *om, const C2<float> *omc, const PairTables &pt,
                                                const float *wt, const WorkEntry we, const int lane)
     {
-        if constexpr (MODE == 0 || MODE == 3) {
+        if constexpr (MODE == 0 || MODE == 3 || MODE == 4) {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            greedy_loop_f32<MODE == 3>(a, rec, om, omc, pt, we, lane, Y);
+            greedy_loop_f32<lay_of(MODE)>(a, rec, om, omc, pt, we, lane, Y);
         } else if constexpr (MODE == 1) {
             const Shortlist &sl = a.shortlists[we.ord];
             if (!(sl.missing <= a.max_missing)) return;
@@ -784,7 +801,7 @@ template <int MODE> struct Loop<float, MODE> {
             if (sl.missing <= a.max_missing) return;
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            greedy_loop_f32<false>(a, rec, om, omc, pt, we, lane, Y);
+            greedy_loop_f32<kLayThreeQuarter>(a, rec, om, omc, pt, we, lane, Y);
         }
     }
 
@@ -816,7 +833,7 @@ template <int MODE> struct Loop<double, MODE> {
     {
         C2<double> Y[8][4];
         initial_projection<double>(a, rec, scratch, omc, wt, we, lane, Y);
-        greedy_loop<double, MODE == 3>(a, rec, om, omc, we, lane, Y);
+        greedy_loop<double, lay_of(MODE)>(a, rec, om, omc, we, lane, Y);
     }
     static __device__ __forceinline__ void run_pair(const Args &a, const Record<double> &rec, C2<double> *scratch,
                                                     const C2<double> *om, const C2<double> *omc,
@@ -1057,7 +1074,7 @@ __global__ void __launch_bounds__(kFlyWarps * 32, 2) onthefly_kernel(const Args 
 #pragma unroll
                 for (int B = 0; B < 2; ++B) rec.invD[(8 * h + i + 16 * A) * kW + k2 + 16 * B] = invd[i][2 * A + B];
         __syncwarp();
-        greedy_loop_f32<false>(a, rec, om, omc, *pt, we, lane, Y);
+        greedy_loop_f32<kLayThreeQuarter>(a, rec, om, omc, *pt, we, lane, Y);
     }
 }
 
@@ -1243,6 +1260,7 @@ const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 8, 1, 0), RLJSDE_VARIANT(double, 4, 1, 0), RLJSDE_VARIANT(double, 8, 1, 0),
     RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 3, 2),
     RLJSDE_VARIANT(float, 4, 3, 3), RLJSDE_VARIANT(float, 8, 2, 3), RLJSDE_VARIANT(double, 4, 1, 3),
+    RLJSDE_VARIANT(float, 4, 3, 4), RLJSDE_VARIANT(float, 8, 2, 4), RLJSDE_VARIANT(double, 4, 1, 4),
 };
 #undef RLJSDE_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -1341,7 +1359,7 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
     // Default: 4 warps per CTA, as many CTAs as the 168-register variant fits.
     if (warps == 0) { warps = 4; if (ctas_per_sm == 0) ctas_per_sm = 3; }
     const int fp64 = p->params.precision == 1;
-    const int mode = p->kind == 1 ? 3 : 0;
+    const int mode = p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0;
     // The variant with this precision and warp count whose register budget
     // admits the requested CTAs per SM (the largest one not above it).
     int best = -1, best_occ = 0;

@@ -287,12 +287,14 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     if (total_blocks > (1ll << 30)) return RLJSDE_ERR_BAD_SHAPE;
 
     // Aperture slots of the factored tables (Sec. I layouts).  Three-quarter
-    // apertures keep slot t = opaque quadrant t; up to four other apertures
-    // take slots in increasing code order; more need the direct path.
+    // apertures keep slot t = opaque quadrant t, single sub-pixels (quarter
+    // sampling) slot t = sub-pixel t; up to four other apertures take slots in
+    // increasing code order; more need the direct path.
     present &= ~1u;                             // an empty aperture measures nothing
     int n_ap = 0;
     for (int a = 1; a < 16; ++a) n_ap += (present >> a) & 1;
     const uint32_t tq = (1u << 14) | (1u << 13) | (1u << 11) | (1u << 7);
+    const uint32_t single = (1u << 1) | (1u << 2) | (1u << 4) | (1u << 8);
     int kind;
     uint32_t slot_ap = 0;
     uint8_t slot_of_ap[16];
@@ -300,6 +302,9 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     if ((present & ~tq) == 0) {
         kind = 0;
         for (int t = 0; t < 4; ++t) { slot_of_ap[15 ^ (1 << t)] = (uint8_t)t; slot_ap |= (uint32_t)(15 ^ (1 << t)) << (4 * t); }
+    } else if ((present & ~single) == 0) {
+        kind = 3;
+        for (int t = 0; t < 4; ++t) { slot_of_ap[1 << t] = (uint8_t)t; slot_ap |= (uint32_t)(1 << t) << (4 * t); }
     } else if (n_ap <= 4) {
         kind = 1;
         int t = 0;

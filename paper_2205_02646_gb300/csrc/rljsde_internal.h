@@ -120,7 +120,8 @@ struct rljsde_plan {
     int direct = 0;                   // path == 2
     int onthefly = 0;                 // tables built per block in the kernel (path 3, or auto)
     int kind = 0;                     // 0: three-quarter apertures (slot t = opaque quadrant t);
-                                      // 1: up to four other apertures; 2: more (direct path only)
+                                      // 1: up to four other apertures; 2: more (direct path only);
+                                      // 3: single sub-pixels (slot t = sub-pixel t)
     uint32_t slot_ap = 0;             // aperture code of slot t in bits 4t..4t+3
     int n_apertures = 0;              // distinct non-empty apertures in the masks
     int device = 0, sm_count = 0;

@@ -44,7 +44,7 @@ def test_recurrent_layouts_vs_oracle(rl, name, seed):
           % (name, res["matched"], res["n"], res["near_ties"], res["max_err"]))
 
 
-@pytest.mark.parametrize("name", ["mixed", "symmetric"])
+@pytest.mark.parametrize("name", ["mixed", "symmetric", "quarter"])
 def test_layout_fp64_loop_vs_oracle(rl, name):
     """FP64 loop: the same selections as the oracle, including the exact
     ties of the transpose-symmetric layout (both sides compare binary32
