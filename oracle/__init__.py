@@ -21,6 +21,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   aperture layouts: three-quarter apertures == opaque codes, quarter
   sampling and the full 2x2 aperture reduce to closed forms built on
   ``numpy.fft.fft2``, unobservable Nyquist candidates never selected.
+* ``pairs=1`` (conjugate-pair update, a variant of the paper's loop) --
+  pinned: residual and model stay exactly real, E_w non-increasing for
+  gamma <= 1, identity measurement recovers conjugate-pair sparse signals
+  exactly and equals two single updates per pair, direct == recurrent.
 * ``frequency_weight``   -- the paper gives no formula (Sec. IV only says q
   prefers low frequencies): parity unpinned against the paper; the tests
   check the stated reading's properties (1 at DC, symmetric, isotropic,
@@ -47,7 +51,7 @@ class _CParams(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("block", ctypes.c_int), ("nu_max", ctypes.c_int),
                 ("gamma_odc", ctypes.c_double), ("rho_decay", ctypes.c_double),
                 ("q_mode", ctypes.c_int), ("q_table", ctypes.POINTER(ctypes.c_double)),
-                ("layout", ctypes.c_int)]
+                ("layout", ctypes.c_int), ("pairs", ctypes.c_int)]
 
 
 LAYOUT_THREE_QUARTER = 0   # mask code = index 2 * dy + dx of the opaque sub-pixel
@@ -56,21 +60,23 @@ LAYOUT_APERTURE = 1        # mask code = bit set of the transparent sub-pixels
 
 class Params:
     """Reconstruction parameters (window W, block B, nu_max, gamma_odc, rho, q,
-    and the meaning of the mask codes)."""
+    the meaning of the mask codes, and the update: one complex coefficient
+    per iteration, or ``pairs=1`` for the conjugate-pair update)."""
 
     def __init__(self, window=32, block=4, nu_max=100, gamma_odc=0.5, rho_decay=0.7,
-                 q_mode=0, q_table=None, layout=LAYOUT_THREE_QUARTER):
+                 q_mode=0, q_table=None, layout=LAYOUT_THREE_QUARTER, pairs=0):
         self.window, self.block, self.nu_max = int(window), int(block), int(nu_max)
         self.gamma_odc, self.rho_decay, self.q_mode = float(gamma_odc), float(rho_decay), int(q_mode)
         self.q_table = None if q_table is None else np.ascontiguousarray(q_table, dtype=np.float64)
         self.layout = int(layout)
+        self.pairs = int(pairs)
 
     def c(self):
         qp = None
         if self.q_table is not None:
             qp = self.q_table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         return _CParams(self.window, self.block, self.nu_max, self.gamma_odc, self.rho_decay,
-                        self.q_mode, qp, self.layout)
+                        self.q_mode, qp, self.layout, self.pairs)
 
 
 def load():

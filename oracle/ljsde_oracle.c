@@ -48,6 +48,13 @@
  *   - the target block sits at window offset (W - B) / 2 in both axes;
  *   - the output is the real part of the back-transformed model (Eq. 18).
  *
+ * Variant (pairs = 1), the conjugate-pair update of the frequency selective
+ * reconstruction family, for real measurements: the argmax runs over one
+ * half of the candidates (k with k <= -k mod W in linear order, the other
+ * half being their conjugate mirrors), and each selection updates both
+ * c_k += gamma delta and c_-k += conj(gamma delta), so the model and the
+ * residual stay real.  A self-conjugate k (k = -k) is updated once.
+ *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fcx-limited-range -shared -fPIC
  */
 #include <complex.h>
@@ -72,7 +79,16 @@ typedef struct {
     int layout;          /* mask codes: 0 = index of the opaque sub-pixel of
                             a three-quarter pixel (0..3); 1 = set of
                             transparent sub-pixels, bit 2 * dy + dx (0..15) */
+    int pairs;           /* 0: one complex coefficient per iteration (Eq. 15);
+                            1: conjugate-pair update (see above)            */
 } orc_params;
+
+/* Linear index of the conjugate mirror -k (mod W in both axes). */
+static int mirror_of(int k, int W)
+{
+    int k1 = k / W, k2 = k % W;
+    return ((W - k1) % W) * W + (W - k2) % W;
+}
 
 /* Sub-pixel s = 2 * dy + dx of an L-pixel with mask code `code` is
  * transparent (Eq. 1: A = 1 there). */
@@ -196,18 +212,20 @@ static void unobservable(const orc_window *win, char *flag)
 }
 
 /* Argmax of Eq. 10 / Eq. 11 on binary32-rounded scores, lowest index on
- * ties.  Also reports the FP64 relative gap to the best other candidate. */
-static int select_atom(int K, const double *score, double *gap_out)
+ * ties; with `half`, over the candidates k <= mirror(k) only.  Also reports
+ * the FP64 relative gap to the best other candidate. */
+static int select_atom(int K, int W, int half, const double *score, double *gap_out)
 {
     int best = 0;
     float bkey = (float)score[0];
     for (int k = 1; k < K; ++k) {
+        if (half && mirror_of(k, W) < k) continue;
         float key = (float)score[k];
         if (key > bkey) { bkey = key; best = k; }
     }
     double other = 0.0;
     for (int k = 0; k < K; ++k)
-        if (k != best && score[k] > other) other = score[k];
+        if (k != best && !(half && mirror_of(k, W) < k) && score[k] > other) other = score[k];
     if (gap_out)
         *gap_out = score[best] > 0.0 ? (score[best] - other) / score[best] : 0.0;
     return best;
@@ -262,12 +280,21 @@ static int window_direct(const orc_window *win, const orc_params *p, const cplx 
         for (int k = 0; k < K; ++k)
             score[k] = (D[k] < 1e-300 || zero[k]) ? 0.0
                      : q[k] * (creal(N[k]) * creal(N[k]) + cimag(N[k]) * cimag(N[k])) / D[k];
-        int uv = select_atom(K, score, tr->gap ? &tr->gap[nu] : NULL);
+        int uv = select_atom(K, W, p->pairs, score, tr->gap ? &tr->gap[nu] : NULL);
         cplx delta = (D[uv] < 1e-300 || zero[uv]) ? 0.0 : N[uv] / D[uv];      /* Eq. 16 */
         cplx step = p->gamma_odc * delta;
+        int vu = mirror_of(uv, W);
         tr->c[uv] += step;                                         /* Eq. 15 */
         const cplx *au = a + (size_t)uv;
-        for (int m = 0; m < nm; ++m) r[m] -= step * au[(size_t)m * K];   /* Eq. 7 */
+        if (p->pairs && vu != uv) {
+            /* conjugate partner: c_-k += conj(step), r -= step a_k + conj(step) a_-k */
+            tr->c[vu] += conj(step);
+            const cplx *av = a + (size_t)vu;
+            for (int m = 0; m < nm; ++m)
+                r[m] -= step * au[(size_t)m * K] + conj(step) * av[(size_t)m * K];
+        } else {
+            for (int m = 0; m < nm; ++m) r[m] -= step * au[(size_t)m * K];   /* Eq. 7 */
+        }
         if (tr->sel) tr->sel[nu] = uv;
         if (tr->dc) { tr->dc[2 * nu] = creal(step); tr->dc[2 * nu + 1] = cimag(step); }
         if (tr->energy) tr->energy[nu + 1] = weighted_energy(nm, win->w, r);
@@ -334,12 +361,19 @@ static int window_recurrent(const orc_window *win, const orc_tables *t, const or
         for (int k = 0; k < K; ++k)                                   /* Eq. 11 */
             score[k] = (t->D[k] < 1e-300 || zero[k]) ? 0.0
                      : q[k] * (creal(R[k]) * creal(R[k]) + cimag(R[k]) * cimag(R[k])) / t->D[k];
-        int uv = select_atom(K, score, tr->gap ? &tr->gap[nu] : NULL);
+        int uv = select_atom(K, win->W, p->pairs, score, tr->gap ? &tr->gap[nu] : NULL);
         cplx delta = (t->D[uv] < 1e-300 || zero[uv]) ? 0.0 : R[uv] / t->D[uv];    /* Eq. 16 */
         cplx step = p->gamma_odc * delta;
+        int vu = mirror_of(uv, win->W);
         tr->c[uv] += step;                                            /* Eq. 15 */
         const cplx *Cu = t->CT + (size_t)uv * K;
-        for (int k = 0; k < K; ++k) R[k] -= step * Cu[k];             /* Eq. 17 */
+        if (p->pairs && vu != uv) {
+            tr->c[vu] += conj(step);
+            const cplx *Cv = t->CT + (size_t)vu * K;
+            for (int k = 0; k < K; ++k) R[k] -= step * Cu[k] + conj(step) * Cv[k];
+        } else {
+            for (int k = 0; k < K; ++k) R[k] -= step * Cu[k];         /* Eq. 17 */
+        }
         if (tr->sel) tr->sel[nu] = uv;
         if (tr->dc) { tr->dc[2 * nu] = creal(step); tr->dc[2 * nu + 1] = cimag(step); }
     }
@@ -355,6 +389,7 @@ static int check_params(const orc_params *p)
     if (!p || p->window < 8 || p->window % 8 || p->window > 128 || p->nu_max < 0) return ORC_EINVAL;
     if (p->q_mode == 2 && !p->q_table) return ORC_EINVAL;
     if (p->layout != 0 && p->layout != 1) return ORC_EINVAL;
+    if (p->pairs != 0 && p->pairs != 1) return ORC_EINVAL;
     return ORC_OK;
 }
 

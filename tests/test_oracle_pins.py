@@ -454,3 +454,93 @@ def test_transpose_symmetric_apertures_make_identical_atoms():
     codes = synth.aperture_mask(16, 16, 4, 81, synth.APERTURE_SETS["mixed"])
     M = dense_M(aperture_pixels(codes), W)
     assert np.abs(M[:, 26 * W + 10] - M[:, 10 * W + 26]).max() > 1e-3
+
+
+# --- conjugate-pair update (pairs=1), the frequency selective variant -------
+def _three_quarter_window(seed, W=16):
+    L = W // 2
+    r0 = rng(seed)
+    codes = r0.integers(0, 4, (L, L)).astype(np.uint8)
+    pix = three_quarter_pixels(codes)
+    return pix, r0.uniform(0.05, 1.0, len(pix)), r0.uniform(0.0, 3.0, len(pix))
+
+
+def test_pairs_keep_residual_and_model_real():
+    W = 16
+    pix, w, y = _three_quarter_window(90, W)
+    out = oracle.window_solve(pix, w, y, oracle.Params(window=W, nu_max=30, pairs=1))
+    assert np.all(out["r"].imag == 0.0)
+    c = out["c"]
+    k = np.arange(W)
+    np.testing.assert_array_equal(c[(-k) % W][:, (-k) % W], np.conj(c))
+    sel = out["sel"]
+    assert np.all(sel <= mirror(sel, W))                    # half-plane representatives
+    # with a q that is not symmetric the mirror scores differ; the argmax
+    # still only looks at the representatives
+    qt = rng(93).uniform(0.1, 1.0, W * W)
+    oq = oracle.window_solve(pix, w, y, oracle.Params(window=W, nu_max=30, pairs=1, q_mode=2, q_table=qt))
+    assert np.all(oq["sel"] <= mirror(oq["sel"], W))
+    # the model is real on the whole window
+    eta = np.arange(W)
+    ph = np.exp(2j * np.pi * np.outer(eta, k) / W)
+    assert np.abs((ph @ c @ ph.T).imag).max() < 1e-12
+    # measurement consistency (Eq. 7) with the pair updates
+    model = (ph @ c @ ph.T).real
+    re_int = np.array([sum(model[e, g] for e, g in px) for px in pix])
+    np.testing.assert_allclose(out["r"].real, y - re_int, atol=1e-10)
+
+
+@pytest.mark.parametrize("gam", [0.3, 0.5, 1.0])
+def test_pairs_energy_non_increasing(gam):
+    """For a real residual r, the pair step v = 2 Re(gamma delta a_k) gives
+    E' - E = -4 gamma |delta|^2 D_k + |v|_w^2 <= -4 gamma (1 - gamma) |delta|^2 D_k."""
+    W = 16
+    pix, w, y = _three_quarter_window(91, W)
+    out = oracle.window_solve(pix, w, y, oracle.Params(window=W, nu_max=40, gamma_odc=gam, pairs=1))
+    e = out["energy"]
+    assert np.all(np.diff(e) <= 1e-12 * e[0])
+    # the bound, checked step by step with dense numpy atoms
+    M = dense_M(pix, W)
+    D = (w[:, None] * np.abs(M) ** 2).sum(0)
+    for i in range(5):
+        k = out["sel"][i]
+        d = out["dc"][i] / gam
+        if mirror(k, W) != k:
+            assert e[i + 1] - e[i] <= -4 * gam * (1 - gam) * abs(d) ** 2 * D[k] + 1e-12 * e[0]
+
+
+def test_pairs_identity_measurement_recovers_real_sparse_and_equals_two_single_steps():
+    W = 8
+    pix = [[(e, g)] for e in range(W) for g in range(W)]
+    w = np.ones(W * W)
+    r0 = rng(92)
+    ks = [9, 18, 43]                                        # none self-conjugate
+    coef = r0.uniform(0.5, 2.0, 3) * np.exp(2j * np.pi * r0.random(3))
+    k1, k2 = np.meshgrid(np.arange(W), np.arange(W), indexing="ij")
+    img = np.zeros((W, W), complex)
+    truth = np.zeros(W * W, complex)
+    for k, a in zip(ks, coef):
+        for kk, aa in ((k, a), (mirror(k, W), np.conj(a))):
+            img += aa * np.exp(2j * np.pi * ((kk // W) * k1 + (kk % W) * k2) / W)
+            truth[kk] += aa
+    y = img.real.ravel()
+    p3 = oracle.Params(window=W, nu_max=3, gamma_odc=1.0, q_mode=1, pairs=1)
+    out = oracle.window_solve(pix, w, y, p3)
+    np.testing.assert_allclose(out["c"].ravel(), truth, atol=1e-12)
+    F = np.fft.fft2(img.real).ravel()
+    kstar = int(np.argmax(np.abs(F)))
+    kstar = min(kstar, mirror(kstar, W))
+    assert out["sel"][0] == kstar
+    np.testing.assert_allclose(out["dc"][0], F[kstar] / W ** 2, rtol=1e-12)
+    # orthogonal atoms: one pair step == the two single steps k, -k
+    single = oracle.window_solve(pix, w, y, oracle.Params(window=W, nu_max=6, gamma_odc=1.0, q_mode=1))
+    np.testing.assert_allclose(single["c"], out["c"], atol=1e-12)
+
+
+def test_pairs_direct_equals_recurrent_w16_full_image():
+    f, mask, y = synth.workload("rljsde_64x64")
+    p = oracle.Params(window=16, nu_max=40, pairs=1)
+    a, ta = oracle.reconstruct(y, mask, p, trace=True)
+    b, tb = oracle.reconstruct(y, mask, p, recurrent=True, trace=True)
+    assert (ta["sel"] == tb["sel"]).all()
+    assert np.max(np.abs(a - b)) <= 1e-10
