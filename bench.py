@@ -516,6 +516,38 @@ def run_layouts(args):
     print(json.dumps(out), flush=True)
 
 
+def run_pairs(args):
+    """Single complex-coefficient updates (the paper's Eq. 15) against the
+    conjugate-pair update on the 1024x1024 workload: throughput and PSNR
+    against the ground-truth image for several iteration counts (a pair
+    iteration adds two coefficients)."""
+    import torch
+    from paper_2205_02646_gb300 import build, proposal, rljsde, synth
+    build.build()
+    torch.cuda.set_device(0)
+    f, mask, y = synth.workload("rljsde_1024x1024")
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.empty((1024, 1024), device="cuda")
+    truth = torch.from_numpy(f).cuda()
+    out = {"study": "pairs", "workload": "rljsde_1024x1024", "points": []}
+    for pairs, nu in ((0, 100), (0, 50), (1, 50), (1, 100), (0, 200), (1, 25)):
+        plan = rljsde.Plan(mask, rljsde.default_params(nu_max=nu, pairs=pairs))
+        plan.reconstruct(lr, hr)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.reconstruct(lr, hr)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        plan.check()
+        out["points"].append({"pairs": pairs, "nu_max": nu, "mp_per_s": 1.048576 / (best / 1e3), "ms": best,
+                              "psnr": proposal.psnr(hr.double(), truth)})
+    print(json.dumps(out), flush=True)
+
+
 def run_learned_launch(args):
     """The learned inference path (whole-image proposal, shortlist loop,
     fallback pass) run twice with a seeded untrained network: the launch
@@ -548,7 +580,7 @@ def main():
     ap.add_argument("--ref-blocks", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", default=None,
-                    choices=[None, "precision", "learned-launch", "random-mask", "layouts"])
+                    choices=[None, "precision", "learned-launch", "random-mask", "layouts", "pairs"])
     ap.add_argument("--sample", type=int, default=3072)
     ap.add_argument("--train-images", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=6)
@@ -573,6 +605,9 @@ def main():
         return
     if args.study == "layouts":
         run_layouts(args)
+        return
+    if args.study == "pairs":
+        run_pairs(args)
         return
     if args.workload == "rljsde_learned":
         run_learned(args)

@@ -93,6 +93,13 @@ typedef struct {
                              three-quarter.  A candidate whose atom cancels on
                              every measurement of its window (e.g. the Nyquist
                              row under full 2x2 apertures) is never selected   */
+    int pairs;            /* 0 (default) = one complex coefficient per iteration
+                             (Eq. 15, the paper's loop); 1 = conjugate-pair
+                             update of the frequency selective reconstruction
+                             family: the argmax runs over k <= -k (linear order)
+                             and each selection adds gamma delta to c_k and its
+                             conjugate to c_-k (once if k = -k), so model and
+                             residual stay real.  Not with the learned proposal */
 } rljsde_params;
 
 /* Fill *p with the defaults above.  Returns RLJSDE_ERR_INVALID_ARG on NULL. */

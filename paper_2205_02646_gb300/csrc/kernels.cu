@@ -145,6 +145,7 @@ struct Args {
     // and the meaning of the mask codes (direct path)
     uint32_t slot_ap;
     int layout;
+    int pairs;                 // conjugate-pair update (direct path; the loops take it as a template flag)
     // direct path only
     const uint8_t *masks;
     const long long *mask_offset;
@@ -325,11 +326,14 @@ constexpr int kLayThreeQuarter = 0, kLayGeneral = 1, kLaySingle = 2;
 
 // Per-iteration bookkeeping shared by both loops: delta, the update
 // coefficients g_t = gamma delta h_t(uv) and the synthesis of Eq. 18.
-template <typename T, int LAY = kLayThreeQuarter>
+// With PAIRS (conjugate-pair update) the selection also updates c_-uv by
+// conj(gamma delta); its coefficients are conj(g_t), since h_t(-k) =
+// conj h_t(k), and pw = 1 (0 when uv is its own mirror) scales them.
+template <typename T, int LAY = kLayThreeQuarter, bool PAIRS = false>
 __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, const T invD, const T gamma,
                                             const int bk, const T Rre, const T Rim, const int eta, const int gam,
                                             const int lane, const long long trow, const int it, int &u, int &v,
-                                            C2<T> (&g)[4], T &fpix)
+                                            C2<T> (&g)[4], T &fpix, T &pw)
 {
     const C2<T> gd = {gamma * (Rre * invD), gamma * (Rim * invD)};   // gamma * delta (Eqs. 15, 16)
     u = bk >> 5;
@@ -361,7 +365,13 @@ __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, cons
         g[3] = cmul(gd, csub(P, euv));
     }
     const C2<T> ph = om[(eta * u + gam * v) & 31];
-    fpix += gd.re * ph.re - gd.im * ph.im;
+    if constexpr (PAIRS) {
+        // Re(x Phi_uv) + Re(conj(x) Phi_-uv) = 2 Re(x Phi_uv) unless uv = -uv
+        pw = ((u & 15) == 0 && (v & 15) == 0) ? T(0) : T(1);
+        fpix += (T(1) + pw) * (gd.re * ph.re - gd.im * ph.im);
+    } else {
+        fpix += gd.re * ph.re - gd.im * ph.im;
+    }
     if (a.trace_sel != nullptr && lane == 0) {
         a.trace_sel[trow + it] = (uint16_t)bk;
         a.trace_dc[2 * (trow + it)] = (float)gd.re;
@@ -370,7 +380,7 @@ __device__ __forceinline__ void select_step(const Args &a, const C2<T> *om, cons
 }
 
 // ------------------------------------------------------ FP64 (scalar) loop --
-template <typename T, int LAY = kLayThreeQuarter>
+template <typename T, int LAY = kLayThreeQuarter, bool PAIRS = false>
 __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec, const C2<T> *om,
                                             const C2<T> *omc, const WorkEntry we, const int lane,
                                             C2<T> (&Y)[8][4])
@@ -381,13 +391,14 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
     const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
     T fpix = 0;                                     // Eq. 18 accumulator
     int u = 0, v = 0;
+    T pw = 0;
     C2<T> g[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     const long long trow = (long long)we.ord * a.nu_max;
 
     for (int it = 0; it < a.nu_max; ++it) {
         T bs0 = -1, bs1 = -1, b0re = 0, b0im = 0, b1re = 0, b1im = 0;
         int bk0 = 0, bk1 = 0;
-        const int d2 = (v - k2) & 15;
+        const int d2 = (v - k2) & 15, d2c = (-v - k2) & 15;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int k1 = 8 * h + i;
@@ -398,6 +409,15 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
                 Y[i][1] = csub(Y[i][1], cmul(g[1], C2<T>{G01.z, G01.w}));
                 Y[i][2] = csub(Y[i][2], cmul(g[2], C2<T>{G23.x, G23.y}));
                 Y[i][3] = csub(Y[i][3], cmul(g[3], C2<T>{G23.z, G23.w}));
+                if constexpr (PAIRS) {
+                    // the partner -uv: Y_t -= pw conj(g_t) G_t((-uv - kap) mod 16)
+                    const int dc = (((-u - k1) & 15) << 4) | d2c;
+                    const Vec4<T> H01 = ld4(&rec.G01[dc]), H23 = ld4(&rec.G23[dc]);
+                    Y[i][0] = csub(Y[i][0], cmul(C2<T>{pw * g[0].re, -pw * g[0].im}, C2<T>{H01.x, H01.y}));
+                    Y[i][1] = csub(Y[i][1], cmul(C2<T>{pw * g[1].re, -pw * g[1].im}, C2<T>{H01.z, H01.w}));
+                    Y[i][2] = csub(Y[i][2], cmul(C2<T>{pw * g[2].re, -pw * g[2].im}, C2<T>{H23.x, H23.y}));
+                    Y[i][3] = csub(Y[i][3], cmul(C2<T>{pw * g[3].re, -pw * g[3].im}, C2<T>{H23.z, H23.w}));
+                }
             }
             // R_k = sum_s conj(e_s(k)) Z_s, e = (1, w^k2, w^k1, w^(k1+k2)), with Z_s the
             // sum of Y_t over the slots t whose aperture holds sub-pixel s
@@ -439,7 +459,8 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;    // lane owning kap = (k1 & 15, k2 & 15)
         const T Rre = __shfl_sync(0xffffffffu, b0re, wl);
         const T Rim = __shfl_sync(0xffffffffu, b0im, wl);
-        select_step<T, LAY>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
+        select_step<T, LAY, PAIRS>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix,
+                                   pw);
     }
     if (lane < 16) {
         const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
@@ -484,7 +505,7 @@ __device__ __forceinline__ CP rot(float2 c, float2 s, float2 ns, CP z)
 }
 __device__ __forceinline__ float2 energy(float2 q, CP r) { return mul2(q, fma2(r.im, r.im, mul2(r.re, r.re))); }
 
-template <int LAY = kLayThreeQuarter>
+template <int LAY = kLayThreeQuarter, bool PAIRS = false>
 __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &rec, const C2<float> *om,
                                                 const C2<float> *omc, const PairTables &pt, const WorkEntry we,
                                                 const int lane, C2<float> (&Y0)[8][4])
@@ -500,7 +521,7 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
     const float2 e1c = f2(c1, c1), e1s = f2(s1, s1), e1n = f2(-s1, -s1);
     const float gamma = (float)a.gamma;
     const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
-    float fpix = 0.f;
+    float fpix = 0.f, pw = 0.f;
     int u = 0, v = 0;
     C2<float> g[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     const long long trow = (long long)we.ord * a.nu_max;
@@ -508,13 +529,22 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
     for (int it = 0; it < a.nu_max; ++it) {
         float bs0 = -1.f, bs1 = -1.f, b0re = 0.f, b0im = 0.f, b1re = 0.f, b1im = 0.f;
         int bk0 = 0, bk1 = 0;
-        const int d2 = (v - k2) & 15;
+        const int d2 = (v - k2) & 15, d2c = (-v - k2) & 15;
         float2 ngre[4], gim[4], ngim[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             ngre[t] = f2(-g[t].re, -g[t].re);
             gim[t] = f2(g[t].im, g[t].im);
             ngim[t] = f2(-g[t].im, -g[t].im);
+        }
+        // partner coefficients pw conj(g_t) = (pr, pi), packed as -pr, pi, -pi
+        float2 npre[4], ppim[4], nppim[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float pr = pw * g[t].re, pi = -pw * g[t].im;
+            npre[t] = f2(-pr, -pr);
+            ppim[t] = f2(pi, pi);
+            nppim[t] = f2(-pi, -pi);
         }
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
@@ -528,6 +558,17 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
                     const float2 Gre = f2(G.x, G.y), Gim = f2(G.z, G.w);
                     Y[jj][t].re = fma2(Gim, gim[t], fma2(Gre, ngre[t], Y[jj][t].re));
                     Y[jj][t].im = fma2(Gre, ngim[t], fma2(Gim, ngre[t], Y[jj][t].im));
+                }
+                if constexpr (PAIRS) {
+                    // the partner -uv: Y_t -= pw conj(g_t) G_t((-uv - kap) mod 16)
+                    const int d1c = (-u - k1) & 15;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float4 G = *reinterpret_cast<const float4 *>(rec.GP[t][d1c][d2c]);
+                        const float2 Gre = f2(G.x, G.y), Gim = f2(G.z, G.w);
+                        Y[jj][t].re = fma2(Gim, ppim[t], fma2(Gre, npre[t], Y[jj][t].re));
+                        Y[jj][t].im = fma2(Gre, nppim[t], fma2(Gim, npre[t], Y[jj][t].im));
+                    }
                 }
             }
             // Z_s = sum of Y_t over the slots holding sub-pixel s (three-quarter: S - Y_s)
@@ -577,7 +618,8 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;
         const float Rre = __shfl_sync(0xffffffffu, b0re, wl);
         const float Rim = __shfl_sync(0xffffffffu, b0im, wl);
-        select_step<float, LAY>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix);
+        select_step<float, LAY, PAIRS>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g,
+                                       fpix, pw);
     }
     if (lane < 16) {
         const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
@@ -728,8 +770,9 @@ __device__ __forceinline__ void shortlist_loop(const Args &a, const RecordShortF
             const C2<float> send = s.kc[0] == bk[b] ? s.R[0] : s.R[1];
             const float Rre = __shfl_sync(0xffffffffu, send.re, wl);
             const float Rim = __shfl_sync(0xffffffffu, send.im, wl);
+            float unused_pw;
             select_step<float>(a, om, rec.invD[bk[b]], gamma, bk[b], Rre, Rim, eta, gam, lane, trow[b], it, u[b],
-                               v[b], g[b], fpix[b]);
+                               v[b], g[b], fpix[b], unused_pw);
             // Eq. 17 on the shortlist
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -775,7 +818,14 @@ __device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortli
 // every block once; each is its own instantiation, so the register budget
 // of one does not constrain the other.  3 and 4 = mode 0 for other sensor
 // layouts: slot apertures from a.slot_ap (3), or one sub-pixel per slot (4).
-__host__ __device__ constexpr int lay_of(int mode) { return mode == 3 ? kLayGeneral : mode == 4 ? kLaySingle : kLayThreeQuarter; }
+// Bit 3 (kModePairs) added to modes 0, 3, 4: the conjugate-pair update.
+constexpr int kModePairs = 8;
+__host__ __device__ constexpr int lay_of(int mode)
+{
+    return (mode & 7) == 3 ? kLayGeneral : (mode & 7) == 4 ? kLaySingle : kLayThreeQuarter;
+}
+__host__ __device__ constexpr bool pairs_of(int mode) { return (mode & kModePairs) != 0; }
+__host__ __device__ constexpr bool plain_of(int mode) { return (mode & 7) == 0 || (mode & 7) == 3 || (mode & 7) == 4; }
 
 template <typename T, int MODE> struct Loop;
 template <int MODE> struct Loop<float, MODE> {
@@ -784,10 +834,10 @@ template <int MODE> struct Loop<float, MODE> {
                                                const C2<float> *om, const C2<float> *omc, const PairTables &pt,
                                                const float *wt, const WorkEntry we, const int lane)
     {
-        if constexpr (MODE == 0 || MODE == 3 || MODE == 4) {
+        if constexpr (plain_of(MODE)) {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            greedy_loop_f32<lay_of(MODE)>(a, rec, om, omc, pt, we, lane, Y);
+            greedy_loop_f32<lay_of(MODE), pairs_of(MODE)>(a, rec, om, omc, pt, we, lane, Y);
         } else if constexpr (MODE == 1) {
             const Shortlist &sl = a.shortlists[we.ord];
             if (!(sl.missing <= a.max_missing)) return;
@@ -833,7 +883,7 @@ template <int MODE> struct Loop<double, MODE> {
     {
         C2<double> Y[8][4];
         initial_projection<double>(a, rec, scratch, omc, wt, we, lane, Y);
-        greedy_loop<double, lay_of(MODE)>(a, rec, om, omc, we, lane, Y);
+        greedy_loop<double, lay_of(MODE), pairs_of(MODE)>(a, rec, om, omc, we, lane, Y);
     }
     static __device__ __forceinline__ void run_pair(const Args &a, const Record<double> &rec, C2<double> *scratch,
                                                     const C2<double> *om, const C2<double> *omc,
@@ -970,6 +1020,7 @@ struct FlySmem {
 static_assert(offsetof(RecordF32, invD) % 16 == 0 && sizeof(RecordF32::invD) >= 256 * 2 * sizeof(C2<float>),
               "the DFT scratch must fit in invD");
 
+template <bool PAIRS>
 __global__ void __launch_bounds__(kFlyWarps * 32, 2) onthefly_kernel(const Args a, int n_entries)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1055,6 +1106,11 @@ __global__ void __launch_bounds__(kFlyWarps * 32, 2) onthefly_kernel(const Args 
                     const float inv = D > 1e-30f ? 1.0f / D : 0.f;
                     invd[i][2 * A + B] = inv;
                     qd[2 * A + B] = qv[k] * inv;
+                    if (PAIRS) {
+                        // the argmax sees one member of each conjugate pair
+                        const int k1 = k >> 5, kk2 = k & 31;
+                        if (((-k1) & 31) * kW + ((-kk2) & 31) < k) qd[2 * A + B] = 0.f;
+                    }
                 }
             // qDP[j][A][k2] = (qD(2j, B=0), qD(2j+1, B=0), qD(2j, B=1), qD(2j+1, B=1))
             const int j = (8 * h + i) >> 1, el = i & 1;
@@ -1074,7 +1130,7 @@ __global__ void __launch_bounds__(kFlyWarps * 32, 2) onthefly_kernel(const Args 
 #pragma unroll
                 for (int B = 0; B < 2; ++B) rec.invD[(8 * h + i + 16 * A) * kW + k2 + 16 * B] = invd[i][2 * A + B];
         __syncwarp();
-        greedy_loop_f32<kLayThreeQuarter>(a, rec, om, omc, *pt, we, lane, Y);
+        greedy_loop_f32<kLayThreeQuarter, PAIRS>(a, rec, om, omc, *pt, we, lane, Y);
     }
 }
 
@@ -1193,6 +1249,8 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int k = j * kW + lane;
+                // conjugate-pair update: the argmax sees one member of each pair
+                if (a.pairs && ((-j) & 31) * kW + ((-lane) & 31) < k) continue;
                 const float s = D[j] > 0.f ? a.q[k] * (Nre[j] * Nre[j] + Nim[j] * Nim[j]) / D[j] : 0.f;
                 if (s > bs) {
                     bs = s;
@@ -1211,6 +1269,9 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
             const float dre = __shfl_sync(0xffffffffu, bre, wl), dim = __shfl_sync(0xffffffffu, bim, wl);
             const float gre = gamma * dre, gim = gamma * dim;
             const int u = bk >> 5, v = bk & 31;
+            // conjugate-pair update: c_-uv += conj(gamma delta) as well (not for uv = -uv),
+            // so r -= x + conj(x) with x = gamma delta a_m(uv): twice its real part
+            const float pf = (a.pairs && ((u & 15) != 0 || (v & 15) != 0)) ? 2.f : 1.f;
             // r_m -= gamma delta a_m(uv)   (Eq. 7)
             for (int m = lane; m < 256; m += 32) {
                 const int t = sm.type[warp][m];
@@ -1224,12 +1285,16 @@ __global__ void __launch_bounds__(kDirectWarps * 32) direct_kernel(const Args a,
                     aim += z.y;
                 }
                 float2 r = sm.r[warp][m];
-                r.x -= gre * are - gim * aim;
-                r.y -= gre * aim + gim * are;
+                if (pf == 2.f) {
+                    r.x -= 2.f * (gre * are - gim * aim);
+                } else {
+                    r.x -= gre * are - gim * aim;
+                    r.y -= gre * aim + gim * are;
+                }
                 sm.r[warp][m] = r;
             }
             const float2 ph = sm.om[(eta * u + gam * v) & 31];
-            fpix += gre * ph.x - gim * ph.y;
+            fpix += pf * (gre * ph.x - gim * ph.y);
             if (a.trace_sel && lane == 0) {
                 a.trace_sel[trow + it] = (uint16_t)bk;
                 a.trace_dc[2 * (trow + it)] = gre;
@@ -1261,6 +1326,8 @@ const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 3, 2),
     RLJSDE_VARIANT(float, 4, 3, 3), RLJSDE_VARIANT(float, 8, 2, 3), RLJSDE_VARIANT(double, 4, 1, 3),
     RLJSDE_VARIANT(float, 4, 3, 4), RLJSDE_VARIANT(float, 8, 2, 4), RLJSDE_VARIANT(double, 4, 1, 4),
+    RLJSDE_VARIANT(float, 4, 3, 8), RLJSDE_VARIANT(float, 4, 3, 11), RLJSDE_VARIANT(float, 4, 3, 12),
+    RLJSDE_VARIANT(double, 4, 1, 8), RLJSDE_VARIANT(double, 4, 1, 11), RLJSDE_VARIANT(double, 4, 1, 12),
 };
 #undef RLJSDE_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -1293,6 +1360,7 @@ Args make_args(const rljsde_plan *p)
     a.q = p->d_qD;
     a.slot_ap = p->slot_ap;
     a.layout = p->params.layout;
+    a.pairs = p->params.pairs;
     return a;
 }
 
@@ -1301,7 +1369,8 @@ int launch(const rljsde_plan *p, const Args &a, cudaStream_t s)
     if (p->direct) {
         direct_kernel<<<p->grid, kDirectWarps * 32, 0, s>>>(a, p->n_entries);
     } else if (p->onthefly) {
-        onthefly_kernel<<<p->grid, kFlyWarps * 32, FlySmem::bytes, s>>>(a, p->n_entries);
+        if (p->params.pairs) onthefly_kernel<true><<<p->grid, kFlyWarps * 32, FlySmem::bytes, s>>>(a, p->n_entries);
+        else onthefly_kernel<false><<<p->grid, kFlyWarps * 32, FlySmem::bytes, s>>>(a, p->n_entries);
     } else {
         const Variant &v = kVariants[p->variant];
         v.fn<<<p->grid, v.warps * 32, v.smem, s>>>(a);
@@ -1331,10 +1400,10 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
 {
     if (p->onthefly) {
         int n = 0;
-        if (cudaFuncSetAttribute(onthefly_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FlySmem::bytes) !=
+        void (*fly)(const Args, int) = p->params.pairs ? onthefly_kernel<true> : onthefly_kernel<false>;
+        if (cudaFuncSetAttribute(fly, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FlySmem::bytes) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, onthefly_kernel, kFlyWarps * 32, FlySmem::bytes) !=
-                cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fly, kFlyWarps * 32, FlySmem::bytes) != cudaSuccess)
             return RLJSDE_ERR_CUDA;
         if (n < 1) return RLJSDE_ERR_UNSUPPORTED;
         p->warps = kFlyWarps;
@@ -1359,7 +1428,7 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
     // Default: 4 warps per CTA, as many CTAs as the 168-register variant fits.
     if (warps == 0) { warps = 4; if (ctas_per_sm == 0) ctas_per_sm = 3; }
     const int fp64 = p->params.precision == 1;
-    const int mode = p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0;
+    const int mode = (p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0) | (p->params.pairs ? kModePairs : 0);
     // The variant with this precision and warp count whose register budget
     // admits the requested CTAs per SM (the largest one not above it).
     int best = -1, best_occ = 0;
@@ -1416,7 +1485,7 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
 {
     if (!plan || !lr || !hr || !shortlists) return RLJSDE_ERR_INVALID_ARG;
     if (plan->n_images != 1 || plan->direct || plan->onthefly || plan->params.precision != 0 || plan->kind != 0 ||
-        plan->params.layout != RLJSDE_LAYOUT_THREE_QUARTER)
+        plan->params.layout != RLJSDE_LAYOUT_THREE_QUARTER || plan->params.pairs)
         return RLJSDE_ERR_UNSUPPORTED;
     if (lr_pitch < (size_t)plan->lr_w[0] || hr_pitch < (size_t)(2 * plan->lr_w[0])) return RLJSDE_ERR_INVALID_ARG;
     if ((sel == nullptr) != (dc == nullptr)) return RLJSDE_ERR_INVALID_ARG;

@@ -143,7 +143,11 @@ void build_tables(const uint8_t *key, const double *w, const Cd *r32, uint32_t s
 
 inline double inv_or_zero(double num, double den) { return den > 1e-300 ? num / den : 0.0; }
 
-void build_record64(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap,
+// Conjugate-pair update: the argmax sees only k <= -k (linear order); the
+// other member of each pair gets q/D = 0.
+inline bool pair_hidden(bool pairs, int k) { return pairs && ((-(k / kW)) & 31) * kW + ((-(k % kW)) & 31) < k; }
+
+void build_record64(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap, bool pairs,
                     const std::vector<double> &q, Record<double> *rec)
 {
     static thread_local Tables T;
@@ -159,14 +163,14 @@ void build_record64(const uint8_t *key, const double *w, const Cd *r32, uint32_t
             for (int a = 0; a < 2; ++a)
                 for (int b = 0; b < 2; ++b) {
                     int k = (k1 + 16 * a) * kW + k2 + 16 * b;
-                    v[2 * a + b] = inv_or_zero(q[k], T.D[k]);
+                    v[2 * a + b] = pair_hidden(pairs, k) ? 0.0 : inv_or_zero(q[k], T.D[k]);
                 }
             rec->qD[k1 * 16 + k2] = {v[0], v[1], v[2], v[3]};
         }
     std::memcpy(rec->types, key, 256);
 }
 
-void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap,
+void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap, bool pairs,
                     const std::vector<double> &q, RecordF32 *rec, RecordShortF32 *sh)
 {
     static thread_local Tables T;
@@ -200,7 +204,7 @@ void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t
                 for (int b = 0; b < 2; ++b)
                     for (int e = 0; e < 2; ++e) {
                         int k = (2 * j + e + 16 * a) * kW + k2 + 16 * b;
-                        v[2 * b + e] = (float)inv_or_zero(q[k], T.D[k]);
+                        v[2 * b + e] = pair_hidden(pairs, k) ? 0.f : (float)inv_or_zero(q[k], T.D[k]);
                     }
             }
     std::memcpy(rec->types, key, 256);
@@ -238,6 +242,7 @@ int check_params(const rljsde_params *p)
     if (p->path < 0 || p->path > 3) return RLJSDE_ERR_INVALID_ARG;
     if (p->layout != RLJSDE_LAYOUT_THREE_QUARTER && p->layout != RLJSDE_LAYOUT_APERTURE)
         return RLJSDE_ERR_INVALID_ARG;
+    if (p->pairs != 0 && p->pairs != 1) return RLJSDE_ERR_INVALID_ARG;
     if ((p->path == 2 || p->path == 3) && p->precision != 0) return RLJSDE_ERR_UNSUPPORTED;
     return RLJSDE_OK;
 }
@@ -459,10 +464,11 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             for (int t = 0; t < p->n_tables; ++t) {
                 const uint8_t *key = (const uint8_t *)keys[t].data();
                 if (prm->precision)
-                    build_record64(key, w64, r32, slot_ap, p->q,
+                    build_record64(key, w64, r32, slot_ap, prm->pairs != 0, p->q,
                                    (Record<double> *)(host.data() + p->record_bytes * t));
                 else
-                    build_record32(key, w64, r32, slot_ap, p->q, (RecordF32 *)(host.data() + p->record_bytes * t),
+                    build_record32(key, w64, r32, slot_ap, prm->pairs != 0, p->q,
+                                   (RecordF32 *)(host.data() + p->record_bytes * t),
                                    (RecordShortF32 *)(host_short.data() + sizeof(RecordShortF32) * t));
             }
             st = upload(&p->d_records, host.data(), host.size());
@@ -512,6 +518,7 @@ int rljsde_default_params(rljsde_params *p)
     p->precision = 0;
     p->path = 0;
     p->layout = RLJSDE_LAYOUT_THREE_QUARTER;
+    p->pairs = 0;
     return RLJSDE_OK;
 }
 

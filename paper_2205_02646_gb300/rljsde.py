@@ -28,11 +28,12 @@ class RljsdeError(RuntimeError):
 
 class Params(ctypes.Structure):
     """``rljsde_params``: B, W, nu_max, gamma_odc, rho_decay, q_mode, q_table,
-    precision, path, layout (see the header for meanings and defaults)."""
+    precision, path, layout, pairs (see the header for meanings and defaults)."""
     _fields_ = [("block", ctypes.c_int), ("window", ctypes.c_int), ("nu_max", ctypes.c_int),
                 ("gamma_odc", ctypes.c_double), ("rho_decay", ctypes.c_double),
                 ("q_mode", ctypes.c_int), ("q_table", ctypes.POINTER(ctypes.c_double)),
-                ("precision", ctypes.c_int), ("path", ctypes.c_int), ("layout", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("path", ctypes.c_int), ("layout", ctypes.c_int),
+                ("pairs", ctypes.c_int)]
 
 
 LAYOUT_THREE_QUARTER = 0   # mask code = opaque sub-pixel 2 * dy + dx
