@@ -353,7 +353,8 @@ def run_learned(args):
     f, mask, y = synth.workload("rljsde_4096x3072_t4")
     tiles = [synth.recurrent_mask(256, 256, 4, 1000 + t) for t in range(15)]
     tiles.append(np.ascontiguousarray(np.tile(mask[:4, :4], (64, 64))))
-    data = proposal.make_dataset(args.train_images, tiles=tiles, nu_max=args.nu_max, seed=1)
+    data = proposal.make_dataset(args.train_images, blocks_per_image=args.blocks_per_image, tiles=tiles,
+                                 nu_max=args.nu_max, seed=1)
     held = proposal.make_dataset(16, tiles=tiles, nu_max=args.nu_max, seed=2)
     t_data = time.time() - t0
     net = rljsde.Net(seed=5)
@@ -418,7 +419,8 @@ def run_learned(args):
     best = max(ok, key=lambda q: q["mp_per_s"]) if ok else None
     line = {"study": "learned_proposal", "workload": "rljsde_4096x3072_t4", "nu_max": args.nu_max,
             "plain_mp_per_s": mp / (ms_plain / 1e3), "plain_psnr": psnr_plain,
-            "train": {"images": args.train_images, "samples": args.train_images * 256, "epochs": args.epochs,
+            "train": {"images": args.train_images, "samples": args.train_images * args.blocks_per_image,
+                      "image_size": 512, "epochs": args.epochs,
                       "data_s": t_data, "train_s": t_train, "loss_first": losses[0], "loss_last": losses[-1],
                       "heldout_recall_at_64": rec},
             "missing_quantiles": {"p10": float(np.quantile(missing, 0.1)), "p50": float(np.quantile(missing, 0.5)),
@@ -582,7 +584,8 @@ def main():
     ap.add_argument("--study", default=None,
                     choices=[None, "precision", "learned-launch", "random-mask", "layouts", "pairs"])
     ap.add_argument("--sample", type=int, default=3072)
-    ap.add_argument("--train-images", type=int, default=2000)
+    ap.add_argument("--train-images", type=int, default=20000)
+    ap.add_argument("--blocks-per-image", type=int, default=32)
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=2e-3)
     args = ap.parse_args()

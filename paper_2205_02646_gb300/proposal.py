@@ -62,13 +62,13 @@ def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu
         f = synth.image_torch(size, size, n_sin, n_edges, seed * 100003 + i, 0.005, device)
         y = synth.measure_torch(f, masks_d[t]).float().contiguous()
         plans[t].reconstruct_trace(y, hr, sel, dc)
-        tg, nu_t = labels_from_trace(sel.view(nb, nu_max), dc.view(nb, nu_max, 2), nu_max)
         pick = torch.randperm(nb, generator=g, device=device)[:blocks_per_image]
+        tg, nu_t = labels_from_trace(sel.view(nb, nu_max)[pick], dc.view(nb, nu_max, 2)[pick], nu_max)
         blk = torch.stack([pick // nb_side, pick % nb_side], 1).int().contiguous()
         xs.append(rljsde.Net.patches(y, masks_d[t], blk))
         bs.append(blk)
-        ts.append(tg[pick])
-        ns.append(nu_t[pick])
+        ts.append(tg)
+        ns.append(nu_t)
     for p in plans:
         p.check()
     return torch.cat(xs), torch.cat(bs), torch.cat(ts), torch.cat(ns), (lr, lr)
