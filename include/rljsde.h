@@ -238,8 +238,10 @@ int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, 
                       float *z_out, void *stream);
 /* Device workspace bytes rljsde_propose needs for a single-image plan. */
 size_t rljsde_propose_workspace(const rljsde_plan_t *plan);
-/* Run the network over the whole image (convolutions, then the head as one
- * BF16 GEMM per chunk of blocks) and write one rljsde_shortlist per block
+/* Run the network over the whole image (conv1 on the CUDA cores, conv2 and
+ * conv3 on the tensor cores with bfloat16 input taps and FP32 accumulation,
+ * then the head as one BF16 GEMM per chunk of blocks; a tensor-core wait
+ * that gives up is reported by rljsde_check) and write one rljsde_shortlist per block
  * (device, n_blocks entries, block order bi * (2 lr_w / 4) + bj).
  * Asynchronous; the caller owns shortlists and workspace.  The network reads
  * opaque-sub-pixel codes: plans of the three-quarter layout only. */

@@ -7,7 +7,9 @@
 // network is unsure of run the full loop.
 //
 // Network (weights stored FP32 for training and used rounded to bfloat16,
-// activations and accumulation in FP32):
+// activations and accumulation in FP32; in the whole-image pass conv2 and
+// conv3 run on the tensor cores and read their input taps rounded to
+// bfloat16, and the head reads its features rounded to bfloat16):
 //   input 5 channels on the L-pixel grid: y / 3 and the one-hot code
 //   conv1 5->32 3x3 s1, conv2 32->32 3x3 s2 (target-block grid),
 //   conv3 32->32 3x3 s1, all zero-padded, ReLU; activations outside the
@@ -507,6 +509,183 @@ __global__ void head_features_f32_kernel(const float *a3, int nbh, int nbw, long
     }
 }
 
+// ------------------------------------------- tensor-core convolution --
+// conv2 / conv3 of the whole-image pass as an implicit GEMM on the 5th-gen
+// tensor cores: D[128 output positions][32 channels] = A[128][288] x B[288][32]
+// with K index ci * 9 + t (the weight layout), A = the bfloat16-rounded input
+// taps (zero outside the input), B = the bfloat16 weights, FP32 accumulation
+// in tensor memory.  One CTA of 128 threads walks tiles of 128 positions:
+// every thread gathers its position's 288 taps into shared memory, one thread
+// issues the 18 K = 16 MMAs (tcgen05.mma kind::f16, cta_group::1) and
+// commits them to an mbarrier, then each warp reads its 32 accumulator rows
+// back (tcgen05.ld 32x32b) and applies bias and ReLU.  Every output of the
+// whole-image pass lies inside the image, so no validity mask is needed.
+//
+// Shared-memory operands use the no-swizzle K-major layout: 8 x 16-byte core
+// matrices, the 8-element K groups of one 8-row group contiguous (leading
+// byte offset 128), 8-row groups 36 x 128 bytes apart (stride byte offset).
+namespace tc {
+constexpr int kM = 128;                              // output positions per tile (MMA M)
+constexpr int kKTot = 9 * kC;                        // 288
+constexpr uint32_t kLBO = 128;                       // next 8-element K group
+constexpr uint32_t kSBO = (kKTot / 8) * 128;         // next 8-row group: 4608
+constexpr uint32_t kABytes = (kM / 8) * kSBO;        // 73,728
+constexpr uint32_t kBBytes = (kC / 8) * kSBO;        // 18,432
+constexpr uint32_t kSmem = kABytes + kBBytes + 16;   // + mbarrier and tensor-memory address
+static_assert(kSmem <= 227 * 1024, "tile operands must fit in shared memory");
+// D FP32, A and B BF16, both K-major, N = 32, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
+                            ((uint32_t)(kM >> 4) << 24);
+constexpr uint32_t kTmemCols = 32;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
+           (1ull << 46);                              // descriptor version 1, no swizzle
+}
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the mbarrier; give up after about 2 s.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = now_ns();
+    for (uint32_t i = 0; i < (1u << 24); ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((i & 255) == 255 && now_ns() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+
+// in: [32][hi][wi] FP32; out: [32][ho][wo] FP32; w: [32][32][9] (bfloat16-rounded), b: [32].
+__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const float *w, const float *bias,
+                                                         float *out, int hi, int wi, int ho, int wo, int stride,
+                                                         int *status)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *A = sm, *B = sm + kABytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kABytes + kBBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kABytes + kBBytes + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // B: weights as bfloat16 in the core-matrix layout (row = output channel)
+    for (int i = tid; i < kC * (kKTot / 8); i += blockDim.x) {
+        const int co = i / (kKTot / 8), q = i % (kKTot / 8);
+        const float *src = w + co * kKTot + 8 * q;
+        uint4 v;
+        v.x = pack_bf16(src[0], src[1]); v.y = pack_bf16(src[2], src[3]);
+        v.z = pack_bf16(src[4], src[5]); v.w = pack_bf16(src[6], src[7]);
+        *reinterpret_cast<uint4 *>(B + (co >> 3) * kSBO + q * kLBO + (co & 7) * 16) = v;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t a_addr = saddr(A), b_addr = saddr(B), bar_addr = saddr(bar);
+
+    const long long total = (long long)ho * wo;
+    const long long n_tiles = (total + kM - 1) / kM;
+    uint32_t parity = 0;
+    bool failed = false;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // A: this thread's position, its 288 taps as bfloat16
+        const long long pos = tile * kM + tid;
+        const bool valid = pos < total;
+        const int oy = valid ? (int)(pos / wo) : 0, ox = valid ? (int)(pos % wo) : 0;
+        unsigned char *arow = A + (tid >> 3) * kSBO + (tid & 7) * 16;
+#pragma unroll 4
+        for (int q = 0; q < kKTot / 8; ++q) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int kk = 8 * q + e, ci = kk / 9, t = kk % 9;
+                const int y = stride * oy + t / 3 - 1, x = stride * ox + t % 3 - 1;
+                v[e] = (valid && y >= 0 && y < hi && x >= 0 && x < wi) ? in[((long long)ci * hi + y) * wi + x] : 0.f;
+            }
+            uint4 u;
+            u.x = pack_bf16(v[0], v[1]); u.y = pack_bf16(v[2], v[3]);
+            u.z = pack_bf16(v[4], v[5]); u.w = pack_bf16(v[6], v[7]);
+            *reinterpret_cast<uint4 *>(arow + q * kLBO) = u;
+        }
+        // generic-proxy writes -> tensor-core (async proxy) reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < kKTot / 16; ++j) {
+                const uint64_t da = desc(a_addr + j * 2 * kLBO), db = desc(b_addr + j * 2 * kLBO);
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                             ::"r"(tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(j)
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(bar_addr)
+                         : "memory");
+        }
+        const bool ok = wait_phase(bar_addr, parity);
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // this warp's 32 accumulator rows (TMEM lanes 32 warp ..), 32 columns each
+        uint32_t r[32];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(tmem + ((uint32_t)(warp * 32) << 16))
+                     : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (valid) {
+#pragma unroll
+            for (int co = 0; co < kC; ++co)
+                out[(long long)co * total + pos] = fmaxf(__uint_as_float(r[co]) + bias[co], 0.f);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        (void)lane;
+    }
+    if (failed) {
+        if (tid == 0) atomicOr(status, 2);
+        wait_phase(bar_addr, parity);                 // let an MMA still in flight finish
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+}  // namespace tc
+
 // Fixed scratch of rljsde_propose_noalloc: part of the library image, so
 // every device that loads the library holds it until the process exits.
 constexpr size_t kStaticScratchBytes = 32u << 20;
@@ -590,6 +769,20 @@ int grid_for(long long work, int threads)
 {
     long long g = (work + threads - 1) / threads;
     return (int)(g < 1 ? 1 : (g > 65535 * 16 ? 65535 * 16 : g));
+}
+
+// conv2 / conv3 of a whole image on the tensor cores (tc::conv_tc_kernel).
+int conv_tc(const float *in, const float *w, const float *b, float *out, int hi, int wi, int ho, int wo, int stride,
+            int sm_count, int *status, cudaStream_t s)
+{
+    if (cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem) !=
+        cudaSuccess)
+        return RLJSDE_ERR_CUDA;
+    const long long tiles = ((long long)ho * wo + tc::kM - 1) / tc::kM;
+    const long long cap = 2ll * (sm_count > 0 ? sm_count : 1);      // two 92 KB CTAs per SM
+    const int grid = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
+    tc::conv_tc_kernel<<<grid, 128, tc::kSmem, s>>>(in, w, b, out, hi, wi, ho, wo, stride, status);
+    return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
 
 void refresh_bf16(rljsde_net *n, cudaStream_t s)
@@ -820,10 +1013,11 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
     image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
     ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
     conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
-    ConvGeom g2{1, kC, lr_h, lr_w, nbh, nbw, 2, 2, nullptr, lr_h, lr_w};
-    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a1, r + kW2, b + kB2, a2, g2);
-    ConvGeom g3{1, kC, nbh, nbw, nbh, nbw, 1, 2, nullptr, lr_h, lr_w};
-    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a2, r + kW3, b + kB3, a3, g3);
+    // conv2 (stride 2, onto the block grid) and conv3 on the tensor cores
+    int cst = conv_tc(a1, r + kW2, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, plan->sm_count, plan->d_status, s);
+    if (cst == RLJSDE_OK)
+        cst = conv_tc(a2, r + kW3, b + kB3, a3, nbh, nbw, nbh, nbw, 1, plan->sm_count, plan->d_status, s);
+    if (cst != RLJSDE_OK) return cst;
     if (cublasSetStream(net->blas, s) != CUBLAS_STATUS_SUCCESS) return RLJSDE_ERR_CUDA;
     const float one = 1.f, zero = 0.f;
     for (size_t b0 = 0; b0 < nb; b0 += chunk) {
@@ -872,10 +1066,11 @@ int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, c
     image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
     ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
     conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
-    ConvGeom g2{1, kC, lr_h, lr_w, nbh, nbw, 2, 2, nullptr, lr_h, lr_w};
-    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a1, r + kW2, b + kB2, a2, g2);
-    ConvGeom g3{1, kC, nbh, nbw, nbh, nbw, 1, 2, nullptr, lr_h, lr_w};
-    conv_fwd_kernel<kC><<<gcap((long long)nb, 128), 128, 0, s>>>(a2, r + kW3, b + kB3, a3, g3);
+    // conv2 (stride 2, onto the block grid) and conv3 on the tensor cores
+    int cst = conv_tc(a1, r + kW2, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, plan->sm_count, plan->d_status, s);
+    if (cst == RLJSDE_OK)
+        cst = conv_tc(a2, r + kW3, b + kB3, a3, nbh, nbw, nbh, nbw, 1, plan->sm_count, plan->d_status, s);
+    if (cst != RLJSDE_OK) return cst;
     for (size_t b0 = 0; b0 < nb; b0 += chunk) {
         const int m = (int)(nb - b0 < chunk ? nb - b0 : chunk);
         head_features_f32_kernel<<<gcap((long long)m * kHeadIn, 256), 256, 0, s>>>(a3, nbh, nbw, (long long)b0, m, f);

@@ -82,6 +82,41 @@ def test_whole_image_shortlists_match_patch_logits(rl):
         assert abs(nu_frac[bi * nbw + bj] - zb[1024]) < 0.05 * (1 + abs(zb[1024]))
 
 
+def test_tensor_core_convolutions_match_fp64_features(rl):
+    """conv2 and conv3 of the whole-image pass run on the tensor cores
+    (tcgen05, bfloat16 taps, FP32 accumulation in tensor memory).  A head
+    whose iteration row selects one feature turns each block's iteration
+    output into that feature, which must equal the FP64 reference's up to
+    bfloat16 rounding of the activations."""
+    import torch
+    f, mask, y = _image(h=40, w=56, seed=8)
+    net = rl.Net(seed=11)
+    base = cnn_ref.unflatten(net.get_params())
+    plan = rl.Plan(mask, rl.default_params(nu_max=10))
+    lr = torch.from_numpy(y).cuda()
+    nbh, nbw = mask.shape[0] // 2, mask.shape[1] // 2
+    rng = np.random.default_rng(4)
+    blocks = [(0, 0), (0, nbw - 1), (nbh - 1, 0), (nbh - 1, nbw - 1), (1, 2)] + \
+        [tuple(b) for b in rng.integers(0, [nbh, nbw], (20, 2))]
+    ref = {}
+    for bi, bj in blocks:
+        x, origin = cnn_ref.patch(y, mask, bi, bj)
+        ref[(bi, bj)] = cnn_ref.forward(base, x, origin, mask.shape)[1][-1]      # the 288 head features
+    scale = max(np.abs(v).max() for v in ref.values())
+    assert scale > 0.1
+    for fi in (0, 4, 148, 287):                                                # channel 0 / 16 / 31, several taps
+        p = {k: v.copy() for k, v in base.items()}
+        p["head.w"][:] = 0.0
+        p["head.w"][1024, fi] = 1.0
+        p["head.b"][:] = 0.0
+        net.set_params(cnn_ref.flatten(p).astype(np.float32))
+        _, _, nu_frac = rl.shortlist_view(plan.propose(net, lr), nbh * nbw)
+        plan.check()
+        for (bi, bj), fr in ref.items():
+            got = float(nu_frac[bi * nbw + bj])
+            assert abs(got - fr[fi]) <= 0.02 * scale + 0.01 * abs(fr[fi]), (fi, bi, bj, got, fr[fi])
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_restricted_loop_matches_oracle_with_q_zero_outside(rl, seed):
     import torch
