@@ -40,6 +40,13 @@ def flops_per_block(nu: int) -> int:
     return dft + first + (nu - 1) * per_iter + nu * scalar
 
 
+def phase_flops(nu: int):
+    """(initial projection + first iteration, the nu - 1 later iterations)
+    of flops_per_block."""
+    dft = 256 * 16 * 4 + 4 * 256 * 8 * 8 + 4 * 256 * 2
+    return dft + 256 * 64 + 64, (nu - 1) * (256 * 96 + 64)
+
+
 def fp32_peak_tflops() -> float:
     return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -104,30 +111,39 @@ def kernel_traffic(workload: str):
     return None
 
 
-def cpu_oracle_sample(y, mask, nu, budget_s=15.0, seed=0):
-    """Time the FP64 direct oracle on a bounded random sample of blocks."""
+def oracle_band(y, mask, max_blocks=65536, band=0):
+    """The image, or a band of whole block rows of it (about max_blocks
+    blocks, the band-th one cycling down the image) for large workloads."""
+    nbh, nbw = mask.shape[0] // 2, mask.shape[1] // 2
+    rows = max(1, min(nbh, max_blocks // nbw))
+    if rows == nbh:
+        return y, mask
+    r0 = (band * rows) % (nbh - rows + 1)
+    sl = slice(2 * r0, 2 * (r0 + rows))
+    return np.ascontiguousarray(y[sl]), np.ascontiguousarray(mask[sl])
+
+
+def cpu_oracle_sample(y, mask, nu, seed=0):
+    """Time the FP64 recurrent oracle (tables once per local mask, Eqs. 12-17)
+    over every block of the workload (or a band of ~65k blocks) on all host
+    cores."""
     import oracle
-    nb = (mask.shape[0] // 2) * (mask.shape[1] // 2)
-    rng = np.random.default_rng(seed)
-    params = oracle.Params(nu_max=nu)
     threads = os.cpu_count() or 1
-    y64 = np.asarray(y, np.float64)
-    probe = rng.choice(nb, min(nb, 2 * threads), replace=False)
+    yb, mb = oracle_band(np.asarray(y, np.float64), mask)
+    params = oracle.Params(nu_max=nu)
     t0 = time.perf_counter()
-    oracle.reconstruct(y64, mask, params, blocks=probe, n_threads=threads)
-    t_probe = time.perf_counter() - t0
-    per_block = t_probe / len(probe)
-    n = int(min(nb, max(len(probe), (budget_s - t_probe) / max(per_block, 1e-9))))
-    blocks = rng.choice(nb, n, replace=False)
-    t0 = time.perf_counter()
-    oracle.reconstruct(y64, mask, params, blocks=blocks, n_threads=threads)
+    oracle.reconstruct(yb, mb, params, recurrent=True, n_threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": n * 16 / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d random 4x4 blocks of the workload (%.1f s, FP64 direct L-JSDE, %d threads)"
-                      % (n, dt, threads)}, n, dt
+    n = (mb.shape[0] // 2) * (mb.shape[1] // 2)
+    return {"value": 4 * mb.size / 1e6 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d blocks (%s of the workload, %.1f s), FP64 recurrent RL-JSDE oracle, %d threads"
+                      % (n, "all" if mb.shape == mask.shape else "a band", dt, threads)}, n, dt
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step runs the FP64 recurrent
+    oracle over the workload (or a band of ~65k blocks of it) on all host
+    cores."""
     from paper_2205_02646_gb300 import synth
     if rank != 0:
         return
@@ -135,29 +151,28 @@ def run_reference(args, rank, world):
     oracle.load()
     f, mask, y = synth.workload(args.workload)
     nu = args.nu_max
-    nb = (mask.shape[0] // 2) * (mask.shape[1] // 2)
     threads = os.cpu_count() or 1
-    rng = np.random.default_rng(1)
     params = oracle.Params(nu_max=nu)
     y64 = y.astype(np.float64)
-    per_step = max(threads, args.ref_blocks)
-    for _ in range(args.warmup):
-        oracle.reconstruct(y64, mask, params, blocks=rng.choice(nb, threads, replace=False), n_threads=threads)
-    total = 0.0
-    for _ in range(args.steps):
-        bl = rng.choice(nb, per_step, replace=False)
+    small_y, small_m = np.ascontiguousarray(y64[:16, :16]), np.ascontiguousarray(mask[:16, :16])
+    for _ in range(args.warmup):                                  # code and page warm-up on a 16x16 crop
+        oracle.reconstruct(small_y, small_m, params, recurrent=True, n_threads=threads)
+    total, mp, n_blocks = 0.0, 0.0, 0
+    for i in range(args.steps):
+        yb, mb = oracle_band(y64, mask, band=i)
         t0 = time.perf_counter()
-        oracle.reconstruct(y64, mask, params, blocks=bl, n_threads=threads)
+        oracle.reconstruct(yb, mb, params, recurrent=True, n_threads=threads)
         total += time.perf_counter() - t0
-    mp = args.steps * per_step * 16 / 1e6
+        mp += 4 * mb.size / 1e6
+        n_blocks = (mb.shape[0] // 2) * (mb.shape[1] // 2)
     val = mp / total
+    sample = "%d blocks per step (%s of the workload), FP64 recurrent RL-JSDE oracle" % (
+        n_blocks, "all" if n_blocks == (mask.shape[0] // 2) * (mask.shape[1] // 2) else "a band")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "nu_max": nu,
-                                            "blocks_per_step": per_step},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "%d random 4x4 blocks per step, FP64 direct L-JSDE" % per_step},
+            "data": "synthetic", "config": {"workload": args.workload, "nu_max": nu, "blocks_per_step": n_blocks},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -550,6 +565,38 @@ def run_pairs(args):
     print(json.dumps(out), flush=True)
 
 
+def run_cpu_baseline(args):
+    """The FP64 oracle on the host cores, as it stands: the recurrent CPU
+    form over every block of the 1024x1024 image (tables once per local mask,
+    Eqs. 12-17) with all cores and with one core, and the direct form on a
+    block sample, beside the paper's Table II CPU numbers (context only)."""
+    import oracle
+    from paper_2205_02646_gb300 import synth
+    f, mask, y = synth.workload("rljsde_1024x1024")
+    y = y.astype(np.float64)
+    p = oracle.Params(nu_max=args.nu_max)
+    cores = os.cpu_count() or 1
+    out = {"study": "cpu-baseline", "workload": "rljsde_1024x1024", "nu_max": args.nu_max, "cores": cores,
+           "tables": oracle.count_local_masks(mask, p)[0]}
+    mp = 4 * mask.size / 1e6
+    for name, thr in (("recurrent_all_cores", cores), ("recurrent_one_core", 1)):
+        t0 = time.perf_counter()
+        oracle.reconstruct(y, mask, p, recurrent=True, n_threads=thr)
+        dt = time.perf_counter() - t0
+        out[name] = {"threads": thr, "s": dt, "mp_per_s": mp / dt}
+    rng = np.random.default_rng(0)
+    nb = (mask.shape[0] // 2) * (mask.shape[1] // 2)
+    for name, thr, n in (("direct_all_cores", cores, 256), ("direct_one_core", 1, 32)):
+        blocks = rng.choice(nb, n, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.reconstruct(y, mask, p, blocks=blocks, n_threads=thr)
+        dt = time.perf_counter() - t0
+        out[name] = {"threads": thr, "blocks": n, "s": dt, "mp_per_s": n * 16 / 1e6 / dt}
+    out["paper_table2_cpu_one_core"] = {"rl_jsde_mp_per_s": 1.44 / 86, "l_jsde_mp_per_s": 1.44 / 1823,
+                                        "hardware": "Intel Xeon E3-1245v5, 1 core, 1200x1200, period 32 px"}
+    print(json.dumps(out), flush=True)
+
+
 def run_learned_launch(args):
     """The learned inference path (whole-image proposal, shortlist loop,
     fallback pass) run twice with a seeded untrained network: the launch
@@ -579,10 +626,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rljsde_1024x1024")
     ap.add_argument("--nu-max", type=int, default=100)
-    ap.add_argument("--ref-blocks", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", default=None,
-                    choices=[None, "precision", "learned-launch", "random-mask", "layouts", "pairs"])
+                    choices=[None, "precision", "learned-launch", "random-mask", "layouts", "pairs",
+                             "cpu-baseline"])
     ap.add_argument("--sample", type=int, default=3072)
     ap.add_argument("--train-images", type=int, default=20000)
     ap.add_argument("--blocks-per-image", type=int, default=32)
@@ -611,6 +658,9 @@ def main():
         return
     if args.study == "pairs":
         run_pairs(args)
+        return
+    if args.study == "cpu-baseline":
+        run_cpu_baseline(args)
         return
     if args.workload == "rljsde_learned":
         run_learned(args)
@@ -709,6 +759,30 @@ def main():
     mean_s = total_ms / args.steps / 1e3
     achieved = flops / mean_s / 1e12
     peak = fp32_peak_tflops()
+
+    # Per-phase split (outside the timed region): the same image with one
+    # iteration per block times the initial projection and first iteration;
+    # the difference to the full run is the nu_max - 1 later iterations.
+    plan1 = rljsde.Plan(mask, rljsde.default_params(nu_max=1))
+    plan1.reconstruct(lr, hr, stream)
+    torch.cuda.synchronize()
+    t1 = 0.0
+    for i in range(5):
+        flush.fill_(float(i))
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        plan1.reconstruct(lr, hr, stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        t1 += a_.elapsed_time(b_) / 5
+    plan1.check(stream)
+    plan1.close()
+    f_init, f_loop = phase_flops(args.nu_max)
+    t_loop = max(total_ms / args.steps - t1, 1e-6)
+    phases = {"init": {"ms": t1, "tflops": f_init * n_blocks / (t1 / 1e3) / 1e12},
+              "loop": {"ms": t_loop, "tflops": f_loop * n_blocks / (t_loop / 1e3) / 1e12}}
+    for ph in phases.values():
+        ph["frac"] = ph["tflops"] / peak
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -724,7 +798,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": kernel_traffic(args.workload),
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (derived)",
-                     "flops_per_block": flops_per_block(args.nu_max)},
+                     "flops_per_block": flops_per_block(args.nu_max), "phases": phases},
         "clocks": clk,
     }
     if cpu_base is not None:
