@@ -512,7 +512,8 @@ __global__ void head_features_f32_kernel(const float *a3, int nbh, int nbw, long
 // ------------------------------------------- tensor-core convolution --
 // conv2 / conv3 of the whole-image pass as an implicit GEMM on the 5th-gen
 // tensor cores: D[128 output positions][32 channels] = A[128][288] x B[288][32]
-// with K index ci * 9 + t (the weight layout), A = the bfloat16-rounded input
+// with K index t * 32 + ci (tap-major, so each 8-wide K group is one tap of 8
+// consecutive input channels), A = the bfloat16-rounded input
 // taps (zero outside the input), B = the bfloat16 weights, FP32 accumulation
 // in tensor memory.  One CTA of 128 threads walks tiles of 128 positions:
 // every thread gathers its position's 288 taps into shared memory, one thread
@@ -588,13 +589,15 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kABytes + kBBytes + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // B: weights as bfloat16 in the core-matrix layout (row = output channel)
+    // B: weights as bfloat16 in the core-matrix layout (row = output channel,
+    // K group q = tap q / 4, input channels 8 (q % 4) ..)
     for (int i = tid; i < kC * (kKTot / 8); i += blockDim.x) {
         const int co = i / (kKTot / 8), q = i % (kKTot / 8);
-        const float *src = w + co * kKTot + 8 * q;
+        const int t = q >> 2, ci0 = (q & 3) * 8;
+        const float *src = w + (co * kC + ci0) * 9 + t;          // w[co][ci][t]
         uint4 v;
-        v.x = pack_bf16(src[0], src[1]); v.y = pack_bf16(src[2], src[3]);
-        v.z = pack_bf16(src[4], src[5]); v.w = pack_bf16(src[6], src[7]);
+        v.x = pack_bf16(src[0], src[9]); v.y = pack_bf16(src[18], src[27]);
+        v.z = pack_bf16(src[36], src[45]); v.w = pack_bf16(src[54], src[63]);
         *reinterpret_cast<uint4 *>(B + (co >> 3) * kSBO + q * kLBO + (co & 7) * 16) = v;
     }
     if (tid == 0) {
@@ -623,19 +626,22 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
         const bool valid = pos < total;
         const int oy = valid ? (int)(pos / wo) : 0, ox = valid ? (int)(pos % wo) : 0;
         unsigned char *arow = A + (tid >> 3) * kSBO + (tid & 7) * 16;
-#pragma unroll 4
-        for (int q = 0; q < kKTot / 8; ++q) {
-            float v[8];
+        const long long plane = (long long)hi * wi;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int kk = 8 * q + e, ci = kk / 9, t = kk % 9;
-                const int y = stride * oy + t / 3 - 1, x = stride * ox + t % 3 - 1;
-                v[e] = (valid && y >= 0 && y < hi && x >= 0 && x < wi) ? in[((long long)ci * hi + y) * wi + x] : 0.f;
+        for (int t = 0; t < 9; ++t) {
+            const int y = stride * oy + t / 3 - 1, x = stride * ox + t % 3 - 1;
+            const bool inb = valid && y >= 0 && y < hi && x >= 0 && x < wi;
+            const float *src = in + (inb ? (long long)y * wi + x : 0);
+#pragma unroll
+            for (int cg = 0; cg < 4; ++cg) {
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = inb ? src[(cg * 8 + e) * plane] : 0.f;
+                uint4 u;
+                u.x = pack_bf16(v[0], v[1]); u.y = pack_bf16(v[2], v[3]);
+                u.z = pack_bf16(v[4], v[5]); u.w = pack_bf16(v[6], v[7]);
+                *reinterpret_cast<uint4 *>(arow + (t * 4 + cg) * kLBO) = u;
             }
-            uint4 u;
-            u.x = pack_bf16(v[0], v[1]); u.y = pack_bf16(v[2], v[3]);
-            u.z = pack_bf16(v[4], v[5]); u.w = pack_bf16(v[6], v[7]);
-            *reinterpret_cast<uint4 *>(arow + q * kLBO) = u;
         }
         // generic-proxy writes -> tensor-core (async proxy) reads
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
