@@ -108,8 +108,9 @@ int rljsde_default_params(rljsde_params *p);
 typedef struct rljsde_plan rljsde_plan_t;   /* opaque; owns all its device memory */
 
 /*
- * Build a plan for one image size and sensor mask (Sec. IV: "pre-computed and
- * re-used for all model windows with the same measurement matrix").
+ * Build a plan for one image size and sensor mask (Sec. IV: the tables of a
+ * local measurement matrix are computed once and shared by every model
+ * window that has that matrix).
  *   mask: host, lr_h x lr_w codes (0..3, or 0..15 for aperture layouts),
  *         row-major, contiguous.
  *   lr_h, lr_w: even, 4 .. 32768.

@@ -25,8 +25,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   pinned: residual and model stay exactly real, E_w non-increasing for
   gamma <= 1, identity measurement recovers conjugate-pair sparse signals
   exactly and equals two single updates per pair, direct == recurrent.
-* ``frequency_weight``   -- the paper gives no formula (Sec. IV only says q
-  prefers low frequencies): parity unpinned against the paper; the tests
+* ``frequency_weight``   -- the paper gives no formula (Sec. IV says only that q
+  favours low frequencies): parity unpinned against the paper; the tests
   check the stated reading's properties (1 at DC, symmetric, isotropic,
   non-increasing in |k|, zero only at (W/2, W/2)).
 * ``count_local_masks``  -- pinned: Table I (64 local masks for a 32-pixel
