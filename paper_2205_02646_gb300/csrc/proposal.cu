@@ -417,11 +417,31 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
             const uint32_t u = __float_as_uint(v[j]);
             key[j] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
         }
-        // Binary search on the key bits for the 64th largest key; stop early
-        // once exactly 64 keys reach the candidate (then they are the set).
-        uint32_t thr = 0;
+        // Bounds on the 64th largest key: at most the warp's largest key, at
+        // least the smallest of the 32 lanes' second-largest keys (those 64
+        // keys all reach it).  Its bits above the first bit where the two
+        // bounds differ are theirs, so the search starts below that bit.
+        uint32_t m1 = 0, m2 = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t k = key[j];
+            m2 = max(m2, min(m1, k));
+            m1 = max(m1, k);
+        }
+        uint32_t hi = m1, lo = m2;
+        for (int o = 16; o; o >>= 1) {
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        }
+        const uint32_t diff = hi ^ lo;
+        const int top = diff ? 31 - __clz(diff) : -1;          // highest differing bit
+        // Binary search on the remaining key bits for the 64th largest key;
+        // stop early once exactly 64 keys reach the candidate (then they are
+        // the set).
+        uint32_t thr = top >= 31 ? 0u : (hi & ~((2u << top) - 1u));
         bool exact = false;
-        for (int bit = 31; bit >= 0; --bit) {
+        if (top < 0) thr = hi;                                   // all candidates equal at the top
+        for (int bit = top; bit >= 0; --bit) {
             const uint32_t cand = thr | (1u << bit);
             int cnt = 0;
 #pragma unroll
@@ -448,7 +468,7 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
                 if (key[j] >= thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                if (key[j] < thr) rest += 1.f / (1.f + __expf(-v[j]));
+                if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-v[j]));
             for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
             if (lane == 0) {
                 sl.missing = rest;
@@ -483,7 +503,7 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
         }
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (key[j] < thr) rest += 1.f / (1.f + __expf(-v[j]));
+            if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-v[j]));
         for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
         if (lane == 0) {
             sl.missing = rest;
