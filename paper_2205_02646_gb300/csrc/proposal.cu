@@ -383,18 +383,44 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n,
 
 // ---------------------------------------------------- whole-image pass --
 // im2col of the head: f[b][c * 9 + t] (bf16) for block b = by * nbw + bx of a
-// chunk, from a3[c][nbh][nbw] with zero padding.
-__global__ void head_features_kernel(const float *a3, int nbh, int nbw, long long b0, int nb, __nv_bfloat16 *f)
+// chunk, from a3[c][nbh][nbw] with zero padding, for tiles of 32 consecutive
+// blocks per CTA: the 32 x 288
+// values are gathered with reads that run along the blocks of a tile
+// (coalesced), staged as bfloat16 in shared memory, and written out as one
+// contiguous 18 KB row range with 16-byte stores.
+constexpr int kFeatTile = 32;
+__global__ void __launch_bounds__(256) head_features_tile_kernel(const float *a3, int nbh, int nbw, long long b0,
+                                                                 int nb, __nv_bfloat16 *f)
 {
-    const long long total = (long long)nb * kHeadIn;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long b = b0 + i / kHeadIn;
-        const int j = (int)(i % kHeadIn), c = j / 9, t = j % 9;
-        const int by = (int)(b / nbw) + t / 3 - 1, bx = (int)(b % nbw) + t % 3 - 1;
-        float v = 0.f;
-        if (by >= 0 && by < nbh && bx >= 0 && bx < nbw) v = a3[((long long)c * nbh + by) * nbw + bx];
-        f[i] = __float2bfloat16_rn(v);
+    // blockDim.x must be 256 (8 threads per block of the tile)
+    // rows padded to 296 bfloat16 (592 bytes): bank groups of consecutive blocks differ
+    constexpr int kRow = kHeadIn + 8;
+    __shared__ __align__(16) __nv_bfloat16 tile[kFeatTile * kRow];
+    const int n_tiles = (nb + kFeatTile - 1) / kFeatTile;
+    for (int tl = blockIdx.x; tl < n_tiles; tl += gridDim.x) {
+        const int first = tl * kFeatTile;
+        const int n = nb - first < kFeatTile ? nb - first : kFeatTile;
+        // thread: block bt of the tile, features ct = ct0 + 8 i
+        const int bt = threadIdx.x % kFeatTile, ct0 = threadIdx.x / kFeatTile;
+        const long long b = b0 + first + bt;
+        const int by0 = (int)(b / nbw), bx0 = (int)(b - (long long)by0 * nbw);
+        const long long plane = (long long)nbh * nbw;
+#pragma unroll 4
+        for (int ct = ct0; ct < kHeadIn; ct += 256 / kFeatTile) {
+            const int c = ct / 9, t = ct - 9 * c;
+            const int by = by0 + t / 3 - 1, bx = bx0 + t % 3 - 1;
+            float v = 0.f;
+            if (bt < n && by >= 0 && by < nbh && bx >= 0 && bx < nbw) v = a3[c * plane + (long long)by * nbw + bx];
+            tile[bt * kRow + ct] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+        uint4 *dst = reinterpret_cast<uint4 *>(f + (long long)first * kHeadIn);
+        const int n16 = n * (kHeadIn * 2 / 16);         // 36 x 16 bytes per block
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) {
+            const int blk = i / (kHeadIn * 2 / 16), part = i - blk * (kHeadIn * 2 / 16);
+            dst[i] = reinterpret_cast<const uint4 *>(tile + blk * kRow)[part];
+        }
+        __syncthreads();
     }
 }
 
@@ -513,7 +539,7 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
 }
 
 // Head im2col for the no-allocation path: the same features as
-// head_features_kernel, rounded through bfloat16 but stored as float so the
+// head_features_tile_kernel, rounded through bfloat16 but stored as float so the
 // FP32 GEMM kernel multiplies exactly the operands the BF16 GEMM would.
 __global__ void head_features_f32_kernel(const float *a3, int nbh, int nbw, long long b0, int nb, float *f)
 {
@@ -1048,7 +1074,8 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
     const float one = 1.f, zero = 0.f;
     for (size_t b0 = 0; b0 < nb; b0 += chunk) {
         const int m = (int)(nb - b0 < chunk ? nb - b0 : chunk);
-        head_features_kernel<<<gcap((long long)m * kHeadIn, 256), 256, 0, s>>>(a3, nbh, nbw, (long long)b0, m, f16);
+        head_features_tile_kernel<<<gcap(((long long)m + kFeatTile - 1) / kFeatTile * 256, 256), 256, 0, s>>>(
+            a3, nbh, nbw, (long long)b0, m, f16);
         // z (row-major m x 1040) = f16 (m x 288) * Wh_pad^T: column-major z^T = Wh_pad * f16^T
         if (cublasGemmEx(net->blas, CUBLAS_OP_T, CUBLAS_OP_N, kOutPad, m, kHeadIn, &one, net->head16, CUDA_R_16BF,
                          kHeadIn, f16, CUDA_R_16BF, kHeadIn, &zero, z, CUDA_R_32F, kOutPad, CUBLAS_COMPUTE_32F,
