@@ -306,16 +306,24 @@ __device__ __forceinline__ void keep_best(T s, int k, T re, T im, T &bs, int &bk
 // index wins, as in the FP32 loop.
 template <typename T> __device__ __forceinline__ T key32(T s) { return (T)(float)s; }
 
-// Warp argmax over (score, index), ties to the lowest index.
+// Warp argmax over (score, index), ties to the lowest index, with two warp
+// reductions: the largest score (a non-negative binary32 value, so its bit
+// pattern orders like the value), then the smallest index among the lanes
+// holding it.  Every lane's score is a binary32 key (scores of the FP64
+// loop are rounded to binary32 first), so the conversion below is exact.
+__device__ __forceinline__ void warp_argmax_bits(const float s, int &bk, float &best)
+{
+    const unsigned bits = __float_as_uint(s);
+    const unsigned smax = __reduce_max_sync(0xffffffffu, bits);
+    bk = (int)__reduce_min_sync(0xffffffffu, bits == smax ? (unsigned)bk : 0xffffffffu);
+    best = __uint_as_float(smax);
+}
 template <typename T>
 __device__ __forceinline__ void warp_argmax(T &bs, int &bk)
 {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        const T os = __shfl_xor_sync(0xffffffffu, bs, m);
-        const int ok = __shfl_xor_sync(0xffffffffu, bk, m);
-        if (os > bs || (os == bs && ok < bk)) { bs = os; bk = ok; }
-    }
+    float best;
+    warp_argmax_bits((float)bs, bk, best);
+    bs = (T)best;
 }
 
 // Aperture structure of the table slots, fixed per plan:
@@ -752,15 +760,9 @@ __device__ __forceinline__ void shortlist_loop(const Args &a, const RecordShortF
             bs[b] = second ? s1 : s0;
             bk[b] = second ? s.kc[1] : s.kc[0];
         }
-        // warp argmax of every block in the same rounds, ties to the lower index
+        // warp argmax of every block, ties to the lower index
 #pragma unroll
-        for (int m = 16; m >= 1; m >>= 1)
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const float os = __shfl_xor_sync(0xffffffffu, bs[b], m);
-                const int ok = __shfl_xor_sync(0xffffffffu, bk[b], m);
-                if (os > bs[b] || (os == bs[b] && ok < bk[b])) { bs[b] = os; bk[b] = ok; }
-            }
+        for (int b = 0; b < NB; ++b) warp_argmax(bs[b], bk[b]);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             if (it >= nu[b]) continue;                 // this block is done (warp-uniform)
