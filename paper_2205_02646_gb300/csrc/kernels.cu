@@ -187,14 +187,17 @@ __device__ __forceinline__ const uint8_t *rec_types(const RecordShortF32 &r) { r
 __device__ __forceinline__ const uint8_t *rec_types(const Record<double> &r) { return r.types; }
 
 // ------------------------------------------- initial projected residual --
-// Steps 1-2 for one block: gather the weighted window and run the 16x16 DFTs
-// per type; returns Y[i][t] for kap = (8h + i, lane & 15), h = lane >> 4.
+// Step 1 and the row half of step 2 for one block: gather the weighted
+// window into the four type planes x_t(p, q) and sum the row DFTs
+// T_t(p, k2) = sum_q x_t(p, q) w16^-(q k2).  x is real, so
+// T_t(p, 16 - k2) = conj(T_t(p, k2)) and only k2 in [0, 8] is summed: lane
+// (c, r) = (lane & 7, lane >> 3) takes rows p = 4r..4r+3 at k2 = c for c >= 1;
+// lane c = 0 sums the two real columns, k2 = 0 (re slot) and k2 = 8 (im slot).
 // With UNIT, y is taken as 1 for every present L-pixel: the result is then
 // the DFT of the type-split spatial weights, whose conjugate is G_t.
 template <typename T, bool UNIT = false, typename Rec>
-__device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec, C2<T> *scratch,
-                                                   const C2<T> *omc, const T *wt, const WorkEntry we,
-                                                   const int lane, C2<T> (&Y)[8][4])
+__device__ __forceinline__ void window_rows(const Args &a, const Rec &rec, C2<T> *scratch, const C2<T> *omc,
+                                            const T *wt, const WorkEntry we, const int lane, C2<T> (&acc)[4][4])
 {
     const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
     const int p0 = 2 * we.bi - kOff / 2, q0 = 2 * we.bj - kOff / 2;
@@ -227,27 +230,56 @@ __device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec
     }
     __syncwarp();
 
-    const int k2 = lane & 15, h = lane >> 4;
-
-    // 2a. row DFTs: T_t(p, k2) = sum_q x_t(p, q) w16^-(q k2), p in this half.
-    C2<T> acc[8][4];
+    // 2a. row DFTs, k2 in [0, 8] (see above)
+    const int c = lane & 7, r = lane >> 3;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int t = 0; t < 4; ++t) acc[i][t] = {0, 0};
 #pragma unroll 4
     for (int q = 0; q < 16; ++q) {
-        const C2<T> tw = omc[(2 * q * k2) & 31];
+        const C2<T> tq = omc[(2 * q * c) & 31];
+        const T twre = c == 0 ? T(1) : tq.re;
+        const T twim = c == 0 ? ((q & 1) ? T(-1) : T(1)) : tq.im;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const Vec4<T> x = ld4(&x4[(8 * h + i) * 16 + q]);
-            acc[i][0].re += x.x * tw.re; acc[i][0].im += x.x * tw.im;
-            acc[i][1].re += x.y * tw.re; acc[i][1].im += x.y * tw.im;
-            acc[i][2].re += x.z * tw.re; acc[i][2].im += x.z * tw.im;
-            acc[i][3].re += x.w * tw.re; acc[i][3].im += x.w * tw.im;
+        for (int i = 0; i < 4; ++i) {
+            const Vec4<T> x = ld4(&x4[(4 * r + i) * 16 + q]);
+            acc[i][0].re += x.x * twre; acc[i][0].im += x.x * twim;
+            acc[i][1].re += x.y * twre; acc[i][1].im += x.y * twim;
+            acc[i][2].re += x.z * twre; acc[i][2].im += x.z * twim;
+            acc[i][3].re += x.w * twre; acc[i][3].im += x.w * twim;
         }
     }
+}
 
+// Write rows 4r..4r+3 of the type pair (2 pass, 2 pass + 1) into the scratch
+// as tb[p][k2] (two complex values), all 16 columns: (p, c) and its conjugate
+// (p, 16 - c), or for c = 0 the real columns (p, 0) and (p, 8).
+template <typename T>
+__device__ __forceinline__ void rows_to_scratch(const C2<T> (&acc)[4][4], Vec4<T> *tb, const int pass, const int lane)
+{
+    const int c = lane & 7, r = lane >> 3, t0 = 2 * pass;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int p = 4 * r + i;
+        const C2<T> a0 = acc[i][t0], a1 = acc[i][t0 + 1];
+        st4(&tb[p * 16 + c], c == 0 ? Vec4<T>{a0.re, T(0), a1.re, T(0)} : Vec4<T>{a0.re, a0.im, a1.re, a1.im});
+        st4(&tb[p * 16 + (c == 0 ? 8 : 16 - c)],
+            c == 0 ? Vec4<T>{a0.im, T(0), a1.im, T(0)} : Vec4<T>{a0.re, -a0.im, a1.re, -a1.im});
+    }
+}
+
+// Steps 1-2 for one block: the window's row DFTs, then the column DFTs
+//     Y_t(kap) = sum_{m: t(m) = t} w_m y_m w16^-(p kap1 + q kap2);
+// returns Y[i][t] for kap = (8h + i, lane & 15), h = lane >> 4.
+template <typename T, bool UNIT = false, typename Rec>
+__device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec, C2<T> *scratch,
+                                                   const C2<T> *omc, const T *wt, const WorkEntry we,
+                                                   const int lane, C2<T> (&Y)[8][4])
+{
+    C2<T> acc[4][4];
+    window_rows<T, UNIT>(a, rec, scratch, omc, wt, we, lane, acc);
+    const int k2 = lane & 15, h = lane >> 4;
     // 2b. column DFTs, two types at a time through the scratch, split by the
     // parity of p: half h sums p = 2j + h for kap1' in [0, 8); then
     // Y(kap1') = E + O and Y(kap1' + 8) = E - O.
@@ -256,10 +288,7 @@ __device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec
     for (int pass = 0; pass < 2; ++pass) {
         const int t0 = 2 * pass;
         __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            st4(&tb[(8 * h + i) * 16 + k2],
-                Vec4<T>{acc[i][t0].re, acc[i][t0].im, acc[i][t0 + 1].re, acc[i][t0 + 1].im});
+        rows_to_scratch<T>(acc, tb, pass, lane);
         __syncwarp();
         C2<T> cc[8][2];
 #pragma unroll
@@ -671,9 +700,6 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
                                                 const WorkEntry we, const Shortlist &sl, const int lane,
                                                 ShortState &st)
 {
-    C2<float> Y[8][4];
-    initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-    const int k2l = lane & 15, h = lane >> 4;
     // Reorder the 64 candidates so that the 8 lanes of a quarter warp hold
     // candidates with distinct (k2 mod 8) where possible: the per-iteration
     // table reads at ((u - k1) mod 16, (v - k2) mod 16) then fall in distinct
@@ -693,7 +719,7 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
         }
         // scatter through the scratch: position i -> lane (g % 4) * 8 + i / 8, slot g / 4
         int *pos = reinterpret_cast<int *>(scratch);
-        __syncwarp();
+        __syncwarp();    // the previous block of this warp is done with the scratch
         const int g0 = r0 & 7, g1 = r1 & 7;
         pos[(g0 >> 2) * 32 + (g0 & 3) * 8 + (r0 >> 3)] = c0;
         pos[(g1 >> 2) * 32 + (g1 & 3) * 8 + (r1 >> 3)] = c1;
@@ -705,21 +731,30 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
     for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int t = 0; t < 4; ++t) st.hk[c][t] = h_of(om, st.kc[c], t);
+    // R0_k = sum_t conj(h_t(k)) Y_t(k mod 16), with Y_t(kap) evaluated at this
+    // lane's two candidates only: Y_t(kap) = sum_p T_t(p, kap2) w16^-(p kap1)
+    // over the row DFTs of the window (through the scratch, two types a pass).
+    C2<float> acc[4][4];
+    window_rows<float>(a, rec, scratch, omc, wt, we, lane, acc);
+    Vec4<float> *tb = reinterpret_cast<Vec4<float> *>(scratch);
     st.R[0] = st.R[1] = C2<float>{0, 0};
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
         __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int u = 0; u < 2; ++u) scratch[((8 * h + i) * 16 + k2l) * 2 + u] = Y[i][2 * pass + u];
+        rows_to_scratch<float>(acc, tb, pass, lane);
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const int kap = (((st.kc[c] >> 5) & 15) << 4) | (st.kc[c] & 15);
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-                st.R[c] = cadd(st.R[c], cmul(cconj(st.hk[c][2 * pass + u]), scratch[kap * 2 + u]));
+            const int kap1 = (st.kc[c] >> 5) & 15, kap2 = st.kc[c] & 15;
+            C2<float> y0 = {0, 0}, y1 = {0, 0};
+#pragma unroll 4
+            for (int p = 0; p < 16; ++p) {
+                const C2<float> tw = omc[(2 * p * kap1) & 31];
+                const Vec4<float> tv = ld4(&tb[p * 16 + kap2]);
+                y0 = cadd(y0, cmul(C2<float>{tv.x, tv.y}, tw));
+                y1 = cadd(y1, cmul(C2<float>{tv.z, tv.w}, tw));
+            }
+            st.R[c] = cadd(st.R[c], cadd(cmul(cconj(st.hk[c][2 * pass]), y0), cmul(cconj(st.hk[c][2 * pass + 1]), y1)));
         }
     }
 #pragma unroll
