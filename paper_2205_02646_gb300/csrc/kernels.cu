@@ -674,9 +674,12 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
 
 // ------------------------------------------ restricted (shortlist) loop --
 // The greedy loop of Eqs. 11-17 over the 64 shortlisted candidates only, in
-// the projected-residual form: lane l holds R for candidates S[l], S[l + 32],
-// and the column C_{k,uv} of Eq. 14 is rebuilt from the factored tables,
-// C_{k,uv} = sum_t conj(h_t(k)) h_t(uv) G_t((uv - k) mod 16).
+// the projected-residual form, two blocks per warp: half-warp hb works on
+// block hb, its lane l holding R for the candidates at positions l + 16 s,
+// s = 0..3, and the column C_{k,uv} of Eq. 14 is rebuilt from the factored
+// tables, C_{k,uv} = sum_t conj(h_t(k)) h_t(uv) G_t((uv - k) mod 16).  The
+// per-iteration bookkeeping (delta, g_t, Eq. 18) then runs once for both
+// blocks, each half-warp for its own.
 __device__ __forceinline__ C2<float> h_of(const C2<float> *om, int k, int t)
 {
     const int k1 = k >> 5, k2 = k & 31;
@@ -685,30 +688,33 @@ __device__ __forceinline__ C2<float> h_of(const C2<float> *om, int k, int t)
     return csub(P, t == 0 ? C2<float>{1, 0} : t == 1 ? ev : t == 2 ? eu : euv);
 }
 
-// Setup of one block for the shortlist loop: its DFT state, the reordered
-// candidates of this lane, h_t(k), R^0_k = sum_t conj(h_t(k)) Y_t(k mod 16)
-// (Y gathered through the scratch) and q_k / D_k.
-struct ShortState {
-    int kc[2];
-    C2<float> hk[2][4];
-    C2<float> R[2];
-    float qd[2];
+struct HalfState {
+    int kc[4];
+    C2<float> hk[4][4];
+    C2<float> R[4];
+    float qd[4];
 };
 
+// Setup of one block for half-warp hb, with the whole warp working on it:
+// the candidates reordered, R^0_k = sum_t conj(h_t(k)) Y_t(k mod 16) with
+// the column DFTs evaluated at the candidates only, then handed to the lanes
+// of half hb, which add h_t(k) and q_k / D_k.
 __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShortF32 &rec, C2<float> *scratch,
                                                 const C2<float> *om, const C2<float> *omc, const float *wt,
-                                                const WorkEntry we, const Shortlist &sl, const int lane,
-                                                ShortState &st)
+                                                const WorkEntry we, const Shortlist &sl, const int lane, const int hb,
+                                                HalfState &st)
 {
-    // Reorder the 64 candidates so that the 8 lanes of a quarter warp hold
-    // candidates with distinct (k2 mod 8) where possible: the per-iteration
-    // table reads at ((u - k1) mod 16, (v - k2) mod 16) then fall in distinct
-    // shared-memory bank groups.  Sorted position i (by k2 mod 8, then by
-    // index) goes to quarter group g = i mod 8, member i / 8; the order does
-    // not change any result (ties are broken on the candidate index).
+    // Reorder the 64 candidates so that the 8 lanes of a quarter warp hold,
+    // in each slot, candidates with distinct (k2 mod 8) where possible: the
+    // per-iteration table reads at ((u - k1) mod 16, (v - k2) mod 16) then
+    // fall in distinct shared-memory bank groups.  Sorted position r (by k2
+    // mod 8, then by index) goes to group g = r mod 8, member r / 8; group g
+    // is slot g / 2 of quarter g mod 2 of the half, i.e. position
+    // 16 (g / 2) + 8 (g mod 2) + r / 8.  The order does not change any
+    // result (ties are broken on the candidate index).
+    int kw[2];
     {
         const int c0 = sl.idx[lane] & (kK - 1), c1 = sl.idx[lane + 32] & (kK - 1);   // in range for any input
-        // rank in (k2 mod 8, k) order over all 64 candidates (distinct keys)
         const int key0 = ((c0 & 7) << 10) | c0, key1 = ((c1 & 7) << 10) | c1;
         int r0 = 0, r1 = 0;
 #pragma unroll 4
@@ -717,27 +723,27 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
             r0 += (o0 < key0) + (o1 < key0);
             r1 += (o0 < key1) + (o1 < key1);
         }
-        // scatter through the scratch: position i -> lane (g % 4) * 8 + i / 8, slot g / 4
         int *pos = reinterpret_cast<int *>(scratch);
         __syncwarp();    // the previous block of this warp is done with the scratch
         const int g0 = r0 & 7, g1 = r1 & 7;
-        pos[(g0 >> 2) * 32 + (g0 & 3) * 8 + (r0 >> 3)] = c0;
-        pos[(g1 >> 2) * 32 + (g1 & 3) * 8 + (r1 >> 3)] = c1;
+        pos[(g0 >> 1) * 16 + (g0 & 1) * 8 + (r0 >> 3)] = c0;
+        pos[(g1 >> 1) * 16 + (g1 & 1) * 8 + (r1 >> 3)] = c1;
         __syncwarp();
-        st.kc[0] = pos[lane] & (kK - 1);               // duplicates in a caller's list leave slots unset
-        st.kc[1] = pos[32 + lane] & (kK - 1);
+        kw[0] = pos[lane] & (kK - 1);                  // duplicates in a caller's list leave positions unset
+        kw[1] = pos[32 + lane] & (kK - 1);
     }
+    // R0 of the candidates at positions lane and lane + 32: Y_t(kap) =
+    // sum_p T_t(p, kap2) w16^-(p kap1) over the row DFTs of the window
+    // (through the scratch, two types a pass).
+    C2<float> hw[2][4];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) st.hk[c][t] = h_of(om, st.kc[c], t);
-    // R0_k = sum_t conj(h_t(k)) Y_t(k mod 16), with Y_t(kap) evaluated at this
-    // lane's two candidates only: Y_t(kap) = sum_p T_t(p, kap2) w16^-(p kap1)
-    // over the row DFTs of the window (through the scratch, two types a pass).
+        for (int t = 0; t < 4; ++t) hw[c][t] = h_of(om, kw[c], t);
     C2<float> acc[4][4];
     window_rows<float>(a, rec, scratch, omc, wt, we, lane, acc);
     Vec4<float> *tb = reinterpret_cast<Vec4<float> *>(scratch);
-    st.R[0] = st.R[1] = C2<float>{0, 0};
+    C2<float> Rw[2] = {{0, 0}, {0, 0}};
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
         __syncwarp();
@@ -745,7 +751,7 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const int kap1 = (st.kc[c] >> 5) & 15, kap2 = st.kc[c] & 15;
+            const int kap1 = (kw[c] >> 5) & 15, kap2 = kw[c] & 15;
             C2<float> y0 = {0, 0}, y1 = {0, 0};
 #pragma unroll 4
             for (int p = 0; p < 16; ++p) {
@@ -754,97 +760,122 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
                 y0 = cadd(y0, cmul(C2<float>{tv.x, tv.y}, tw));
                 y1 = cadd(y1, cmul(C2<float>{tv.z, tv.w}, tw));
             }
-            st.R[c] = cadd(st.R[c], cadd(cmul(cconj(st.hk[c][2 * pass]), y0), cmul(cconj(st.hk[c][2 * pass + 1]), y1)));
+            Rw[c] = cadd(Rw[c], cadd(cmul(cconj(hw[c][2 * pass]), y0), cmul(cconj(hw[c][2 * pass + 1]), y1)));
         }
     }
+    // position 16 s + (lane & 15) sits at lane (16 s + (lane & 15)) mod 32, entry s / 2
+    const int l16 = lane & 15;
+    int kn[4];
+    C2<float> Rn[4];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) st.qd[c] = rec.qD[st.kc[c]];
+    for (int sl4 = 0; sl4 < 4; ++sl4) {
+        const int src = l16 + 16 * (sl4 & 1);
+        kn[sl4] = __shfl_sync(0xffffffffu, kw[sl4 >> 1], src);
+        Rn[sl4].re = __shfl_sync(0xffffffffu, Rw[sl4 >> 1].re, src);
+        Rn[sl4].im = __shfl_sync(0xffffffffu, Rw[sl4 >> 1].im, src);
+    }
+    if ((lane >> 4) == hb) {
+#pragma unroll
+        for (int sl4 = 0; sl4 < 4; ++sl4) {
+            st.kc[sl4] = kn[sl4];
+            st.R[sl4] = Rn[sl4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) st.hk[sl4][t] = h_of(om, kn[sl4], t);
+            st.qd[sl4] = rec.qD[kn[sl4]];
+        }
+    }
 }
 
-// The greedy loop of Eqs. 11-17 over the 64 shortlisted candidates of NB
-// blocks at once (one warp; NB = 2 interleaves two independent iteration
-// chains, hiding each other's shuffle and shared-memory latency), in the
-// projected-residual form: lane l holds R for two candidates per block, and
-// the column C_{k,uv} of Eq. 14 is rebuilt from the factored tables,
-// C_{k,uv} = sum_t conj(h_t(k)) h_t(uv) G_t((uv - k) mod 16).
-template <int NB>
-__device__ __forceinline__ void shortlist_loop(const Args &a, const RecordShortF32 &rec, C2<float> *scratch,
+__device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortlist &sl);
+
+// The shortlist loop for up to two blocks (on[b]: block b is present), one
+// per half-warp.  All lanes take part in every shuffle and ballot; a half
+// whose block is absent or done only skips the update.
+__device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF32 &rec, C2<float> *scratch,
                                                const C2<float> *om, const C2<float> *omc, const float *wt,
-                                               const WorkEntry (&we)[NB], const Shortlist *const (&sl)[NB],
-                                               const int (&nu)[NB], const int lane)
+                                               const WorkEntry (&we)[2], const bool (&on)[2], const int lane)
 {
-    ShortState st[NB];
+    const int hb = lane >> 4;
+    HalfState st;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) shortlist_setup(a, rec, scratch, om, omc, wt, we[b], *sl[b], lane, st[b]);
+    for (int sl4 = 0; sl4 < 4; ++sl4) {
+        st.kc[sl4] = 0;
+        st.R[sl4] = {0, 0};
+        st.qd[sl4] = 0.f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) st.hk[sl4][t] = {0, 0};
+    }
+    int nu[2] = {0, 0};
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+        if (on[b]) {
+            const Shortlist &sl = a.shortlists[we[b].ord];
+            shortlist_setup(a, rec, scratch, om, omc, wt, we[b], sl, lane, b, st);
+            nu[b] = shortlist_iterations(a, sl);
+        }
+    const int nu_h = hb == 0 ? nu[0] : nu[1];
+    const int numax = nu[0] > nu[1] ? nu[0] : nu[1];
+    const WorkEntry me = hb == 0 ? we[0] : we[1];
     const float gamma = (float)a.gamma;
     const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
-    float fpix[NB];
-    int u[NB], v[NB];
-    C2<float> g[NB][4];
-    long long trow[NB];
-    int numax = 0;
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        fpix[b] = 0.f;
-        u[b] = v[b] = 0;
-        trow[b] = (long long)we[b].ord * a.nu_max;
-        numax = nu[b] > numax ? nu[b] : numax;
-    }
+    float fpix = 0.f, unused_pw = 0.f;
+    int u = 0, v = 0;
+    C2<float> g[4];
+    const long long trow = (long long)me.ord * a.nu_max;
     for (int it = 0; it < numax; ++it) {
-        float bs[NB];
-        int bk[NB];
+        // this lane's best (score, index), ties to the lower index
+        float bs = -1.f;
+        int bk = kK;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const ShortState &s = st[b];
-            const float s0 = s.qd[0] * (s.R[0].re * s.R[0].re + s.R[0].im * s.R[0].im);
-            const float s1 = s.qd[1] * (s.R[1].re * s.R[1].re + s.R[1].im * s.R[1].im);
-            const bool second = s1 > s0 || (s1 == s0 && s.kc[1] < s.kc[0]);
-            bs[b] = second ? s1 : s0;
-            bk[b] = second ? s.kc[1] : s.kc[0];
+        for (int sl4 = 0; sl4 < 4; ++sl4) {
+            const C2<float> R = st.R[sl4];
+            const float sc = st.qd[sl4] * (R.re * R.re + R.im * R.im);
+            if (sc > bs || (sc == bs && st.kc[sl4] < bk)) { bs = sc; bk = st.kc[sl4]; }
         }
-        // warp argmax of every block, ties to the lower index
+        // the half-warp's best: butterfly over its 16 lanes
 #pragma unroll
-        for (int b = 0; b < NB; ++b) warp_argmax(bs[b], bk[b]);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            if (it >= nu[b]) continue;                 // this block is done (warp-uniform)
-            ShortState &s = st[b];
-            const unsigned owner = __ballot_sync(0xffffffffu, s.kc[0] == bk[b] || s.kc[1] == bk[b]);
-            const int wl = __ffs(owner) - 1;
-            const C2<float> send = s.kc[0] == bk[b] ? s.R[0] : s.R[1];
-            const float Rre = __shfl_sync(0xffffffffu, send.re, wl);
-            const float Rim = __shfl_sync(0xffffffffu, send.im, wl);
-            float unused_pw;
-            select_step<float>(a, om, rec.invD[bk[b]], gamma, bk[b], Rre, Rim, eta, gam, lane, trow[b], it, u[b],
-                               v[b], g[b], fpix[b], unused_pw);
+        for (int off = 8; off >= 1; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, bs, off);
+            const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
+            if (os > bs || (os == bs && ok < bk)) { bs = os; bk = ok; }
+        }
+        // the lane of this half holding bk, and its R
+        const bool has = st.kc[0] == bk || st.kc[1] == bk || st.kc[2] == bk || st.kc[3] == bk;
+        const unsigned mine = (__ballot_sync(0xffffffffu, has) >> (16 * hb)) & 0xFFFFu;
+        const int wl = 16 * hb + (mine ? __ffs(mine) - 1 : 0);
+        const C2<float> send = st.kc[0] == bk ? st.R[0] : st.kc[1] == bk ? st.R[1] : st.kc[2] == bk ? st.R[2] : st.R[3];
+        const float Rre = __shfl_sync(0xffffffffu, send.re, wl);
+        const float Rim = __shfl_sync(0xffffffffu, send.im, wl);
+        if (it < nu_h) {
+            select_step<float>(a, om, rec.invD[bk & (kK - 1)], gamma, bk & (kK - 1), Rre, Rim, eta, gam, lane & 15,
+                               trow, it, u, v, g, fpix, unused_pw);
             // Eq. 17 on the shortlist
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int d1 = (u[b] - (s.kc[c] >> 5)) & 15, d2 = (v[b] - s.kc[c]) & 15;
+            for (int sl4 = 0; sl4 < 4; ++sl4) {
+                const int kc = st.kc[sl4];
+                const int d1 = (u - (kc >> 5)) & 15, d2 = (v - kc) & 15;
                 // two 16-byte loads at (d1, d2): bank group (v - k2) mod 8, which the
                 // candidate order keeps distinct within each quarter warp
                 const float4 G01 = lds4(rec.G01[d1 * 16 + d2]), G23 = lds4(rec.G23[d1 * 16 + d2]);
                 const C2<float> G[4] = {{G01.x, G01.y}, {G01.z, G01.w}, {G23.x, G23.y}, {G23.z, G23.w}};
                 C2<float> dR = {0, 0};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) dR = cadd(dR, cmul(cconj(s.hk[c][t]), cmul(g[b][t], G[t])));
-                s.R[c] = csub(s.R[c], dR);
+                for (int t = 0; t < 4; ++t) dR = cadd(dR, cmul(cconj(st.hk[sl4][t]), cmul(g[t], G[t])));
+                st.R[sl4] = csub(st.R[sl4], dR);
             }
         }
     }
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        if (a.trace_sel != nullptr && lane == 0)
-            for (int it = nu[b]; it < a.nu_max; ++it) {
-                a.trace_sel[trow[b] + it] = 0xFFFF;
-                a.trace_dc[2 * (trow[b] + it)] = 0.f;
-                a.trace_dc[2 * (trow[b] + it) + 1] = 0.f;
+    const bool mine_on = hb == 0 ? on[0] : on[1];
+    if (mine_on) {
+        if (a.trace_sel != nullptr && (lane & 15) == 0)
+            for (int it = nu_h; it < a.nu_max; ++it) {
+                a.trace_sel[trow + it] = 0xFFFF;
+                a.trace_dc[2 * (trow + it)] = 0.f;
+                a.trace_dc[2 * (trow + it) + 1] = 0.f;
             }
-        if (lane < 16) {
-            const ImageDesc img = a.descs ? a.descs[we[b].img] : a.single;
-            const int yy = 4 * we[b].bi + (lane >> 2), xx = 4 * we[b].bj + (lane & 3);
-            img.hr[(long long)yy * img.hr_pitch + xx] = fpix[b];
-        }
+        const ImageDesc img = a.descs ? a.descs[me.img] : a.single;
+        const int yy = 4 * me.bi + ((lane >> 2) & 3), xx = 4 * me.bj + (lane & 3);
+        img.hr[(long long)yy * img.hr_pitch + xx] = fpix;
     }
 }
 
@@ -885,11 +916,10 @@ template <int MODE> struct Loop<float, MODE> {
         } else if constexpr (MODE == 1) {
             const Shortlist &sl = a.shortlists[we.ord];
             if (!(sl.missing <= a.max_missing)) return;
-            const WorkEntry w1[1] = {we};
-            const Shortlist *const s1[1] = {&sl};
-            const int n1[1] = {shortlist_iterations(a, sl)};
             if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 1);
-            shortlist_loop<1>(a, rec, scratch, om, omc, wt, w1, s1, n1, lane);
+            const WorkEntry w2[2] = {we, we};
+            const bool on[2] = {true, false};
+            shortlist_pair(a, rec, scratch, om, omc, wt, w2, on, lane);
         } else {
             const Shortlist &sl = a.shortlists[we.ord];
             if (sl.missing <= a.max_missing) return;
@@ -899,8 +929,8 @@ template <int MODE> struct Loop<float, MODE> {
         }
     }
 
-    // Mode 1 with two entries per warp: blocks that both take the shortlist
-    // loop run it interleaved.
+    // Mode 1 with two entries per warp: the blocks that take the shortlist
+    // loop run it together, one per half-warp.
     static __device__ __forceinline__ void run_pair(const Args &a, const Rec &rec, C2<float> *scratch,
                                                     const C2<float> *om, const C2<float> *omc,
                                                     const PairTables &pt, const float *wt, const WorkEntry e0,
@@ -908,16 +938,11 @@ template <int MODE> struct Loop<float, MODE> {
     {
         const bool r0 = e0.img >= 0 && a.shortlists[e0.ord].missing <= a.max_missing;
         const bool r1 = e1.img >= 0 && a.shortlists[e1.ord].missing <= a.max_missing;
-        if (r0 && r1) {
-            const WorkEntry w2[2] = {e0, e1};
-            const Shortlist *const s2[2] = {&a.shortlists[e0.ord], &a.shortlists[e1.ord]};
-            const int n2[2] = {shortlist_iterations(a, *s2[0]), shortlist_iterations(a, *s2[1])};
-            if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 2);
-            shortlist_loop<2>(a, rec, scratch, om, omc, wt, w2, s2, n2, lane);
-        } else {
-            if (e0.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e0, lane);
-            if (e1.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e1, lane);
-        }
+        if (!r0 && !r1) return;
+        if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, (int)r0 + (int)r1);
+        const WorkEntry w2[2] = {e0, e1};
+        const bool on[2] = {r0, r1};
+        shortlist_pair(a, rec, scratch, om, omc, wt, w2, on, lane);
     }
 };
 template <int MODE> struct Loop<double, MODE> {
@@ -1367,7 +1392,7 @@ struct Variant {
 const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 0), RLJSDE_VARIANT(float, 4, 4, 0), RLJSDE_VARIANT(float, 8, 2, 0),
     RLJSDE_VARIANT(float, 8, 1, 0), RLJSDE_VARIANT(double, 4, 1, 0), RLJSDE_VARIANT(double, 8, 1, 0),
-    RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 3, 2),
+    RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 4, 1), RLJSDE_VARIANT(float, 4, 3, 2),
     RLJSDE_VARIANT(float, 4, 3, 3), RLJSDE_VARIANT(float, 8, 2, 3), RLJSDE_VARIANT(double, 4, 1, 3),
     RLJSDE_VARIANT(float, 4, 3, 4), RLJSDE_VARIANT(float, 8, 2, 4), RLJSDE_VARIANT(double, 4, 1, 4),
     RLJSDE_VARIANT(float, 4, 3, 8), RLJSDE_VARIANT(float, 4, 3, 11), RLJSDE_VARIANT(float, 4, 3, 12),

@@ -127,7 +127,7 @@ struct rljsde_plan {
     int device = 0, sm_count = 0;
     int warps = 4, ctas_per_sm = 0, grid = 0, variant = 0;
     int learned_warps = 4;            // warps per CTA of the shortlist-loop kernel (4: two blocks per warp)
-    int learned_minb = 3;             // its register budget: resident CTAs per SM
+    int learned_minb = 4;             // its register budget: resident CTAs per SM (4: 128 registers)
     // device memory, all owned by the plan
     void *d_records = nullptr;        // n_tables records (float or double)
     size_t record_bytes = 0;
