@@ -688,11 +688,14 @@ __device__ __forceinline__ C2<float> h_of(const C2<float> *om, int k, int t)
     return csub(P, t == 0 ? C2<float>{1, 0} : t == 1 ? ev : t == 2 ? eu : euv);
 }
 
+// State of one half-warp lane: its four candidates, their R, q_k / D_k, and
+// h_t(k) packed by type pairs (t = 0, 1 and t = 2, 3 in the two halves of
+// an f32x2 register): re, im and -im.
 struct HalfState {
     int kc[4];
-    C2<float> hk[4][4];
     C2<float> R[4];
     float qd[4];
+    float2 hre[4][2], him[4][2], nhim[4][2];
 };
 
 // Setup of one block for half-warp hb, with the whole warp working on it:
@@ -779,8 +782,15 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
         for (int sl4 = 0; sl4 < 4; ++sl4) {
             st.kc[sl4] = kn[sl4];
             st.R[sl4] = Rn[sl4];
+            C2<float> hk[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) st.hk[sl4][t] = h_of(om, kn[sl4], t);
+            for (int t = 0; t < 4; ++t) hk[t] = h_of(om, kn[sl4], t);
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                st.hre[sl4][pr] = f2(hk[2 * pr].re, hk[2 * pr + 1].re);
+                st.him[sl4][pr] = f2(hk[2 * pr].im, hk[2 * pr + 1].im);
+                st.nhim[sl4][pr] = f2(-hk[2 * pr].im, -hk[2 * pr + 1].im);
+            }
             st.qd[sl4] = rec.qD[kn[sl4]];
         }
     }
@@ -803,7 +813,7 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
         st.R[sl4] = {0, 0};
         st.qd[sl4] = 0.f;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) st.hk[sl4][t] = {0, 0};
+        for (int pr = 0; pr < 2; ++pr) st.hre[sl4][pr] = st.him[sl4][pr] = st.nhim[sl4][pr] = f2(0.f, 0.f);
     }
     int nu[2] = {0, 0};
 #pragma unroll
@@ -832,12 +842,16 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
             const float sc = st.qd[sl4] * (R.re * R.re + R.im * R.im);
             if (sc > bs || (sc == bs && st.kc[sl4] < bk)) { bs = sc; bk = st.kc[sl4]; }
         }
-        // the half-warp's best: butterfly over its 16 lanes
-#pragma unroll
-        for (int off = 8; off >= 1; off >>= 1) {
-            const float os = __shfl_xor_sync(0xffffffffu, bs, off);
-            const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
-            if (os > bs || (os == bs && ok < bk)) { bs = os; bk = ok; }
+        // the half-warp's best: warp reductions over each half's inputs, the
+        // largest score (non-negative, so its bits order like the value), then
+        // the smallest index among the lanes holding it
+        {
+            const unsigned bits = __float_as_uint(bs);
+            const unsigned m0 = __reduce_max_sync(0xffffffffu, hb == 0 ? bits : 0u);
+            const unsigned m1 = __reduce_max_sync(0xffffffffu, hb == 1 ? bits : 0u);
+            const unsigned i0 = __reduce_min_sync(0xffffffffu, (hb == 0 && bits == m0) ? (unsigned)bk : 0xffffffffu);
+            const unsigned i1 = __reduce_min_sync(0xffffffffu, (hb == 1 && bits == m1) ? (unsigned)bk : 0xffffffffu);
+            bk = (int)(hb == 0 ? i0 : i1);
         }
         // the lane of this half holding bk, and its R
         const bool has = st.kc[0] == bk || st.kc[1] == bk || st.kc[2] == bk || st.kc[3] == bk;
@@ -849,19 +863,29 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
         if (it < nu_h) {
             select_step<float>(a, om, rec.invD[bk & (kK - 1)], gamma, bk & (kK - 1), Rre, Rim, eta, gam, lane & 15,
                                trow, it, u, v, g, fpix, unused_pw);
-            // Eq. 17 on the shortlist
+            // Eq. 17 on the shortlist: R_k -= sum_t conj(h_t(k)) g_t G_t(uv - k), two
+            // types per f32x2 register
+            const float2 gre[2] = {f2(g[0].re, g[1].re), f2(g[2].re, g[3].re)};
+            const float2 gim[2] = {f2(g[0].im, g[1].im), f2(g[2].im, g[3].im)};
+            const float2 ngim[2] = {f2(-g[0].im, -g[1].im), f2(-g[2].im, -g[3].im)};
 #pragma unroll
             for (int sl4 = 0; sl4 < 4; ++sl4) {
                 const int kc = st.kc[sl4];
                 const int d1 = (u - (kc >> 5)) & 15, d2 = (v - kc) & 15;
                 // two 16-byte loads at (d1, d2): bank group (v - k2) mod 8, which the
                 // candidate order keeps distinct within each quarter warp
-                const float4 G01 = lds4(rec.G01[d1 * 16 + d2]), G23 = lds4(rec.G23[d1 * 16 + d2]);
-                const C2<float> G[4] = {{G01.x, G01.y}, {G01.z, G01.w}, {G23.x, G23.y}, {G23.z, G23.w}};
-                C2<float> dR = {0, 0};
+                const float4 G[2] = {lds4(rec.G01[d1 * 16 + d2]), lds4(rec.G23[d1 * 16 + d2])};
+                float2 are = f2(0.f, 0.f), aim = f2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < 4; ++t) dR = cadd(dR, cmul(cconj(st.hk[sl4][t]), cmul(g[t], G[t])));
-                st.R[sl4] = csub(st.R[sl4], dR);
+                for (int pr = 0; pr < 2; ++pr) {
+                    const float2 Gre = f2(G[pr].x, G[pr].y), Gim = f2(G[pr].z, G[pr].w);
+                    const float2 gGre = fma2(Gre, gre[pr], mul2(Gim, ngim[pr]));   // g_t G_t
+                    const float2 gGim = fma2(Gim, gre[pr], mul2(Gre, gim[pr]));
+                    are = fma2(st.hre[sl4][pr], gGre, fma2(st.him[sl4][pr], gGim, are));
+                    aim = fma2(st.hre[sl4][pr], gGim, fma2(st.nhim[sl4][pr], gGre, aim));
+                }
+                st.R[sl4].re -= are.x + are.y;
+                st.R[sl4].im -= aim.x + aim.y;
             }
         }
     }
@@ -1392,7 +1416,7 @@ struct Variant {
 const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 0), RLJSDE_VARIANT(float, 4, 4, 0), RLJSDE_VARIANT(float, 8, 2, 0),
     RLJSDE_VARIANT(float, 8, 1, 0), RLJSDE_VARIANT(double, 4, 1, 0), RLJSDE_VARIANT(double, 8, 1, 0),
-    RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 4, 1), RLJSDE_VARIANT(float, 4, 3, 2),
+    RLJSDE_VARIANT(float, 4, 3, 1), RLJSDE_VARIANT(float, 8, 2, 1), RLJSDE_VARIANT(float, 4, 3, 2),
     RLJSDE_VARIANT(float, 4, 3, 3), RLJSDE_VARIANT(float, 8, 2, 3), RLJSDE_VARIANT(double, 4, 1, 3),
     RLJSDE_VARIANT(float, 4, 3, 4), RLJSDE_VARIANT(float, 8, 2, 4), RLJSDE_VARIANT(double, 4, 1, 4),
     RLJSDE_VARIANT(float, 4, 3, 8), RLJSDE_VARIANT(float, 4, 3, 11), RLJSDE_VARIANT(float, 4, 3, 12),

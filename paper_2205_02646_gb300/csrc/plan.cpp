@@ -177,8 +177,8 @@ void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t
     build_tables(key, w, r32, slot_ap, T);
     for (int d = 0; d < 256; ++d) {
         float *a = sh->G01[d], *b = sh->G23[d];
-        a[0] = (float)T.Gre[0][d]; a[1] = (float)T.Gim[0][d]; a[2] = (float)T.Gre[1][d]; a[3] = (float)T.Gim[1][d];
-        b[0] = (float)T.Gre[2][d]; b[1] = (float)T.Gim[2][d]; b[2] = (float)T.Gre[3][d]; b[3] = (float)T.Gim[3][d];
+        a[0] = (float)T.Gre[0][d]; a[1] = (float)T.Gre[1][d]; a[2] = (float)T.Gim[0][d]; a[3] = (float)T.Gim[1][d];
+        b[0] = (float)T.Gre[2][d]; b[1] = (float)T.Gre[3][d]; b[2] = (float)T.Gim[2][d]; b[3] = (float)T.Gim[3][d];
     }
     for (int k = 0; k < kK; ++k) {
         sh->qD[k] = (float)inv_or_zero(q[k], T.D[k]);

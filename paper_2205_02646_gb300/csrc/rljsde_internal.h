@@ -86,7 +86,8 @@ static_assert(sizeof(RecordF32) % 16 == 0, "record size must allow bulk copies")
 
 // FP32 tables of the shortlist loop, which reads the four G_t at one
 // (d1, d2) per candidate: G01[d] = (G_0(d), G_1(d)), G23[d] = (G_2(d), G_3(d))
-// as (re, im, re, im), d = d1 * 16 + d2; qD and invD by linear k.
+// as (re, re, im, im) so that each pair of types fills one f32x2 register
+// pair, d = d1 * 16 + d2; qD and invD by linear k.
 struct RecordShortF32 {
     float G01[256][4];
     float G23[256][4];
@@ -127,7 +128,7 @@ struct rljsde_plan {
     int device = 0, sm_count = 0;
     int warps = 4, ctas_per_sm = 0, grid = 0, variant = 0;
     int learned_warps = 4;            // warps per CTA of the shortlist-loop kernel (4: two blocks per warp)
-    int learned_minb = 4;             // its register budget: resident CTAs per SM (4: 128 registers)
+    int learned_minb = 3;             // its register budget: resident CTAs per SM
     // device memory, all owned by the plan
     void *d_records = nullptr;        // n_tables records (float or double)
     size_t record_bytes = 0;
