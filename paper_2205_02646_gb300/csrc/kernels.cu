@@ -711,20 +711,24 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
     // in each slot, candidates with distinct (k2 mod 8) where possible: the
     // per-iteration table reads at ((u - k1) mod 16, (v - k2) mod 16) then
     // fall in distinct shared-memory bank groups.  Sorted position r (by k2
-    // mod 8, then by index) goes to group g = r mod 8, member r / 8; group g
+    // mod 8, then by list position) goes to group g = r mod 8, member r / 8; group g
     // is slot g / 2 of quarter g mod 2 of the half, i.e. position
     // 16 (g / 2) + 8 (g mod 2) + r / 8.  The order does not change any
     // result (ties are broken on the candidate index).
     int kw[2];
     {
         const int c0 = sl.idx[lane] & (kK - 1), c1 = sl.idx[lane + 32] & (kK - 1);   // in range for any input
-        const int key0 = ((c0 & 7) << 10) | c0, key1 = ((c1 & 7) << 10) | c1;
-        int r0 = 0, r1 = 0;
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-            const int o0 = __shfl_sync(0xffffffffu, key0, j), o1 = __shfl_sync(0xffffffffu, key1, j);
-            r0 += (o0 < key0) + (o1 < key0);
-            r1 += (o0 < key1) + (o1 < key1);
+        // rank in (k2 mod 8, list position) order: bucket sizes and the
+        // position inside a bucket from ballots
+        const int q0 = c0 & 7, q1 = c1 & 7;
+        const unsigned lt = (1u << lane) - 1u;
+        int r0 = 0, r1 = 0, below = 0;
+#pragma unroll
+        for (int bv = 0; bv < 8; ++bv) {
+            const unsigned e0 = __ballot_sync(0xffffffffu, q0 == bv), e1 = __ballot_sync(0xffffffffu, q1 == bv);
+            if (q0 == bv) r0 = below + __popc(e0 & lt);
+            if (q1 == bv) r1 = below + __popc(e0) + __popc(e1 & lt);
+            below += __popc(e0) + __popc(e1);
         }
         int *pos = reinterpret_cast<int *>(scratch);
         __syncwarp();    // the previous block of this warp is done with the scratch

@@ -427,6 +427,17 @@ __global__ void __launch_bounds__(256) head_features_tile_kernel(const float *a3
 // Per block (one warp): logits + bias -> shortlist of the 64 largest (ties to
 // the lower index), the expected number of likely candidates left out
 // (sum of sigmoid over the rest), and the iteration output.
+__device__ __forceinline__ uint32_t order_key(float v)
+{
+    // order-preserving unsigned key of a float
+    const uint32_t u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_value(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, long long b0, int nb, Shortlist *out)
 {
     const int lane = threadIdx.x & 31;
@@ -434,15 +445,9 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
     for (long long bl = (long long)blockIdx.x * wpb + wib; bl < nb; bl += (long long)gridDim.x * wpb) {
         // z rows are relative to the chunk, shortlists are indexed by block
         const float *zb = z + bl * ldz;
-        float v[32];
         uint32_t key[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            v[j] = zb[j * 32 + lane] + bias[j * 32 + lane];
-            // order-preserving unsigned key of the float
-            const uint32_t u = __float_as_uint(v[j]);
-            key[j] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-        }
+        for (int j = 0; j < 32; ++j) key[j] = order_key(zb[j * 32 + lane] + bias[j * 32 + lane]);
         // Bounds on the 64th largest key: at most the warp's largest key, at
         // least the smallest of the 32 lanes' second-largest keys (those 64
         // keys all reach it).  Its bits above the first bit where the two
@@ -454,11 +459,8 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
             m2 = max(m2, min(m1, k));
             m1 = max(m1, k);
         }
-        uint32_t hi = m1, lo = m2;
-        for (int o = 16; o; o >>= 1) {
-            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        }
+        const uint32_t hi = __reduce_max_sync(0xffffffffu, m1);
+        const uint32_t lo = __reduce_min_sync(0xffffffffu, m2);
         const uint32_t diff = hi ^ lo;
         const int top = diff ? 31 - __clz(diff) : -1;          // highest differing bit
         // Binary search on the remaining key bits for the 64th largest key;
@@ -469,12 +471,12 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
         if (top < 0) thr = hi;                                   // all candidates equal at the top
         for (int bit = top; bit >= 0; --bit) {
             const uint32_t cand = thr | (1u << bit);
-            int cnt = 0;
+            unsigned cnt = 0;
 #pragma unroll
             for (int j = 0; j < 32; ++j) cnt += key[j] >= cand;
-            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            if (cnt >= kShortlist) thr = cand;
-            if (cnt == kShortlist) { exact = true; break; }       // warp-uniform
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if (cnt >= (unsigned)kShortlist) thr = cand;
+            if (cnt == (unsigned)kShortlist) { exact = true; break; }   // warp-uniform
         }
         Shortlist &sl = out[b0 + bl];
         float rest = 0.f;
@@ -494,7 +496,7 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
                 if (key[j] >= thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-v[j]));
+                if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-key_value(key[j])));
             for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
             if (lane == 0) {
                 sl.missing = rest;
@@ -506,8 +508,7 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
         int above = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) above += key[j] > thr;
-        int above_total = above;
-        for (int o = 16; o; o >>= 1) above_total += __shfl_xor_sync(0xffffffffu, above_total, o);
+        const int above_total = (int)__reduce_add_sync(0xffffffffu, (unsigned)above);
         int base = above;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, base, o);
@@ -529,7 +530,7 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
         }
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-v[j]));
+            if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-key_value(key[j])));
         for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
         if (lane == 0) {
             sl.missing = rest;
