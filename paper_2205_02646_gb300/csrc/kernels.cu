@@ -992,6 +992,27 @@ template <int MODE> struct Loop<double, MODE> {
     }
 };
 
+// Modes 1 and 2 each take part of the blocks (by the shortlist's left-out
+// mass); a chunk none of whose blocks this mode takes is skipped, table copy
+// included.  Block-uniform (every thread of the CTA must call it).
+template <int MODE>
+__device__ __forceinline__ bool chunk_has_work(const Args &a, const int c)
+{
+    if constexpr (MODE != 1 && MODE != 2) {
+        return true;
+    } else {
+        bool mine = false;
+        if (threadIdx.x < kChunk) {
+            const WorkEntry we = a.entries[(size_t)c * kChunk + threadIdx.x];
+            if (we.img >= 0) {
+                const bool restricted = a.shortlists[we.ord].missing <= a.max_missing;
+                mine = MODE == 1 ? restricted : !restricted;
+            }
+        }
+        return __syncthreads_or(mine) != 0;
+    }
+}
+
 // --------------------------------------------------- persistent kernel --
 template <typename T, int WARPS, int MINB, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args a)
@@ -1045,7 +1066,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
     uint32_t pending = 0, parity = 0;
     for (int s = 0; s < 2; ++s) {
         const int c = blockIdx.x + s * gridDim.x;
-        if (c < a.n_chunks) {
+        if (c < a.n_chunks && chunk_has_work<MODE>(a, c)) {
             const int t = a.chunk_table[c];
             if (threadIdx.x == 0) bulk_load(slot(s), records + (size_t)t * rb, rb, &bar[s]);
             if (s == 0) held0 = t; else held1 = t;
@@ -1057,13 +1078,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
         const int c = blockIdx.x + r * gridDim.x;
         if (c >= a.n_chunks) break;
         const int s = r & 1;
+        const bool work = chunk_has_work<MODE>(a, c);   // as when its table was fetched
         if (pending & (1u << s)) {
             const bool ok = mbar_wait(&bar[s], (parity >> s) & 1u);
             if (!__syncthreads_and(ok)) { failed = true; break; }
             parity ^= 1u << s;
             pending &= ~(1u << s);
         }
-        if constexpr (MODE == 1 && WARPS * 2 == kChunk) {
+        if (!work) {
+            // no block of this chunk in this mode
+        } else if constexpr (MODE == 1 && WARPS * 2 == kChunk) {
             const WorkEntry e0 = a.entries[(size_t)c * kChunk + warp];
             const WorkEntry e1 = a.entries[(size_t)c * kChunk + warp + WARPS];
             Loop<T, MODE>::run_pair(a, *slot(s), scratch, om, omc, *pt, wt, e0, e1, lane);
@@ -1075,7 +1099,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
         }
         __syncthreads();                       // every warp is done with slot s
         const int c2 = blockIdx.x + (r + 2) * gridDim.x;
-        if (c2 < a.n_chunks) {
+        if (c2 < a.n_chunks && chunk_has_work<MODE>(a, c2)) {
             const int t2 = a.chunk_table[c2];
             if (t2 != (s == 0 ? held0 : held1)) {
                 if (threadIdx.x == 0) {
