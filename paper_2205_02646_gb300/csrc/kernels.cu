@@ -693,8 +693,7 @@ __device__ __forceinline__ C2<float> h_of(const C2<float> *om, int k, int t)
 // an f32x2 register): re, im and -im.
 struct HalfState {
     int kc[4];
-    C2<float> R[4];
-    float qd[4];
+    float2 Rre[2], Rim[2], qd[2];    // slots (0, 1) and (2, 3) packed
     float2 hre[4][2], him[4][2], nhim[4][2];
 };
 
@@ -785,7 +784,8 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
 #pragma unroll
         for (int sl4 = 0; sl4 < 4; ++sl4) {
             st.kc[sl4] = kn[sl4];
-            st.R[sl4] = Rn[sl4];
+            if (sl4 & 1) { st.Rre[sl4 >> 1].y = Rn[sl4].re; st.Rim[sl4 >> 1].y = Rn[sl4].im; }
+            else { st.Rre[sl4 >> 1].x = Rn[sl4].re; st.Rim[sl4 >> 1].x = Rn[sl4].im; }
             C2<float> hk[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) hk[t] = h_of(om, kn[sl4], t);
@@ -795,7 +795,8 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
                 st.him[sl4][pr] = f2(hk[2 * pr].im, hk[2 * pr + 1].im);
                 st.nhim[sl4][pr] = f2(-hk[2 * pr].im, -hk[2 * pr + 1].im);
             }
-            st.qd[sl4] = rec.qD[kn[sl4]];
+            if (sl4 & 1) st.qd[sl4 >> 1].y = rec.qD[kn[sl4]];
+            else st.qd[sl4 >> 1].x = rec.qD[kn[sl4]];
         }
     }
 }
@@ -814,8 +815,7 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
 #pragma unroll
     for (int sl4 = 0; sl4 < 4; ++sl4) {
         st.kc[sl4] = 0;
-        st.R[sl4] = {0, 0};
-        st.qd[sl4] = 0.f;
+        if (sl4 < 2) st.Rre[sl4] = st.Rim[sl4] = st.qd[sl4] = f2(0.f, 0.f);
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) st.hre[sl4][pr] = st.him[sl4][pr] = st.nhim[sl4][pr] = f2(0.f, 0.f);
     }
@@ -837,33 +837,35 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
     C2<float> g[4];
     const long long trow = (long long)me.ord * a.nu_max;
     for (int it = 0; it < numax; ++it) {
-        // this lane's best (score, index), ties to the lower index
-        float bs = -1.f;
-        int bk = kK;
-#pragma unroll
-        for (int sl4 = 0; sl4 < 4; ++sl4) {
-            const C2<float> R = st.R[sl4];
-            const float sc = st.qd[sl4] * (R.re * R.re + R.im * R.im);
-            if (sc > bs || (sc == bs && st.kc[sl4] < bk)) { bs = sc; bk = st.kc[sl4]; }
-        }
-        // the half-warp's best: warp reductions over each half's inputs, the
-        // largest score (non-negative, so its bits order like the value), then
-        // the smallest index among the lanes holding it
+        // scores of the four candidates (two f32x2 pairs), the half-warp's
+        // largest by warp reductions over each half's inputs (non-negative,
+        // so the bits order like the values), then the smallest index among
+        // the candidates holding it
+        const float2 sc01 = mul2(st.qd[0], fma2(st.Rim[0], st.Rim[0], mul2(st.Rre[0], st.Rre[0])));
+        const float2 sc23 = mul2(st.qd[1], fma2(st.Rim[1], st.Rim[1], mul2(st.Rre[1], st.Rre[1])));
+        const unsigned sb[4] = {__float_as_uint(sc01.x), __float_as_uint(sc01.y), __float_as_uint(sc23.x),
+                                __float_as_uint(sc23.y)};
+        int bk;
         {
-            const unsigned bits = __float_as_uint(bs);
+            const unsigned bits = max(max(sb[0], sb[1]), max(sb[2], sb[3]));
             const unsigned m0 = __reduce_max_sync(0xffffffffu, hb == 0 ? bits : 0u);
             const unsigned m1 = __reduce_max_sync(0xffffffffu, hb == 1 ? bits : 0u);
-            const unsigned i0 = __reduce_min_sync(0xffffffffu, (hb == 0 && bits == m0) ? (unsigned)bk : 0xffffffffu);
-            const unsigned i1 = __reduce_min_sync(0xffffffffu, (hb == 1 && bits == m1) ? (unsigned)bk : 0xffffffffu);
+            const unsigned mh = hb == 0 ? m0 : m1;
+            unsigned kmin = 0xffffffffu;
+#pragma unroll
+            for (int sl4 = 0; sl4 < 4; ++sl4) kmin = min(kmin, sb[sl4] == mh ? (unsigned)st.kc[sl4] : 0xffffffffu);
+            const unsigned i0 = __reduce_min_sync(0xffffffffu, hb == 0 ? kmin : 0xffffffffu);
+            const unsigned i1 = __reduce_min_sync(0xffffffffu, hb == 1 ? kmin : 0xffffffffu);
             bk = (int)(hb == 0 ? i0 : i1);
         }
         // the lane of this half holding bk, and its R
         const bool has = st.kc[0] == bk || st.kc[1] == bk || st.kc[2] == bk || st.kc[3] == bk;
         const unsigned mine = (__ballot_sync(0xffffffffu, has) >> (16 * hb)) & 0xFFFFu;
         const int wl = 16 * hb + (mine ? __ffs(mine) - 1 : 0);
-        const C2<float> send = st.kc[0] == bk ? st.R[0] : st.kc[1] == bk ? st.R[1] : st.kc[2] == bk ? st.R[2] : st.R[3];
-        const float Rre = __shfl_sync(0xffffffffu, send.re, wl);
-        const float Rim = __shfl_sync(0xffffffffu, send.im, wl);
+        const float sre = st.kc[0] == bk ? st.Rre[0].x : st.kc[1] == bk ? st.Rre[0].y : st.kc[2] == bk ? st.Rre[1].x : st.Rre[1].y;
+        const float sim = st.kc[0] == bk ? st.Rim[0].x : st.kc[1] == bk ? st.Rim[0].y : st.kc[2] == bk ? st.Rim[1].x : st.Rim[1].y;
+        const float Rre = __shfl_sync(0xffffffffu, sre, wl);
+        const float Rim = __shfl_sync(0xffffffffu, sim, wl);
         if (it < nu_h) {
             select_step<float>(a, om, rec.invD[bk & (kK - 1)], gamma, bk & (kK - 1), Rre, Rim, eta, gam, lane & 15,
                                trow, it, u, v, g, fpix, unused_pw);
@@ -872,6 +874,7 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
             const float2 gre[2] = {f2(g[0].re, g[1].re), f2(g[2].re, g[3].re)};
             const float2 gim[2] = {f2(g[0].im, g[1].im), f2(g[2].im, g[3].im)};
             const float2 ngim[2] = {f2(-g[0].im, -g[1].im), f2(-g[2].im, -g[3].im)};
+            float dre[4], dim[4];
 #pragma unroll
             for (int sl4 = 0; sl4 < 4; ++sl4) {
                 const int kc = st.kc[sl4];
@@ -888,8 +891,13 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
                     are = fma2(st.hre[sl4][pr], gGre, fma2(st.him[sl4][pr], gGim, are));
                     aim = fma2(st.hre[sl4][pr], gGim, fma2(st.nhim[sl4][pr], gGre, aim));
                 }
-                st.R[sl4].re -= are.x + are.y;
-                st.R[sl4].im -= aim.x + aim.y;
+                dre[sl4] = are.x + are.y;
+                dim[sl4] = aim.x + aim.y;
+            }
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                st.Rre[pr] = sub2(st.Rre[pr], f2(dre[2 * pr], dre[2 * pr + 1]));
+                st.Rim[pr] = sub2(st.Rim[pr], f2(dim[2 * pr], dim[2 * pr + 1]));
             }
         }
     }

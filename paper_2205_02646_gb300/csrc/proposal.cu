@@ -448,10 +448,12 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
         uint32_t key[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) key[j] = order_key(zb[j * 32 + lane] + bias[j * 32 + lane]);
-        // Bounds on the 64th largest key: at most the warp's largest key, at
-        // least the smallest of the 32 lanes' second-largest keys (those 64
-        // keys all reach it).  Its bits above the first bit where the two
-        // bounds differ are theirs, so the search starts below that bit.
+        // Bounds on the 64th largest key from the lanes' second-largest keys:
+        // at least their smallest (those 64 keys all reach it), at most their
+        // largest (64 keys over 32 lanes put two in some lane, so that lane's
+        // second largest reaches the 64th).  Its bits above the first bit
+        // where the two bounds differ are theirs, so the search starts below
+        // that bit.
         uint32_t m1 = 0, m2 = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -459,16 +461,16 @@ __global__ void shortlist_kernel(const float *z, int ldz, const float *bias, lon
             m2 = max(m2, min(m1, k));
             m1 = max(m1, k);
         }
-        const uint32_t hi = __reduce_max_sync(0xffffffffu, m1);
+        const uint32_t hi = __reduce_max_sync(0xffffffffu, m2);
         const uint32_t lo = __reduce_min_sync(0xffffffffu, m2);
         const uint32_t diff = hi ^ lo;
         const int top = diff ? 31 - __clz(diff) : -1;          // highest differing bit
         // Binary search on the remaining key bits for the 64th largest key;
         // stop early once exactly 64 keys reach the candidate (then they are
         // the set).
-        uint32_t thr = top >= 31 ? 0u : (hi & ~((2u << top) - 1u));
+        // top < 0: the bounds meet, and hi is the 64th largest key
+        uint32_t thr = top < 0 ? hi : top >= 31 ? 0u : (hi & ~((2u << top) - 1u));
         bool exact = false;
-        if (top < 0) thr = hi;                                   // all candidates equal at the top
         for (int bit = top; bit >= 0; --bit) {
             const uint32_t cand = thr | (1u << bit);
             unsigned cnt = 0;
