@@ -34,8 +34,9 @@ def flops_per_block(nu: int) -> int:
     """Arithmetic of the factored RL-JSDE path per 4x4 block (FMA = 2 flops,
     multiplications by structural zeros not counted)."""
     # row DFTs of the real window, Hermitian half only (k2 = 1..7 complex,
-    # k2 = 0 and 8 real), column DFTs (even/odd), combine
-    dft = 256 * (7 * 4 + 2 * 1) + 4 * 256 * 8 * 8 + 4 * 256 * 2
+    # k2 = 0 and 8 real); column DFTs as 8-point FFTs per parity half (56
+    # flops) with the odd half's 7 twiddles (42); the even/odd combine
+    dft = 256 * (7 * 4 + 2 * 1) + 4 * 16 * (56 + 56 + 42) + 4 * 256 * 2
     first = 256 * 64                                          # transform + scores, no update
     per_iter = 256 * 96                                       # update 32 + transform 48 + scores 16 per kappa
     scalar = 64                                               # delta, h_t(uv), g_t, synthesis
@@ -45,7 +46,7 @@ def flops_per_block(nu: int) -> int:
 def phase_flops(nu: int):
     """(initial projection + first iteration, the nu - 1 later iterations)
     of flops_per_block."""
-    dft = 256 * (7 * 4 + 2 * 1) + 4 * 256 * 8 * 8 + 4 * 256 * 2
+    dft = 256 * (7 * 4 + 2 * 1) + 4 * 16 * (56 + 56 + 42) + 4 * 256 * 2
     return dft + 256 * 64 + 64, (nu - 1) * (256 * 96 + 64)
 
 

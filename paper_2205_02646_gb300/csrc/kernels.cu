@@ -186,6 +186,36 @@ __device__ __forceinline__ const uint8_t *rec_types(const RecordF32 &r) { return
 __device__ __forceinline__ const uint8_t *rec_types(const RecordShortF32 &r) { return r.types; }
 __device__ __forceinline__ const uint8_t *rec_types(const Record<double> &r) { return r.types; }
 
+// X[i] = sum_j x_j w8^-(j i), i, j in [0, 8): radix-2 decimation in
+// frequency (twiddles 1, (1 - i)/sqrt 2, -i, (-1 - i)/sqrt 2, then -i), 52
+// real additions and multiplications instead of 64 complex products.  The same
+// code on conjugated input gives the conjugated, index-mirrored output bit
+// for bit, so mirror ties stay exact.
+template <typename T>
+__device__ __forceinline__ void dft8(const C2<T> (&x)[8], C2<T> (&X)[8])
+{
+    const T c = T(0.70710678118654752440);
+    const C2<T> s0 = cadd(x[0], x[4]), s1 = cadd(x[1], x[5]), s2 = cadd(x[2], x[6]), s3 = cadd(x[3], x[7]);
+    const C2<T> e1 = csub(x[1], x[5]), e2 = csub(x[2], x[6]), e3 = csub(x[3], x[7]);
+    const C2<T> d0 = csub(x[0], x[4]);
+    const C2<T> d1 = {c * (e1.re + e1.im), c * (e1.im - e1.re)};        // e1 (1 - i) / sqrt 2
+    const C2<T> d2 = {e2.im, -e2.re};                                    // e2 (-i)
+    const C2<T> d3 = {c * (e3.im - e3.re), -(c * (e3.re + e3.im))};      // e3 (-1 - i) / sqrt 2
+    // even outputs: 4-point DFT of s; odd outputs: 4-point DFT of d
+    const C2<T> a0 = cadd(s0, s2), a1 = cadd(s1, s3), b0 = csub(s0, s2), bm = csub(s1, s3);
+    const C2<T> b1 = {bm.im, -bm.re};
+    X[0] = cadd(a0, a1);
+    X[4] = csub(a0, a1);
+    X[2] = cadd(b0, b1);
+    X[6] = csub(b0, b1);
+    const C2<T> f0 = cadd(d0, d2), f1 = cadd(d1, d3), g0 = csub(d0, d2), gm = csub(d1, d3);
+    const C2<T> g1 = {gm.im, -gm.re};
+    X[1] = cadd(f0, f1);
+    X[5] = csub(f0, f1);
+    X[3] = cadd(g0, g1);
+    X[7] = csub(g0, g1);
+}
+
 // ------------------------------------------- initial projected residual --
 // Step 1 and the row half of step 2 for one block: gather the weighted
 // window into the four type planes x_t(p, q) and sum the row DFTs
@@ -290,22 +320,23 @@ __device__ __forceinline__ void initial_projection(const Args &a, const Rec &rec
         __syncwarp();
         rows_to_scratch<T>(acc, tb, pass, lane);
         __syncwarp();
+        // half h: cc(i) = sum_j T(2j + h, k2) w16^-((2j + h) i) = w16^-(h i) DFT8_j(T(2j + h, k2))(i)
         C2<T> cc[8][2];
+        {
+            C2<T> x[2][8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) cc[i][0] = cc[i][1] = {0, 0};
-#pragma unroll 2
-        for (int j = 0; j < 8; ++j) {
-            const int p = 2 * j + h;
-            const Vec4<T> tv = ld4(&tb[p * 16 + k2]);
-            const C2<T> tt[2] = {{tv.x, tv.y}, {tv.z, tv.w}};
+            for (int j = 0; j < 8; ++j) {
+                const Vec4<T> tv = ld4(&tb[(2 * j + h) * 16 + k2]);
+                x[0][j] = {tv.x, tv.y};
+                x[1][j] = {tv.z, tv.w};
+            }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const C2<T> tw = omc[(2 * p * i) & 31];
+            for (int u = 0; u < 2; ++u) {
+                C2<T> X[8];
+                dft8<T>(x[u], X);
+                cc[0][u] = X[0];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    cc[i][u].re += tt[u].re * tw.re - tt[u].im * tw.im;
-                    cc[i][u].im += tt[u].re * tw.im + tt[u].im * tw.re;
-                }
+                for (int i = 1; i < 8; ++i) cc[i][u] = cmul(X[i], omc[(2 * h * i) & 31]);
             }
         }
 #pragma unroll

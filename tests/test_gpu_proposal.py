@@ -209,3 +209,39 @@ def test_training_lowers_the_loss(rl):
     net = rl.Net(seed=1)
     losses = [net.train_step(x, bd, mask.shape, td, nud, lr=2e-3) for _ in range(40)]
     assert losses[-1] < 0.8 * losses[0], losses[::8]
+
+
+@pytest.mark.parametrize("tau", [-1.0, 0.1, 0.5, 0.97, 2.0])
+def test_mixed_fallback_matches_both_passes(rl, tau):
+    """With the confidence gate between the extremes, every block is
+    reconstructed either by the shortlist loop (left-out mass <= tau) or by
+    the full loop (the rest), whatever the other blocks of its chunk take:
+    restricted blocks equal the all-restricted run bit for bit, the others
+    match the plain loop."""
+    import torch
+    f, mask, y = _image(96, 128, 7)
+    nbh, nbw = 48, 64
+    nb = nbh * nbw
+    nu = 24
+    rng = np.random.default_rng(11)
+    idx = np.stack([rng.choice(1024, 64, replace=False) for _ in range(nb)])
+    missing = rng.random(nb).astype(np.float32)
+    buf = torch.from_numpy(rl.shortlist_from_indices(idx, missing=missing)).cuda()
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    lr = torch.from_numpy(y).cuda()
+    hr_p = torch.zeros((2 * 96, 2 * 128), device="cuda")
+    plan.reconstruct(lr, hr_p)
+    hr_r = torch.zeros_like(hr_p)
+    plan.reconstruct_learned(lr, hr_r, buf, max_missing=2.0)
+    hr_m = torch.full_like(hr_p, float("nan"))
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    plan.reconstruct_learned(lr, hr_m, buf, max_missing=tau, counter=cnt)
+    plan.check()
+    restricted = missing <= np.float32(tau)
+    assert int(cnt.item()) == int(restricted.sum())
+    blk = lambda t: t.cpu().numpy().reshape(nbh, 4, nbw, 4).transpose(0, 2, 1, 3).reshape(nb, 16)
+    m, r, p = blk(hr_m), blk(hr_r), blk(hr_p)
+    assert np.isfinite(m).all()                       # every block written by one of the passes
+    assert np.array_equal(m[restricted], r[restricted])
+    d = np.abs(m[~restricted] - p[~restricted]).max(axis=1) if (~restricted).any() else np.zeros(0)
+    assert (d <= 1e-4).mean() >= 0.99 if d.size else True
