@@ -37,8 +37,8 @@ def flops_per_block(nu: int) -> int:
     # k2 = 0 and 8 real); column DFTs as 8-point FFTs per parity half (56
     # flops) with the odd half's 7 twiddles (42); the even/odd combine
     dft = 256 * (7 * 4 + 2 * 1) + 4 * 16 * (56 + 56 + 42) + 4 * 256 * 2
-    first = 256 * 64                                          # transform + scores, no update
-    per_iter = 256 * 96                                       # update 32 + transform 48 + scores 16 per kappa
+    first = 256 * 62                                          # transform + scores, no update
+    per_iter = 256 * 94                                       # update 32 + transform 46 + scores 16 per kappa
     scalar = 64                                               # delta, h_t(uv), g_t, synthesis
     return dft + first + (nu - 1) * per_iter + nu * scalar
 
@@ -47,7 +47,7 @@ def phase_flops(nu: int):
     """(initial projection + first iteration, the nu - 1 later iterations)
     of flops_per_block."""
     dft = 256 * (7 * 4 + 2 * 1) + 4 * 16 * (56 + 56 + 42) + 4 * 256 * 2
-    return dft + 256 * 64 + 64, (nu - 1) * (256 * 96 + 64)
+    return dft + 256 * 62 + 64, (nu - 1) * (256 * 94 + 64)
 
 
 def fp32_peak_tflops() -> float:

@@ -503,9 +503,12 @@ __device__ __forceinline__ void greedy_loop(const Args &a, const Record<T> &rec,
                         if ((a.slot_ap >> (4 * t + sp)) & 1u) Z[sp] = cadd(Z[sp], Y[i][t]);
                 }
             } else {
-                const C2<T> S = cadd(cadd(cadd(Y[i][0], Y[i][1]), Y[i][2]), Y[i][3]);
-#pragma unroll
-                for (int sp = 0; sp < 4; ++sp) Z[sp] = csub(S, Y[i][sp]);
+                // Z_s = S - Y_s as the sum of the other three: 6 additions, no cancellation
+                const C2<T> P01 = cadd(Y[i][0], Y[i][1]), P23 = cadd(Y[i][2], Y[i][3]);
+                Z[0] = cadd(Y[i][1], P23);
+                Z[1] = cadd(Y[i][0], P23);
+                Z[2] = cadd(P01, Y[i][3]);
+                Z[3] = cadd(P01, Y[i][2]);
             }
             const C2<T> Z0 = Z[0];
             const C2<T> U = cmul(e1, Z[1]);
@@ -660,9 +663,12 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
                         if ((a.slot_ap >> (4 * t + sp)) & 1u) Z[sp] = addc(Z[sp], Y[jj][t]);
                 }
             } else {
-                const CP S = addc(addc(Y[jj][0], Y[jj][1]), addc(Y[jj][2], Y[jj][3]));
-#pragma unroll
-                for (int sp = 0; sp < 4; ++sp) Z[sp] = subc(S, Y[jj][sp]);
+                // Z_s = S - Y_s as the sum of the other three: 6 additions, no cancellation
+                const CP P01 = addc(Y[jj][0], Y[jj][1]), P23 = addc(Y[jj][2], Y[jj][3]);
+                Z[0] = addc(Y[jj][1], P23);
+                Z[1] = addc(Y[jj][0], P23);
+                Z[2] = addc(P01, Y[jj][3]);
+                Z[3] = addc(P01, Y[jj][2]);
             }
             const CP Z0 = Z[0];
             const CP U = rot(e1c, e1s, e1n, Z[1]);
