@@ -772,7 +772,7 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
         pos[(g0 >> 1) * 16 + (g0 & 1) * 8 + (r0 >> 3)] = c0;
         pos[(g1 >> 1) * 16 + (g1 & 1) * 8 + (r1 >> 3)] = c1;
         __syncwarp();
-        kw[0] = pos[lane] & (kK - 1);                  // duplicates in a caller's list leave positions unset
+        kw[0] = pos[lane] & (kK - 1);                  // ranks are a permutation: every position is written
         kw[1] = pos[32 + lane] & (kK - 1);
     }
     // R0 of the candidates at positions lane and lane + 32: Y_t(kap) =

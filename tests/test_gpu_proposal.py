@@ -245,3 +245,44 @@ def test_mixed_fallback_matches_both_passes(rl, tau):
     assert np.array_equal(m[restricted], r[restricted])
     d = np.abs(m[~restricted] - p[~restricted]).max(axis=1) if (~restricted).any() else np.zeros(0)
     assert (d <= 1e-4).mean() >= 0.99 if d.size else True
+
+
+def test_restricted_loop_with_repeated_candidates(rl):
+    """A shortlist that names some candidates twice searches the distinct
+    candidates it names: the same as the oracle with q = 0 outside them."""
+    import torch
+    f, mask, y = _image(24, 24, 3)
+    nbh, nbw = 12, 12
+    nb = nbh * nbw
+    nu = 30
+    rng = np.random.default_rng(8)
+    idx = np.zeros((nb, 64), np.int64)
+    for b in range(nb):
+        distinct = rng.choice(1024, 48, replace=False)
+        idx[b] = np.concatenate([distinct, rng.choice(distinct, 16, replace=True)])
+        rng.shuffle(idx[b])
+    buf = torch.from_numpy(rl.shortlist_from_indices(idx)).cuda()
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    lr = torch.from_numpy(y).cuda()
+    hr = torch.zeros((48, 48), device="cuda")
+    sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
+    dc = torch.zeros(nb * nu * 2, device="cuda")
+    plan.reconstruct_learned(lr, hr, buf, max_missing=1e9, sel=sel, dc=dc)
+    plan.check()
+    g_hr, g_sel = hr.cpu().numpy(), sel.cpu().numpy().reshape(nb, nu)
+    qd = oracle.frequency_weight(oracle.Params()).ravel()
+    blocks = list(range(0, nb, 7))
+    o_hr = np.full((48, 48), np.nan)
+    o_sel, o_gap = [], []
+    for b in blocks:
+        qt = np.zeros(1024)
+        qt[idx[b]] = qd[idx[b]]
+        h_b, tr = oracle.reconstruct(y.astype(np.float64), mask, oracle.Params(nu_max=nu, q_mode=2, q_table=qt),
+                                     blocks=[b], trace=True)
+        bi, bj = divmod(b, nbw)
+        o_hr[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4] = h_b[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4]
+        o_sel.append(tr["sel"][0])
+        o_gap.append(tr["gap"][0])
+    res = compare(g_hr, g_sel[blocks], o_hr, np.array(o_sel), np.array(o_gap), blocks, nbw, tol=1e-4, tie=1e-4)
+    assert not res["fails"], res["fails"][:3]
+    assert all(set(g_sel[b].tolist()) <= set(idx[b].tolist()) for b in blocks)
