@@ -7,7 +7,10 @@ GPU loop runs with ``nu_max`` iterations and records its selections; the
 block's target set is the first 64 distinct candidates it selected (the
 shortlist that would reproduce most of its model), and its iteration target
 is the number of iterations after which the remaining coefficient changes
-add up to less than ``eps`` (as a fraction of ``nu_max``).
+|gamma delta| add up to less than ``eps`` (as a fraction of ``nu_max``).
+``eps`` = 0.2 was chosen by a sweep on synthetic images (0.002 to 0.2): the
+PSNR against the plain loop stayed within 0.012 dB while the mean target fell
+from about 1 to 0.26 of ``nu_max``.
 """
 from __future__ import annotations
 
@@ -21,7 +24,7 @@ from . import rljsde, synth
 SHORTLIST = 64
 
 
-def labels_from_trace(sel, dc, nu_max: int, k: int = SHORTLIST, eps: float = 2e-3):
+def labels_from_trace(sel, dc, nu_max: int, k: int = SHORTLIST, eps: float = 0.2):
     """Targets (n, 1024) uint8 and iteration fractions (n,) from a trace."""
     import torch
     n = sel.shape[0]
