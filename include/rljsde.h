@@ -282,6 +282,20 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
                                size_t hr_pitch, const void *shortlists, float max_missing, int use_nu_hat,
                                uint16_t *sel, float *dc, int *n_restricted, void *stream);
 
+/*
+ * Measurement helper (this library's; the paper has no counterpart).  The
+ * greedy loop of Eqs. 11-17 is bound by FP32 arithmetic, so its roofline
+ * needs the device's FP32 FMA rate.  This times a kernel of independent FMA
+ * chains on every SM of the current device (packed FFMA2 and scalar FFMA
+ * variants, four 256-thread CTAs per SM), reps timed launches of each after
+ * one warm-up (reps 1..1000), with CUDA events on `stream`.  *tflops_out gets
+ * the best rate in TFLOP/s (an FMA counts 2 flops), *ms_out (may be NULL) the
+ * duration of that launch.  Synchronous; allocates nothing.  Errors:
+ * RLJSDE_ERR_INVALID_ARG (reps out of range, NULL tflops_out),
+ * RLJSDE_ERR_CUDA.
+ */
+int rljsde_fp32_peak(int reps, void *stream, double *tflops_out, float *ms_out);
+
 typedef struct {
     int n_images;
     int n_blocks;           /* target blocks over all images                  */

@@ -25,10 +25,20 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   pinned: residual and model stay exactly real, E_w non-increasing for
   gamma <= 1, identity measurement recovers conjugate-pair sparse signals
   exactly and equals two single updates per pair, direct == recurrent.
-* ``frequency_weight``   -- the paper gives no formula (Sec. IV says only that q
-  favours low frequencies): parity unpinned against the paper; the tests
-  check the stated reading's properties (1 at DC, symmetric, isotropic,
-  non-increasing in |k|, zero only at (W/2, W/2)).
+* ``frequency_weight``   -- parity unpinned: default q, its form and its square.
+  The paper gives no formula (Sec. IV, Eq. 11 says only that q favours low
+  frequencies); the tests check the stated reading's properties (1 at DC,
+  symmetric, isotropic, non-increasing in |k|, zero only at (W/2, W/2)),
+  which the same reading without the square would pass too.  No parity
+  check depends on it: the GPU tests also run q = 1 and user tables.
+* spatial weight ``w_m = rho^d_m`` (inside ``reconstruct``) -- parity
+  unpinned: w_m functional form.  The paper (Sec. III, Eq. 8) only calls the
+  weight isotropic and decaying from the window centre; the mirror/transpose
+  test pins its centring on the target block, not its form (rho^(d^2) would
+  pass it).
+* binary32 rounding of the argmax (reading of Eqs. 10-11, Table I's
+  complex64 tables) -- pinned: two scores 2^-40 apart tie after rounding and
+  go to the lower index, 2^-20 apart they do not.
 * ``count_local_masks``  -- pinned: Table I (64 local masks for a 32-pixel
   period) and closed-form counts for small tiles.
 """

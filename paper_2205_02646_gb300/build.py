@@ -10,7 +10,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 SRC = [os.path.join(PKG, "csrc", "kernels.cu"), os.path.join(PKG, "csrc", "proposal.cu"),
-       os.path.join(PKG, "csrc", "plan.cpp")]
+       os.path.join(PKG, "csrc", "peak.cu"), os.path.join(PKG, "csrc", "plan.cpp")]
 DEPS = SRC + [os.path.join(PKG, "csrc", "rljsde_internal.h"), os.path.join(ROOT, "include", "rljsde.h")]
 LIB = os.path.join(PKG, "librljsde.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -26,7 +26,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in DEPS):
         return LIB
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "3", "-shared",
+    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "4", "-shared",
            "-Xcompiler", "-fPIC,-fopenmp,-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
            "-o", tmp] + SRC + ["-lgomp", "-lcublas"]
     if verbose:

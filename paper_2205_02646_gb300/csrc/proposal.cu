@@ -783,6 +783,7 @@ struct rljsde_net {
     __nv_bfloat16 *w16 = nullptr;
     __nv_bfloat16 *head16 = nullptr;     // kOutPad x 288, zero-padded head rows
     int step = 0;
+    int sm_count = 1;                    // SMs of the device the network lives on
     cublasHandle_t blas = nullptr;
     // training buffers, sized for `cap` samples
     int cap = 0;
@@ -880,6 +881,12 @@ int rljsde_net_create(rljsde_net_t **out, uint64_t seed)
               cudaMalloc(&n->v, b) == cudaSuccess && cudaMalloc(&n->w16, (size_t)kParams * 2) == cudaSuccess &&
               cudaMalloc(&n->head16, (size_t)kOutPad * kHeadIn * 2) == cudaSuccess;
     if (!ok || cublasCreate(&n->blas) != CUBLAS_STATUS_SUCCESS) { rljsde_net_destroy(n); return RLJSDE_ERR_OUT_OF_MEMORY; }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n->sm_count < 1) {
+        rljsde_net_destroy(n);
+        return RLJSDE_ERR_CUDA;
+    }
     // He-style uniform init from a SplitMix64 stream; biases zero
     std::vector<float> h(kParams, 0.f);
     uint64_t st = seed;
@@ -972,7 +979,7 @@ static int loss_grad(rljsde_net *net, const float *x, const int32_t *blocks, int
     dim3 gf((kHeadIn + 63) / 64, (n + 63) / 64);
     gemm_kernel<<<gf, 256, 0, s>>>(n, kHeadIn, kOut, net->gz, kOut, 1, r + kWh, kHeadIn, 1, net->gf, kHeadIn, 0.f);
     scatter_centre_kernel<<<grid_for((long long)n * kC * 64, 256), 256, 0, s>>>(net->gf, net->a3, net->g3, n);
-    const int wg = 2 * 152;
+    const int wg = 2 * net->sm_count;
     ConvGeom g3{n, kC, 8, 8, 8, 8, 1, 2, net->origin, lr_h, lr_w};
     conv_bwd_w_kernel<kC><<<wg, 256, 0, s>>>(net->g3, net->a2, net->grad + kW3, net->grad + kB3, g3);
     conv_bwd_data_kernel<kC><<<grid_for((long long)n * 64, 128), 128, 0, s>>>(net->g3, r + kW3, net->a2, net->g2, g3);
@@ -1063,7 +1070,7 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
     __nv_bfloat16 *f16 = reinterpret_cast<__nv_bfloat16 *>(w); w += al(chunk * kHeadIn * 2);
     float *z = reinterpret_cast<float *>(w);
     const float *r = net->rounded, *b = net->master;
-    const int cap = 8 * 152;
+    const int cap = 8 * (plan->sm_count > 0 ? plan->sm_count : 1);     // 8 CTAs per SM at most
     auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
     image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
     ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
@@ -1117,7 +1124,7 @@ int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, c
     float *f = reinterpret_cast<float *>(w);   w += al(chunk * kHeadIn * 4);
     float *z = reinterpret_cast<float *>(w);
     const float *r = net->rounded, *b = net->master;
-    const int cap = 8 * 152;
+    const int cap = 8 * (plan->sm_count > 0 ? plan->sm_count : 1);     // 8 CTAs per SM at most
     auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
     image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
     ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};

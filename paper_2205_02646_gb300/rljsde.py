@@ -61,7 +61,7 @@ EXPORTS = ["rljsde_default_params", "rljsde_plan_create", "rljsde_plan_create_ba
            "rljsde_graph_launch", "rljsde_net_create", "rljsde_net_destroy", "rljsde_net_num_params",
            "rljsde_net_get_params", "rljsde_net_set_params", "rljsde_net_patches", "rljsde_net_gradient",
            "rljsde_net_train_step", "rljsde_net_logits", "rljsde_propose_workspace", "rljsde_propose",
-           "rljsde_reconstruct_learned", "rljsde_propose_noalloc"]
+           "rljsde_reconstruct_learned", "rljsde_propose_noalloc", "rljsde_fp32_peak"]
 
 SHORTLIST_BYTES = 136
 
@@ -109,6 +109,7 @@ def _lib():
         lib.rljsde_propose.argtypes = [vp, vp, vp, sz, vp, vp, sz, vp]
         lib.rljsde_reconstruct_learned.argtypes = [vp, vp, sz, vp, sz, vp, f, i, vp, vp, vp, vp]
         lib.rljsde_propose_noalloc.argtypes = [vp, vp, vp, sz, vp, vp]
+        lib.rljsde_fp32_peak.argtypes = [i, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(f)]
         lib.rljsde_status_string.argtypes = [i]
         lib.rljsde_status_string.restype = ctypes.c_char_p
         _LIB = lib
@@ -299,6 +300,14 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def fp32_peak(reps=5, stream=None) -> dict:
+    """FP32 FMA throughput of the current device (``rljsde_fp32_peak``)."""
+    tf, ms = ctypes.c_double(), ctypes.c_float()
+    _ok(_lib().rljsde_fp32_peak(int(reps), _stream_ptr(stream), ctypes.byref(tf), ctypes.byref(ms)),
+        "rljsde_fp32_peak")
+    return dict(tflops=tf.value, ms=ms.value)
 
 
 def shortlist_view(buf, n_blocks):

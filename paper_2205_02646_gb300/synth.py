@@ -40,7 +40,7 @@ import numpy as np
 __all__ = [
     "image", "recurrent_mask", "random_mask", "measure", "workload",
     "batch_sizes", "OPAQUE_OFFSETS", "image_torch", "measure_torch",
-    "APERTURE_SETS", "aperture_mask", "apertures_of",
+    "APERTURE_SETS", "aperture_mask", "apertures_of", "workload_config",
 ]
 
 # Named aperture sets for recurrent layouts other than three-quarter
@@ -199,6 +199,12 @@ _WORKLOADS = {
     "rljsde_4096x3072_t4": dict(h=3072, w=4096, n_sin=2048, n_edges=256, sigma=0.0,  tile=4, seed=5000, mseed=12),
     "rljsde_1200x1200":  dict(h=1200, w=1200, n_sin=256,  n_edges=32,  sigma=0.005, tile=16, seed=6000, mseed=13),
 }
+
+
+def workload_config(name: str) -> dict:
+    """Recipe of a named workload: HR size, sinusoids, edges, noise, LR mask
+    tile and seeds."""
+    return dict(_WORKLOADS[name])
 
 
 def workload(name: str, index: int = 0, random: bool = False):

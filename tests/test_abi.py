@@ -21,7 +21,7 @@ def rl():
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "rljsde.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rljsde_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(rljsde_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_exports_every_declared_symbol(rl):

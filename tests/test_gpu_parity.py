@@ -223,16 +223,20 @@ def test_batch_graph_and_autotune(rl):
     plan.check()
     for a, b in zip(hr_a, hr_b):
         assert torch.equal(a, b)
-    # the images of the batch against the oracle on a few blocks each
+    # the images of the batch against the oracle on a few blocks each: the
+    # batch output equals a traced single-image launch bit for bit, whose
+    # selections let parity.compare excuse a block only for a near-tie at its
+    # own first differing iteration
     for m, y, hr in zip(masks, ys, hr_b):
-        nbw = m.shape[1] // 2
-        blocks = np.array([0, nbw - 1, (m.shape[0] // 2 - 1) * nbw, 5 * nbw + 5])
-        ohr, tr = oracle_run(y, m, blocks=blocks, nu_max=20)
+        nbh, nbw = m.shape[0] // 2, m.shape[1] // 2
+        blocks = np.array([0, nbw - 1, (nbh - 1) * nbw, nbh * nbw - 1, 5 * nbw + 5, (nbh // 2) * nbw + nbw // 2])
+        single = gpu_run(rl, y, m, nu_max=20)
         g = hr.cpu().numpy()
-        for b in blocks:
-            bi, bj = divmod(int(b), nbw)
-            err = np.abs(g[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4] - ohr[4 * bi:4 * bi + 4, 4 * bj:4 * bj + 4])
-            assert err.max() < TOL or tr["gap"].min() < TIE
+        assert np.array_equal(single["hr"], g)
+        ohr, tr = oracle_run(y, m, blocks=blocks, nu_max=20)
+        res = compare(g, single["sel"][blocks], ohr, tr["sel"], tr["gap"], blocks, nbw, TOL, TIE,
+                      gpu_dc=single["dc"][blocks], orc_dc=tr["dc"])
+        check(res, max_tie_frac=0.0)
 
 
 def test_random_mask_tables_built_in_kernel_vs_oracle(rl):

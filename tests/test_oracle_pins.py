@@ -243,6 +243,33 @@ def test_structural_conjugate_tie_goes_to_lower_index():
     assert k < mirror(k, W)
 
 
+def test_argmax_takes_binary32_rounded_scores():
+    """Reading of Eqs. 10-11: the argmax compares scores rounded to binary32
+    (the precision of the paper's complex64 tables), lowest index on ties.
+    Identity measurement of two unit atoms: both project to W^2 exactly, so
+    their scores are q_k * W^2.  A frequency weight 2^-40 above 1 on the
+    higher index wins in FP64 but rounds to the same binary32 value, so the
+    lower index must win; 2^-20 above 1 survives the rounding and must win."""
+    W = 8
+    pix = [[(e, g)] for e in range(W) for g in range(W)]
+    w = np.ones(W * W)
+    k1, k2 = np.meshgrid(np.arange(W), np.arange(W), indexing="ij")
+    lo, hi = 1 * W + 2, 5 * W + 3                        # not each other's mirror
+    assert mirror(lo, W) != hi
+    atom = lambda k: np.exp(2j * np.pi * ((k // W) * k1 + (k % W) * k2) / W).ravel()
+    y = atom(lo) + atom(hi)
+    for bump, want in ((2.0 ** -40, lo), (2.0 ** -20, hi)):
+        q = np.full(W * W, 0.5)
+        q[lo], q[hi] = 1.0, 1.0 + bump
+        out = oracle.window_solve(pix, w, y, oracle.Params(window=W, nu_max=1, gamma_odc=1.0, q_mode=2, q_table=q))
+        assert out["sel"][0] == want, (bump, out["sel"][0])
+    # the FP64 gap the oracle reports still sees the 2^-40 difference
+    q = np.full(W * W, 0.5)
+    q[lo], q[hi] = 1.0, 1.0 + 2.0 ** -40
+    out = oracle.window_solve(pix, w, y, oracle.Params(window=W, nu_max=1, gamma_odc=1.0, q_mode=2, q_table=q))
+    assert out["gap"][0] < 1e-10
+
+
 # --- image-level: direct == recurrent, local-mask counts (Table I) ----------
 def test_direct_equals_recurrent_w16_full_image():
     f, mask, y = synth.workload("rljsde_64x64")
