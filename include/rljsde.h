@@ -200,11 +200,16 @@ int rljsde_graph_launch(const rljsde_plan_t *plan, void *stream);
  * extension, which predicts per block the 64 candidates (of Eq. 11's 1024)
  * the greedy loop is likely to select, so the loop can search those only.
  * ---------------------------------------------------------------------- */
-typedef struct rljsde_net rljsde_net_t;   /* weights, Adam state, cuBLAS handle */
+typedef struct rljsde_net rljsde_net_t;   /* weights, Adam state, packed head weights */
 
 /* One block's proposal (device layout, 136 bytes): candidate indices
- * sigma * W + rho, the network's expected number of likely candidates left
- * out (sum of sigmoid over the rest), and its iteration output. */
+ * sigma * W + rho of the 64 largest logits z (ranked by z truncated to
+ * bfloat16 precision, i.e. the upper 16 bits of its order-preserving integer
+ * image; ties to the lower index; in increasing index order); `missing`, the
+ * network's expected number of the plain loop's candidates left out: the sum
+ * over the other candidates of the calibrated probability sigmoid(z - log w),
+ * w the positive weight of the network's last training step (1 before any);
+ * and its iteration output. */
 typedef struct {
     uint16_t idx[64];
     float missing;
@@ -239,13 +244,17 @@ int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, 
                       float *z_out, void *stream);
 /* Device workspace bytes rljsde_propose needs for a single-image plan. */
 size_t rljsde_propose_workspace(const rljsde_plan_t *plan);
-/* Run the network over the whole image (conv1 on the CUDA cores, conv2 and
- * conv3 on the tensor cores with bfloat16 input taps and FP32 accumulation,
- * then the head as one BF16 GEMM per chunk of blocks; a tensor-core wait
- * that gives up is reported by rljsde_check) and write one rljsde_shortlist per block
- * (device, n_blocks entries, block order bi * (2 lr_w / 4) + bj).
- * Asynchronous; the caller owns shortlists and workspace.  The network reads
- * opaque-sub-pixel codes: plans of the three-quarter layout only. */
+/* Run the network over the whole image and write one rljsde_shortlist per
+ * block (device, n_blocks entries, block order bi * (2 lr_w / 4) + bj):
+ * conv1 on the CUDA cores, conv2 and conv3 on the tensor cores (bfloat16
+ * input taps, FP32 accumulation), then one kernel that gathers each block's
+ * head features, multiplies them by the head on the tensor cores (bfloat16
+ * operands, FP32 accumulation in tensor memory) and selects the 64 largest
+ * logits on the SM, so the logits never reach device memory.  A tensor-core
+ * or copy wait that gives up is reported by rljsde_check.  Asynchronous; the
+ * caller owns shortlists and workspace (rljsde_propose_workspace bytes:
+ * 212 bytes per L-pixel).  The network reads opaque-sub-pixel codes: plans
+ * of the three-quarter layout only. */
 int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
                    void *shortlists, void *workspace, size_t workspace_bytes, void *stream);
 /*
@@ -259,15 +268,14 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
  * The scratch is one fixed 32 MiB array inside the library, so every GPU
  * that loads the library holds it until the process exits.  Images whose
  * working set does not fit are rejected with RLJSDE_ERR_BAD_SHAPE: about
- * 130,000 L-pixels at most (for example 360 x 360 L-pixels, a 720 x 720 HR
- * image).  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the one array: two calls whose work overlaps on the GPU
- * (different streams, or different host threads) race and corrupt each
- * other's results, so serialise them.  Nothing in the array needs to start
- * at zero; each call overwrites what it reads.  The head is computed with
- * the library's own FP32 GEMM on the same bfloat16-rounded operands as
- * rljsde_propose, so results agree up to summation order.  Arguments,
+ * 158,000 L-pixels at most (212 bytes each; for example 396 x 396 L-pixels,
+ * a 792 x 792 HR image).  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: two calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race and corrupt
+ * each other's results, so serialise them.  Nothing in the array needs to
+ * start at zero; each call overwrites what it reads.  It runs the same
+ * kernels as rljsde_propose, so the shortlists are identical.  Arguments,
  * output and the remaining errors are those of rljsde_propose.
  */
 int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,

@@ -28,7 +28,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "4", "-shared",
            "-Xcompiler", "-fPIC,-fopenmp,-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
-           "-o", tmp] + SRC + ["-lgomp", "-lcublas"]
+           "-o", tmp] + SRC + ["-lgomp"]
     if verbose:
         cmd.insert(4, "-Xptxas=-v")
     subprocess.check_call(cmd)

@@ -19,7 +19,6 @@
 //   output.
 // Training runs on 16x16 L-pixel patches (rows/cols [2bi - 8, 2bi + 8)), whose
 // centre features equal those of the whole-image pass.
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -37,7 +36,6 @@ namespace net {
 
 constexpr int kC = 32;
 constexpr int kOut = 1025;
-constexpr int kOutPad = 1040;    // head rows padded so the BF16 GEMM sees 16-element-aligned strides
 constexpr int kHeadIn = 9 * kC;
 // flat parameter layout
 constexpr int kW1 = 0, kB1 = kW1 + kC * 5 * 9, kW2 = kB1 + kC, kB2 = kW2 + kC * kC * 9, kW3 = kB2 + kC,
@@ -51,13 +49,6 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, float *roun
         dst[i] = b;
         rounded[i] = __bfloat162float(b);
     }
-}
-
-// Head weights in bfloat16, padded with zero rows to kOutPad x 288.
-__global__ void head_pad_kernel(const float *wh, __nv_bfloat16 *out, int rows, int rows_pad, int cols)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows_pad * cols; i += gridDim.x * blockDim.x)
-        out[i] = i < rows * cols ? __float2bfloat16_rn(wh[i]) : __float2bfloat16_rn(0.f);
 }
 
 // Input planes of one patch per sample: x[n][5][16][16], plus its origin.
@@ -381,183 +372,6 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n,
     }
 }
 
-// ---------------------------------------------------- whole-image pass --
-// im2col of the head: f[b][c * 9 + t] (bf16) for block b = by * nbw + bx of a
-// chunk, from a3[c][nbh][nbw] with zero padding, for tiles of 32 consecutive
-// blocks per CTA: the 32 x 288
-// values are gathered with reads that run along the blocks of a tile
-// (coalesced), staged as bfloat16 in shared memory, and written out as one
-// contiguous 18 KB row range with 16-byte stores.
-constexpr int kFeatTile = 32;
-__global__ void __launch_bounds__(256) head_features_tile_kernel(const float *a3, int nbh, int nbw, long long b0,
-                                                                 int nb, __nv_bfloat16 *f)
-{
-    // blockDim.x must be 256 (8 threads per block of the tile)
-    // rows padded to 296 bfloat16 (592 bytes): bank groups of consecutive blocks differ
-    constexpr int kRow = kHeadIn + 8;
-    __shared__ __align__(16) __nv_bfloat16 tile[kFeatTile * kRow];
-    const int n_tiles = (nb + kFeatTile - 1) / kFeatTile;
-    for (int tl = blockIdx.x; tl < n_tiles; tl += gridDim.x) {
-        const int first = tl * kFeatTile;
-        const int n = nb - first < kFeatTile ? nb - first : kFeatTile;
-        // thread: block bt of the tile, features ct = ct0 + 8 i
-        const int bt = threadIdx.x % kFeatTile, ct0 = threadIdx.x / kFeatTile;
-        const long long b = b0 + first + bt;
-        const int by0 = (int)(b / nbw), bx0 = (int)(b - (long long)by0 * nbw);
-        const long long plane = (long long)nbh * nbw;
-#pragma unroll 4
-        for (int ct = ct0; ct < kHeadIn; ct += 256 / kFeatTile) {
-            const int c = ct / 9, t = ct - 9 * c;
-            const int by = by0 + t / 3 - 1, bx = bx0 + t % 3 - 1;
-            float v = 0.f;
-            if (bt < n && by >= 0 && by < nbh && bx >= 0 && bx < nbw) v = a3[c * plane + (long long)by * nbw + bx];
-            tile[bt * kRow + ct] = __float2bfloat16_rn(v);
-        }
-        __syncthreads();
-        uint4 *dst = reinterpret_cast<uint4 *>(f + (long long)first * kHeadIn);
-        const int n16 = n * (kHeadIn * 2 / 16);         // 36 x 16 bytes per block
-        for (int i = threadIdx.x; i < n16; i += blockDim.x) {
-            const int blk = i / (kHeadIn * 2 / 16), part = i - blk * (kHeadIn * 2 / 16);
-            dst[i] = reinterpret_cast<const uint4 *>(tile + blk * kRow)[part];
-        }
-        __syncthreads();
-    }
-}
-
-// Per block (one warp): logits + bias -> shortlist of the 64 largest (ties to
-// the lower index), the expected number of likely candidates left out
-// (sum of sigmoid over the rest), and the iteration output.
-__device__ __forceinline__ uint32_t order_key(float v)
-{
-    // order-preserving unsigned key of a float
-    const uint32_t u = __float_as_uint(v);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float key_value(uint32_t k)
-{
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
-
-__global__ void shortlist_kernel(const float *z, int ldz, const float *bias, long long b0, int nb, Shortlist *out)
-{
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    for (long long bl = (long long)blockIdx.x * wpb + wib; bl < nb; bl += (long long)gridDim.x * wpb) {
-        // z rows are relative to the chunk, shortlists are indexed by block
-        const float *zb = z + bl * ldz;
-        uint32_t key[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) key[j] = order_key(zb[j * 32 + lane] + bias[j * 32 + lane]);
-        // Bounds on the 64th largest key from the lanes' second-largest keys:
-        // at least their smallest (those 64 keys all reach it), at most their
-        // largest (64 keys over 32 lanes put two in some lane, so that lane's
-        // second largest reaches the 64th).  Its bits above the first bit
-        // where the two bounds differ are theirs, so the search starts below
-        // that bit.
-        uint32_t m1 = 0, m2 = 0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const uint32_t k = key[j];
-            m2 = max(m2, min(m1, k));
-            m1 = max(m1, k);
-        }
-        const uint32_t hi = __reduce_max_sync(0xffffffffu, m2);
-        const uint32_t lo = __reduce_min_sync(0xffffffffu, m2);
-        const uint32_t diff = hi ^ lo;
-        const int top = diff ? 31 - __clz(diff) : -1;          // highest differing bit
-        // Binary search on the remaining key bits for the 64th largest key;
-        // stop early once exactly 64 keys reach the candidate (then they are
-        // the set).
-        // top < 0: the bounds meet, and hi is the 64th largest key
-        uint32_t thr = top < 0 ? hi : top >= 31 ? 0u : (hi & ~((2u << top) - 1u));
-        bool exact = false;
-        for (int bit = top; bit >= 0; --bit) {
-            const uint32_t cand = thr | (1u << bit);
-            unsigned cnt = 0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) cnt += key[j] >= cand;
-            cnt = __reduce_add_sync(0xffffffffu, cnt);
-            if (cnt >= (unsigned)kShortlist) thr = cand;
-            if (cnt == (unsigned)kShortlist) { exact = true; break; }   // warp-uniform
-        }
-        Shortlist &sl = out[b0 + bl];
-        float rest = 0.f;
-        if (exact) {
-            // exactly the keys >= thr, in lane-major order
-            int mine = 0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) mine += key[j] >= thr;
-            int base = mine;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, base, o);
-                if (lane >= o) base += y;
-            }
-            int pos = base - mine;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (key[j] >= thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-key_value(key[j])));
-            for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
-            if (lane == 0) {
-                sl.missing = rest;
-                sl.nu_frac = zb[1024] + bias[1024];
-            }
-            continue;
-        }
-        // thr is the 64th largest key: take keys > thr, then keys == thr by increasing index
-        int above = 0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) above += key[j] > thr;
-        const int above_total = (int)__reduce_add_sync(0xffffffffu, (unsigned)above);
-        int base = above;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, base, o);
-            if (lane >= o) base += y;
-        }
-        base -= above;                           // exclusive prefix
-        int pos = base;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (key[j] > thr) sl.idx[pos++] = (uint16_t)(j * 32 + lane);
-        // equal keys, in increasing candidate index k = j * 32 + lane
-        int slot = above_total;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const unsigned eq = __ballot_sync(0xffffffffu, key[j] == thr);
-            const int before = __popc(eq & ((1u << lane) - 1));
-            if (((eq >> lane) & 1u) && slot + before < kShortlist) sl.idx[slot + before] = (uint16_t)(j * 32 + lane);
-            slot += __popc(eq);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (key[j] < thr) rest += __frcp_rn(1.f + __expf(-key_value(key[j])));
-        for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
-        if (lane == 0) {
-            sl.missing = rest;
-            sl.nu_frac = zb[1024] + bias[1024];
-        }
-    }
-}
-
-// Head im2col for the no-allocation path: the same features as
-// head_features_tile_kernel, rounded through bfloat16 but stored as float so the
-// FP32 GEMM kernel multiplies exactly the operands the BF16 GEMM would.
-__global__ void head_features_f32_kernel(const float *a3, int nbh, int nbw, long long b0, int nb, float *f)
-{
-    const long long total = (long long)nb * kHeadIn;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long b = b0 + i / kHeadIn;
-        const int j = (int)(i % kHeadIn), c = j / 9, t = j % 9;
-        const int by = (int)(b / nbw) + t / 3 - 1, bx = (int)(b % nbw) + t % 3 - 1;
-        float v = 0.f;
-        if (by >= 0 && by < nbh && bx >= 0 && bx < nbw) v = a3[((long long)c * nbh + by) * nbw + bx];
-        f[i] = __bfloat162float(__float2bfloat16_rn(v));
-    }
-}
-
 // ------------------------------------------- tensor-core convolution --
 // conv2 / conv3 of the whole-image pass as an implicit GEMM on the 5th-gen
 // tensor cores: D[128 output positions][32 channels] = A[128][288] x B[288][32]
@@ -741,10 +555,456 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
 }
 }  // namespace tc
 
+// ------------------------------------------ fused head and shortlist --
+// The head and the top-64 selection of the whole-image pass in one kernel on
+// the 5th-gen tensor cores.  Per tile of 128 consecutive blocks:
+//   - four gather warps read each block's 3x3 block-grid neighbourhood of
+//     conv3 (288 features, K index t * 32 + ci as in conv_tc_kernel), round
+//     it to bfloat16 and store it in shared memory as the A operand;
+//   - one issuer thread streams the head weights (bfloat16, pre-packed in the
+//     core-matrix layout, 32 rows per chunk) through a ring of shared-memory
+//     slots with bulk copies and issues, per chunk, 18 tcgen05.mma (M 128,
+//     N 32, K 16) into one of two 32-column accumulators in tensor memory;
+//   - four consumer warps (warp w owns tensor-memory lanes 32w .. 32w + 31,
+//     one block per lane) read each chunk's logits, add the bias, and keep
+//     only a 16-bit order key per candidate: the upper half of the
+//     order-preserving integer image of the FP32 logit, i.e. the logit
+//     truncated to bfloat16 precision.  Two keys share a 32-bit word; the
+//     keys of chunks 0..27 go back into tensor memory (columns 0..447), the
+//     last four chunks' into shared memory.
+// Once a tile's logits are in, each consumer thread finds its block's 64th
+// largest key by bisection over the key bits (counting with packed 16-bit
+// compares), starting from the bracket given by the chunks' second-largest
+// keys, and writes the candidates above it plus, of those equal to it, the
+// lowest indices.  The 1024 x 4-byte logits of a block never leave the SM.
+// `missing` sums sigmoid(z - offset) over the candidates left out: the sum
+// over all candidates (exact FP32 logits, accumulated as the chunks arrive)
+// minus that over the selected ones (their truncated logits).  The iteration
+// output (head row 1024) is kept in FP32.
+//
+// Waits are bounded (about 2 s each); a wait that gives up sets bit 2 of the
+// status word, makes the other roles leave their loops, and the CTA drains
+// its copies and tensor-core work in flight before freeing tensor memory.
+namespace hd {
+constexpr int kM = 128;                                   // blocks per tile (MMA M, tensor-memory lanes)
+constexpr int kNC = 32;                                   // candidates per chunk (MMA N)
+constexpr int kChunks = 1024 / kNC;                       // 32 candidate chunks
+constexpr int kChunksPerTile = kChunks + 1;               // + head rows 1024..1039 (N = 16)
+constexpr int kTmemKeyChunks = 28;                        // chunks whose keys stay in tensor memory
+constexpr int kKeyWords = kNC / 2;                        // 16 words of two 16-bit keys per chunk
+constexpr uint32_t kAccCol = kTmemKeyChunks * kKeyWords;  // 448: accumulators at 448 and 480
+constexpr uint32_t kTmemCols = 512;
+constexpr int kSmemKeyWords = (kChunks - kTmemKeyChunks) * kKeyWords;   // 64 per block
+constexpr int kSmemKeyStride = kSmemKeyWords + 1;                       // 65: rows start in distinct banks
+constexpr uint32_t kLBO = 128, kSBO = (kHeadIn / 8) * 128;              // 4608
+constexpr uint32_t kABytes = (kM / 8) * kSBO;                           // 73,728
+constexpr uint32_t kBChunkBytes = (kNC / 8) * kSBO;                     // 18,432
+constexpr uint32_t kBExtraBytes = 2 * kSBO;                             // 9,216: 16 rows
+constexpr uint32_t kPackedBytes = kChunks * kBChunkBytes + kBExtraBytes; // 599,040
+constexpr int kSlots = 4;
+constexpr int kBias = 1040;
+constexpr uint32_t kOffB = kABytes;
+constexpr uint32_t kOffKeys = kOffB + kSlots * kBChunkBytes;
+constexpr uint32_t kOffBias = kOffKeys + kM * kSmemKeyStride * 4;
+constexpr uint32_t kOffBar = kOffBias + kBias * 4;
+// barriers: a_full, a_free, b_full[4], b_empty[4], acc_full[2], acc_empty[2]
+constexpr int kBarAFull = 0, kBarAFree = 1, kBarBFull = 2, kBarBEmpty = 2 + kSlots, kBarAccFull = 2 + 2 * kSlots,
+              kBarAccEmpty = kBarAccFull + 2, kNumBars = kBarAccEmpty + 2;
+constexpr uint32_t kOffMisc = kOffBar + kNumBars * 8;     // tensor-memory address, abort flag
+constexpr uint32_t kSmem = kOffMisc + 16;
+static_assert(kSmem <= 227 * 1024, "fused head operands must fit in shared memory");
+static_assert(kOffB % 128 == 0 && kOffKeys % 16 == 0 && kOffBias % 16 == 0 && kOffBar % 8 == 0, "alignment");
+constexpr int kConsumers = 128, kGatherers = 128;
+constexpr int kThreads = kConsumers + kGatherers + 32;   // + the issuer warp
+// D FP32, A and B bfloat16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
+           (1ull << 46);                              // descriptor version 1, no swizzle
+}
+
+// Wait for phase `parity` of a shared-memory mbarrier; give up after about
+// 2 s, or as soon as another role has raised the abort flag.
+__device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    const uint64_t t0 = tc::now_ns();
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((i & 255) == 255 && (*abort || tc::now_ns() - t0 > 2000000000ull)) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// the same without waiting: tensor-memory loads in flight until wait_ld()
+__device__ __forceinline__ void ld32_nw(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void ld1(uint32_t taddr, uint32_t &r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 : "memory");
+}
+
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 16-bit key: upper half of the order-preserving image of a float
+__device__ __forceinline__ uint32_t key16(float z)
+{
+    const uint32_t u = __float_as_uint(z);
+    return (u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u)) >> 16;
+}
+// the midpoint of the floats whose key is k (lower 16 bits 0x8000): within
+// half a bfloat16 step of each of them, and not biased to either side
+__device__ __forceinline__ float key16_value(uint32_t k)
+{
+    const uint32_t u = (k << 16) | 0x8000u;
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Number of this lane's block's keys >= cand (all 32 lanes of the warp call
+// it together: the tensor-memory loads are warp-collective).
+__device__ __forceinline__ uint32_t count_ge(uint32_t trow, const uint32_t *skeys, uint32_t cand)
+{
+    const uint32_t c2 = cand | (cand << 16);
+    uint32_t acc = 0;
+#pragma unroll 1
+    for (int i = 0; i < kTmemKeyChunks / 2; i += 2) {
+        uint32_t v[32], u[32];
+        ld32_nw(trow + 32 * i, v);
+        ld32_nw(trow + 32 * i + 32, u);
+        wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc = __vsub2(acc, __vcmpgeu2(v[j], c2));
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc = __vsub2(acc, __vcmpgeu2(u[j], c2));
+    }
+#pragma unroll 8
+    for (int j = 0; j < kSmemKeyWords; ++j) acc = __vsub2(acc, __vcmpgeu2(skeys[j], c2));
+    return (acc & 0xFFFFu) + (acc >> 16);
+}
+
+// a3: conv3 output [32][nbh][nbw]; packed: head weights (see pack_head_kernel);
+// bias: 1025 FP32; out: one Shortlist per block.
+__global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a3, int nbh, int nbw,
+                                                                  const unsigned char *packed, const float *bias,
+                                                                  float offset, Shortlist *out, int *status)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *A = sm;
+    uint32_t *skeys_all = reinterpret_cast<uint32_t *>(sm + kOffKeys);
+    float *bias_s = reinterpret_cast<float *>(sm + kOffBias);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kOffMisc);
+    volatile int *abort = reinterpret_cast<volatile int *>(sm + kOffMisc + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar0 = tc::saddr(sm + kOffBar);
+    auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+
+    for (int i = tid; i < kBias; i += blockDim.x) bias_s[i] = i < kOut ? bias[i] : 0.f;
+    if (tid == 0) {
+        for (int i = 0; i < kNumBars; ++i) {
+            const uint32_t count = i == kBarAFull ? kGatherers : i >= kBarAccEmpty ? kConsumers : 1u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(count) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const long long nb = (long long)nbh * nbw;
+    const long long n_tiles = (nb + kM - 1) / kM;
+    const float half_off = 0.5f * offset;
+
+    if (warp < 4) {
+        // ------------------------------------------------ consumers --
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        const int r = 32 * warp + lane;
+        uint32_t *skeys = skeys_all + r * kSmemKeyStride;
+        long long g = 0;
+        bool ok = true;
+        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            const long long b = tile * kM + r;
+            const bool valid = b < nb;
+            uint32_t lo = 0xFFFFu, hi = 0;
+            float tsum = 0.f, nu = 0.f;
+            for (int c = 0; c < kChunksPerTile; ++c, ++g) {
+                const int ab = (int)(g & 1);
+                const bool got = wait(bar(kBarAccFull + ab), (uint32_t)((g >> 1) & 1), abort);
+                if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (c == kChunks) {
+                    uint32_t v0;
+                    ld1(trow + kAccCol + 32 * ab, v0);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    arrive(bar(kBarAccEmpty + ab));
+                    nu = __uint_as_float(v0) + bias_s[1024];
+                    continue;
+                }
+                uint32_t v[32];
+                ld32(trow + kAccCol + 32 * ab, v);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                arrive(bar(kBarAccEmpty + ab));
+                uint32_t pk[16], m1 = 0, m2 = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float z = __uint_as_float(v[j]) + bias_s[kNC * c + j];
+                    tsum += tanh_approx(fmaf(0.5f, z, -half_off));
+                    const uint32_t k = key16(z);
+                    m2 = max(m2, min(m1, k));
+                    m1 = max(m1, k);
+                    if (j < 16) pk[j] = k;
+                    else pk[j - 16] |= k << 16;
+                }
+                lo = min(lo, m2);
+                hi = max(hi, m2);
+                if (c < kTmemKeyChunks) {
+                    st16(trow + kKeyWords * c, pk);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < 16; ++w) skeys[(c - kTmemKeyChunks) * kKeyWords + w] = pk[w];
+                }
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            // bisection for the 64th largest key in [lo, hi]
+            const uint32_t diff = hi ^ lo;
+            const int top = diff ? 31 - __clz(diff) : -1;
+            uint32_t thr = top < 0 ? hi : (hi & ~((2u << top) - 1u));
+            int bit = top;
+            bool active = top >= 0;
+            while (__any_sync(0xffffffffu, active)) {
+                const uint32_t cand = active ? (thr | (1u << bit)) : 0u;
+                const uint32_t cnt = count_ge(trow, skeys, cand);
+                if (active) {
+                    if (cnt >= (uint32_t)kShortlist) thr = cand;
+                    if (cnt == (uint32_t)kShortlist || --bit < 0) active = false;
+                }
+            }
+            // candidates above thr, then those equal to it by increasing index
+            const uint32_t n_above = count_ge(trow, skeys, thr < 0xFFFFu ? thr + 1 : 0x10000u);
+            int eq_left = kShortlist - (int)(thr < 0xFFFFu ? n_above : 0u);
+            int pos = 0;
+            float tsel = 0.f;
+            Shortlist *sl = out + b;
+            auto take = [&](uint32_t k, int idx) {
+                const bool t = k > thr || (k == thr && eq_left > 0);
+                if (t) {
+                    if (k == thr) --eq_left;
+                    if (valid && pos < kShortlist) sl->idx[pos] = (uint16_t)idx;
+                    ++pos;
+                    tsel += tanh_approx(fmaf(0.5f, key16_value(k), -half_off));
+                }
+            };
+#pragma unroll 1
+            for (int i = 0; i < kTmemKeyChunks / 2; ++i) {
+                uint32_t v[32];
+                ld32(trow + 32 * i, v);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {        // chunk 2i + h: words 16h .. 16h + 15
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) take(v[16 * h + j] & 0xFFFFu, 64 * i + 32 * h + j);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) take(v[16 * h + j] >> 16, 64 * i + 32 * h + 16 + j);
+                }
+            }
+#pragma unroll 1
+            for (int c = kTmemKeyChunks; c < kChunks; ++c) {
+                const uint32_t *w = skeys + (c - kTmemKeyChunks) * kKeyWords;
+                for (int j = 0; j < 16; ++j) take(w[j] & 0xFFFFu, kNC * c + j);
+                for (int j = 0; j < 16; ++j) take(w[j] >> 16, kNC * c + 16 + j);
+            }
+            if (valid) {
+                sl->missing = 0.5f * (tsum - tsel) + 0.5f * (float)(1024 - kShortlist);
+                sl->nu_frac = nu;
+            }
+            // the key columns are read; the next tile's chunks may overwrite them
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        if (!ok) *abort = 1;
+    } else if (warp < 8) {
+        // -------------------------------------------------- gatherers --
+        const int p = tid - kConsumers;
+        const long long plane = nb;
+        unsigned char *arow = A + (p >> 3) * kSBO + (p & 7) * 16;
+        long long it = 0;
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            if (it > 0 && !wait(bar(kBarAFree), (uint32_t)((it - 1) & 1), abort)) { *abort = 1; break; }
+            const long long b = tile * kM + p;
+            const bool valid = b < nb;
+            const int by = valid ? (int)(b / nbw) : 0, bx = valid ? (int)(b - (long long)by * nbw) : 0;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int y = by + t / 3 - 1, x = bx + t % 3 - 1;
+                const bool inb = valid && y >= 0 && y < nbh && x >= 0 && x < nbw;
+                const float *src = a3 + (inb ? (long long)y * nbw + x : 0);
+#pragma unroll
+                for (int cg = 0; cg < 4; ++cg) {
+                    float v[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = inb ? src[(cg * 8 + e) * plane] : 0.f;
+                    uint4 u;
+                    u.x = tc::pack_bf16(v[0], v[1]); u.y = tc::pack_bf16(v[2], v[3]);
+                    u.z = tc::pack_bf16(v[4], v[5]); u.w = tc::pack_bf16(v[6], v[7]);
+                    *reinterpret_cast<uint4 *>(arow + (t * 4 + cg) * kLBO) = u;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            arrive(bar(kBarAFull));
+        }
+    } else if (lane == 0) {
+        // ----------------------------------------------------- issuer --
+        const uint32_t a_addr = tc::saddr(A), b_addr = tc::saddr(sm + kOffB);
+        auto chunk_src = [&](long long h) { return packed + (size_t)(h % kChunksPerTile) * kBChunkBytes; };
+        auto chunk_bytes = [&](long long h) { return h % kChunksPerTile == kChunks ? kBExtraBytes : kBChunkBytes; };
+        long long loaded = 0, waited = 0, g = 0, it = 0;
+        bool ok = true;
+        if (n_tiles > blockIdx.x) {
+            for (; loaded < 2; ++loaded)
+                bulk_load(b_addr + (uint32_t)(loaded % kSlots) * kBChunkBytes, chunk_src(loaded), chunk_bytes(loaded),
+                          bar(kBarBFull + (int)(loaded % kSlots)));
+        }
+        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+            if (!wait(bar(kBarAFull), (uint32_t)(it & 1), abort)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int c = 0; c < kChunksPerTile; ++c, ++g) {
+                // keep two chunks in flight: chunk g + 2 goes into the slot of chunk g - 2
+                const long long h = g + 2;
+                if (h >= kSlots &&
+                    !wait(bar(kBarBEmpty + (int)(h % kSlots)), (uint32_t)(((h - kSlots) / kSlots) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                bulk_load(b_addr + (uint32_t)(h % kSlots) * kBChunkBytes, chunk_src(h), chunk_bytes(h),
+                          bar(kBarBFull + (int)(h % kSlots)));
+                loaded = h + 1;
+                const int slot = (int)(g % kSlots), ab = (int)(g & 1);
+                if (!wait(bar(kBarBFull + slot), (uint32_t)((g / kSlots) & 1), abort)) { ok = false; break; }
+                waited = g + 1;
+                if (g >= 2 && !wait(bar(kBarAccEmpty + ab), (uint32_t)(((g - 2) >> 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + kAccCol + 32u * (uint32_t)ab;
+                const uint32_t id = idesc(c == kChunks ? 16 : kNC);
+                const uint32_t bs = b_addr + (uint32_t)slot * kBChunkBytes;
+#pragma unroll 1
+                for (int j = 0; j < kHeadIn / 16; ++j) {
+                    const uint64_t da = sdesc(a_addr + j * 2 * kLBO), db = sdesc(bs + j * 2 * kLBO);
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                 ::"r"(d), "l"(da), "l"(db), "r"(id), "r"(j)
+                                 : "memory");
+                }
+                commit(bar(kBarAccFull + ab));
+                commit(bar(kBarBEmpty + slot));
+                if (c == kChunks) commit(bar(kBarAFree));
+            }
+        }
+        if (!ok) *abort = 1;
+        // drain: copies still in flight, then the last tensor-core work
+        for (long long h = waited; h < loaded; ++h) {
+            volatile int no_abort = 0;
+            wait(bar(kBarBFull + (int)(h % kSlots)), (uint32_t)((h / kSlots) & 1), &no_abort);
+        }
+        if (g > 0) {
+            volatile int no_abort = 0;
+            wait(bar(kBarBEmpty + (int)((g - 1) % kSlots)), (uint32_t)(((g - 1) / kSlots) & 1), &no_abort);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0 && *abort) atomicOr(status, 2);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// Head weights (FP32 [1025][288], feature index ci * 9 + t) -> bfloat16 in
+// the core-matrix layout of head_select_kernel: chunk c of 32 rows (the
+// last one 16 rows: 1024..1039, zero beyond 1024), K index t * 32 + ci.
+__global__ void pack_head_kernel(const float *wh, unsigned char *packed)
+{
+    const int total = (kChunks * kNC + 16) * kHeadIn;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int n = i / kHeadIn, k = i % kHeadIn;
+        const int c = n / kNC, rl = n % kNC;
+        const int t = k / kC, ci = k % kC;
+        const float v = n < kOut ? wh[n * kHeadIn + ci * 9 + t] : 0.f;
+        const size_t off = (size_t)c * kBChunkBytes + (rl >> 3) * kSBO + (k >> 3) * kLBO + (rl & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16 *>(packed + off) = __float2bfloat16_rn(v);
+    }
+}
+}  // namespace hd
+
 // Fixed scratch of rljsde_propose_noalloc: part of the library image, so
 // every device that loads the library holds it until the process exits.
 constexpr size_t kStaticScratchBytes = 32u << 20;
-constexpr int kStaticChunk = 1024;       // blocks per head GEMM in that path
 static __device__ __align__(256) unsigned char g_propose_scratch[kStaticScratchBytes];
 
 }  // namespace net
@@ -781,10 +1041,10 @@ int static_scratch(void **out)
 struct rljsde_net {
     float *master = nullptr, *rounded = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *w16 = nullptr;
-    __nv_bfloat16 *head16 = nullptr;     // kOutPad x 288, zero-padded head rows
+    unsigned char *head_packed = nullptr;   // head weights for head_select_kernel (bfloat16, 599,040 B)
     int step = 0;
     int sm_count = 1;                    // SMs of the device the network lives on
-    cublasHandle_t blas = nullptr;
+    float logit_offset = 0.f;            // log of the positive weight of the last training step
     // training buffers, sized for `cap` samples
     int cap = 0;
     float *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *g1 = nullptr, *g2 = nullptr, *g3 = nullptr;
@@ -844,8 +1104,7 @@ int conv_tc(const float *in, const float *w, const float *b, float *out, int hi,
 void refresh_bf16(rljsde_net *n, cudaStream_t s)
 {
     to_bf16_kernel<<<grid_for(kParams, 256), 256, 0, s>>>(n->master, n->w16, n->rounded, kParams);
-    head_pad_kernel<<<grid_for(kOutPad * kHeadIn, 256), 256, 0, s>>>(n->master + kWh, n->head16, kOut, kOutPad,
-                                                                     kHeadIn);
+    hd::pack_head_kernel<<<grid_for(1040 * kHeadIn, 256), 256, 0, s>>>(n->master + kWh, n->head_packed);
 }
 
 // Forward over n patches already in n->x with origins in n->origin; the
@@ -865,6 +1124,50 @@ void forward_patches(rljsde_net *net, int n, int lr_h, int lr_w, cudaStream_t s)
     gemm_kernel<<<gg, 256, 0, s>>>(n, kOut, kHeadIn, net->f, kHeadIn, 1, r + kWh, 1, kHeadIn, net->z, kOut, 0.f);
 }
 
+// Device bytes of the whole-image pass: input planes, conv1 output (both on
+// the L-pixel grid), conv2 and conv3 outputs (block grid), 256-byte aligned.
+size_t propose_bytes(size_t P, size_t nb)
+{
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4);
+}
+
+// The whole-image pass over `ws` (propose_bytes of it): conv1 on the CUDA
+// cores, conv2 and conv3 on the tensor cores, then the fused head and
+// top-64 selection (hd::head_select_kernel), which writes the shortlists.
+int propose_pass(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
+                 void *shortlists, void *ws, cudaStream_t s)
+{
+    const int lr_h = plan->lr_h[0], lr_w = plan->lr_w[0], nbh = lr_h / 2, nbw = lr_w / 2;
+    const size_t P = (size_t)lr_h * lr_w, nb = (size_t)plan->n_blocks;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    char *w = static_cast<char *>(ws);
+    float *x = reinterpret_cast<float *>(w);   w += al(5 * P * 4);
+    float *a1 = reinterpret_cast<float *>(w);  w += al(kC * P * 4);
+    float *a2 = reinterpret_cast<float *>(w);  w += al(kC * nb * 4);
+    float *a3 = reinterpret_cast<float *>(w);
+    const float *r = net->rounded, *b = net->master;
+    const int sms = plan->sm_count > 0 ? plan->sm_count : 1;
+    const int cap = 8 * sms;                                   // 8 CTAs per SM at most
+    auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
+    image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
+    ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
+    conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
+    // conv2 (stride 2, onto the block grid) and conv3 on the tensor cores
+    int cst = conv_tc(a1, r + kW2, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, sms, plan->d_status, s);
+    if (cst == RLJSDE_OK) cst = conv_tc(a2, r + kW3, b + kB3, a3, nbh, nbw, nbh, nbw, 1, sms, plan->d_status, s);
+    if (cst != RLJSDE_OK) return cst;
+    if (cudaFuncSetAttribute(hd::head_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hd::kSmem) !=
+        cudaSuccess)
+        return RLJSDE_ERR_CUDA;
+    const long long tiles = ((long long)nb + hd::kM - 1) / hd::kM;
+    const int grid = (int)(tiles < sms ? tiles : sms);             // one CTA per SM (all of tensor memory)
+    hd::head_select_kernel<<<grid, hd::kThreads, hd::kSmem, s>>>(a3, nbh, nbw, net->head_packed, b + kBh,
+                                                                 net->logit_offset, static_cast<Shortlist *>(shortlists),
+                                                                 plan->d_status);
+    return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -879,8 +1182,8 @@ int rljsde_net_create(rljsde_net_t **out, uint64_t seed)
     bool ok = cudaMalloc(&n->master, b) == cudaSuccess && cudaMalloc(&n->rounded, b) == cudaSuccess &&
               cudaMalloc(&n->grad, b) == cudaSuccess && cudaMalloc(&n->m, b) == cudaSuccess &&
               cudaMalloc(&n->v, b) == cudaSuccess && cudaMalloc(&n->w16, (size_t)kParams * 2) == cudaSuccess &&
-              cudaMalloc(&n->head16, (size_t)kOutPad * kHeadIn * 2) == cudaSuccess;
-    if (!ok || cublasCreate(&n->blas) != CUBLAS_STATUS_SUCCESS) { rljsde_net_destroy(n); return RLJSDE_ERR_OUT_OF_MEMORY; }
+              cudaMalloc(&n->head_packed, hd::kPackedBytes) == cudaSuccess;
+    if (!ok) { rljsde_net_destroy(n); return RLJSDE_ERR_OUT_OF_MEMORY; }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n->sm_count < 1) {
@@ -923,8 +1226,7 @@ void rljsde_net_destroy(rljsde_net_t *n)
     if (!n) return;
     free_train(n);
     cudaFree(n->master); cudaFree(n->rounded); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v); cudaFree(n->w16);
-    cudaFree(n->head16);
-    if (n->blas) cublasDestroy(n->blas);
+    cudaFree(n->head_packed);
     delete n;
 }
 
@@ -1016,6 +1318,7 @@ int rljsde_net_train_step(rljsde_net_t *net, const float *x, const int32_t *bloc
     int st = loss_grad(net, x, blocks, n, lr_h, lr_w, targets, nu_t, pos_w, nu_w, loss_host, s);
     if (st) return st;
     net->step += 1;
+    net->logit_offset = std::log(pos_w > 0.f ? pos_w : 1.f);
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
     adam_kernel<<<grid_for(kParams, 256), 256, 0, s>>>(net->master, net->grad, net->m, net->v, kParams, lr, b1, b2,
@@ -1044,10 +1347,7 @@ int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, 
 size_t rljsde_propose_workspace(const rljsde_plan_t *plan)
 {
     if (!plan || plan->n_images != 1) return 0;
-    const size_t P = (size_t)plan->lr_h[0] * plan->lr_w[0], nb = (size_t)plan->n_blocks;
-    const size_t chunk = nb < 65536 ? nb : 65536;
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    return al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4) + al(chunk * kHeadIn * 2) + al(chunk * kOutPad * 4);
+    return propose_bytes((size_t)plan->lr_h[0] * plan->lr_w[0], (size_t)plan->n_blocks);
 }
 
 int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
@@ -1057,44 +1357,7 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
     if (plan->n_images != 1 || lr_pitch < (size_t)plan->lr_w[0]) return RLJSDE_ERR_INVALID_ARG;
     if (plan->params.layout != RLJSDE_LAYOUT_THREE_QUARTER) return RLJSDE_ERR_UNSUPPORTED;   // opaque-code input
     if (ws_bytes < rljsde_propose_workspace(plan)) return RLJSDE_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int lr_h = plan->lr_h[0], lr_w = plan->lr_w[0], nbh = lr_h / 2, nbw = lr_w / 2;
-    const size_t P = (size_t)lr_h * lr_w, nb = (size_t)plan->n_blocks;
-    const size_t chunk = nb < 65536 ? nb : 65536;
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    char *w = static_cast<char *>(workspace);
-    float *x = reinterpret_cast<float *>(w);            w += al(5 * P * 4);
-    float *a1 = reinterpret_cast<float *>(w);           w += al(kC * P * 4);
-    float *a2 = reinterpret_cast<float *>(w);           w += al(kC * nb * 4);
-    float *a3 = reinterpret_cast<float *>(w);           w += al(kC * nb * 4);
-    __nv_bfloat16 *f16 = reinterpret_cast<__nv_bfloat16 *>(w); w += al(chunk * kHeadIn * 2);
-    float *z = reinterpret_cast<float *>(w);
-    const float *r = net->rounded, *b = net->master;
-    const int cap = 8 * (plan->sm_count > 0 ? plan->sm_count : 1);     // 8 CTAs per SM at most
-    auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
-    image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
-    ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
-    conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
-    // conv2 (stride 2, onto the block grid) and conv3 on the tensor cores
-    int cst = conv_tc(a1, r + kW2, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, plan->sm_count, plan->d_status, s);
-    if (cst == RLJSDE_OK)
-        cst = conv_tc(a2, r + kW3, b + kB3, a3, nbh, nbw, nbh, nbw, 1, plan->sm_count, plan->d_status, s);
-    if (cst != RLJSDE_OK) return cst;
-    if (cublasSetStream(net->blas, s) != CUBLAS_STATUS_SUCCESS) return RLJSDE_ERR_CUDA;
-    const float one = 1.f, zero = 0.f;
-    for (size_t b0 = 0; b0 < nb; b0 += chunk) {
-        const int m = (int)(nb - b0 < chunk ? nb - b0 : chunk);
-        head_features_tile_kernel<<<gcap(((long long)m + kFeatTile - 1) / kFeatTile * 256, 256), 256, 0, s>>>(
-            a3, nbh, nbw, (long long)b0, m, f16);
-        // z (row-major m x 1040) = f16 (m x 288) * Wh_pad^T: column-major z^T = Wh_pad * f16^T
-        if (cublasGemmEx(net->blas, CUBLAS_OP_T, CUBLAS_OP_N, kOutPad, m, kHeadIn, &one, net->head16, CUDA_R_16BF,
-                         kHeadIn, f16, CUDA_R_16BF, kHeadIn, &zero, z, CUDA_R_32F, kOutPad, CUBLAS_COMPUTE_32F,
-                         CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-            return RLJSDE_ERR_CUDA;
-        shortlist_kernel<<<gcap(((long long)m + 7) / 8 * 256, 256), 256, 0, s>>>(
-            z, kOutPad, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
-    }
-    return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+    return propose_pass(plan, net, lr, lr_pitch, shortlists, workspace, (cudaStream_t)stream);
 }
 
 // The proposal pass for callers that must not allocate device memory; see
@@ -1105,44 +1368,11 @@ int rljsde_propose_noalloc(const rljsde_plan_t *plan, const rljsde_net_t *net, c
     if (!plan || !net || !lr || !shortlists) return RLJSDE_ERR_INVALID_ARG;
     if (plan->n_images != 1 || lr_pitch < (size_t)plan->lr_w[0]) return RLJSDE_ERR_INVALID_ARG;
     if (plan->params.layout != RLJSDE_LAYOUT_THREE_QUARTER) return RLJSDE_ERR_UNSUPPORTED;   // opaque-code input
-    const int lr_h = plan->lr_h[0], lr_w = plan->lr_w[0], nbh = lr_h / 2, nbw = lr_w / 2;
-    const size_t P = (size_t)lr_h * lr_w, nb = (size_t)plan->n_blocks;
-    const size_t chunk = nb < (size_t)kStaticChunk ? nb : (size_t)kStaticChunk;
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t need = al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4) + al(chunk * kHeadIn * 4) +
-                        al(chunk * kOut * 4);
-    if (need > kStaticScratchBytes) return RLJSDE_ERR_BAD_SHAPE;    // image too large for the fixed scratch
+    if (rljsde_propose_workspace(plan) > kStaticScratchBytes) return RLJSDE_ERR_BAD_SHAPE;   // too large for the fixed scratch
     void *base = nullptr;
     int st = static_scratch(&base);
     if (st) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    char *w = static_cast<char *>(base);
-    float *x = reinterpret_cast<float *>(w);   w += al(5 * P * 4);
-    float *a1 = reinterpret_cast<float *>(w);  w += al(kC * P * 4);
-    float *a2 = reinterpret_cast<float *>(w);  w += al(kC * nb * 4);
-    float *a3 = reinterpret_cast<float *>(w);  w += al(kC * nb * 4);
-    float *f = reinterpret_cast<float *>(w);   w += al(chunk * kHeadIn * 4);
-    float *z = reinterpret_cast<float *>(w);
-    const float *r = net->rounded, *b = net->master;
-    const int cap = 8 * (plan->sm_count > 0 ? plan->sm_count : 1);     // 8 CTAs per SM at most
-    auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
-    image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
-    ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
-    conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
-    // conv2 (stride 2, onto the block grid) and conv3 on the tensor cores
-    int cst = conv_tc(a1, r + kW2, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, plan->sm_count, plan->d_status, s);
-    if (cst == RLJSDE_OK)
-        cst = conv_tc(a2, r + kW3, b + kB3, a3, nbh, nbw, nbh, nbw, 1, plan->sm_count, plan->d_status, s);
-    if (cst != RLJSDE_OK) return cst;
-    for (size_t b0 = 0; b0 < nb; b0 += chunk) {
-        const int m = (int)(nb - b0 < chunk ? nb - b0 : chunk);
-        head_features_f32_kernel<<<gcap((long long)m * kHeadIn, 256), 256, 0, s>>>(a3, nbh, nbw, (long long)b0, m, f);
-        dim3 gg((kOut + 63) / 64, (m + 63) / 64);
-        gemm_kernel<<<gg, 256, 0, s>>>(m, kOut, kHeadIn, f, kHeadIn, 1, r + kWh, 1, kHeadIn, z, kOut, 0.f);
-        shortlist_kernel<<<gcap(((long long)m + 7) / 8 * 256, 256), 256, 0, s>>>(
-            z, kOut, b + kBh, (long long)b0, m, static_cast<Shortlist *>(shortlists));
-    }
-    return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
+    return propose_pass(plan, net, lr, lr_pitch, shortlists, base, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -24,6 +24,20 @@ from . import rljsde, synth
 SHORTLIST = 64
 
 
+def tail_mass(dc):
+    """Per block, the sum of |gamma delta| from each iteration to the end:
+    tail[b, i] = sum_{j >= i} |dc[b, j]| (dc: (n, nu_max, 2))."""
+    import torch
+    mag = torch.sqrt(dc[..., 0] ** 2 + dc[..., 1] ** 2)
+    return torch.flip(torch.cumsum(torch.flip(mag, [1]), 1), [1])
+
+
+def nu_targets(tail, eps: float, nu_max: int):
+    """Iteration target (fraction of nu_max): the iterations whose remaining
+    |gamma delta| still adds up to eps or more."""
+    return (tail >= eps).sum(1).float() / nu_max
+
+
 def labels_from_trace(sel, dc, nu_max: int, k: int = SHORTLIST, eps: float = 0.2):
     """Targets (n, 1024) uint8 and iteration fractions (n,) from a trace."""
     import torch
@@ -36,17 +50,18 @@ def labels_from_trace(sel, dc, nu_max: int, k: int = SHORTLIST, eps: float = 0.2
     chosen = torch.gather(first, 1, order) < nu_max
     targets = torch.zeros((n, 1024), dtype=torch.uint8, device=sel.device)
     targets.scatter_(1, order, chosen.to(torch.uint8))
-    mag = torch.sqrt(dc[..., 0] ** 2 + dc[..., 1] ** 2)
-    tail = torch.flip(torch.cumsum(torch.flip(mag, [1]), 1), [1])
-    nu_t = (tail >= eps).sum(1).float() / nu_max
-    return targets, nu_t
+    return targets, nu_targets(tail_mass(dc), eps, nu_max)
 
 
 def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu_max: int = 100,
-                 tiles=None, seed: int = 0, n_sin: int = 256, n_edges: int = 32, device: str = "cuda"):
+                 tiles=None, seed: int = 0, n_sin: int = 256, n_edges: int = 32, device: str = "cuda",
+                 keep_tail: bool = False, eps: float = 0.2):
     """Patches, block coordinates, targets and iteration targets for
     ``blocks_per_image`` random blocks of each of ``n_images`` synthetic
-    size x size images (mask tiles cycled from ``tiles``)."""
+    size x size images (mask tiles cycled from ``tiles``).  With
+    ``keep_tail`` a sixth entry holds every sample's tail |gamma delta| sums
+    (n, nu_max), from which ``nu_targets`` gives the iteration targets of any
+    other threshold."""
     import torch
     lr = size // 2
     nb_side = lr // 2
@@ -59,28 +74,32 @@ def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu
     hr = torch.empty((size, size), device=device)
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    xs, bs, ts, ns = [], [], [], []
+    xs, bs, ts, ns, tails = [], [], [], [], []
     for i in range(n_images):
         t = i % len(tiles)
         f = synth.image_torch(size, size, n_sin, n_edges, seed * 100003 + i, 0.005, device)
         y = synth.measure_torch(f, masks_d[t]).float().contiguous()
         plans[t].reconstruct_trace(y, hr, sel, dc)
         pick = torch.randperm(nb, generator=g, device=device)[:blocks_per_image]
-        tg, nu_t = labels_from_trace(sel.view(nb, nu_max)[pick], dc.view(nb, nu_max, 2)[pick], nu_max)
+        dcp = dc.view(nb, nu_max, 2)[pick]
+        tg, nu_t = labels_from_trace(sel.view(nb, nu_max)[pick], dcp, nu_max, eps=eps)
         blk = torch.stack([pick // nb_side, pick % nb_side], 1).int().contiguous()
         xs.append(rljsde.Net.patches(y, masks_d[t], blk))
         bs.append(blk)
         ts.append(tg)
         ns.append(nu_t)
+        if keep_tail:
+            tails.append(tail_mass(dcp))
     for p in plans:
         p.check()
-    return torch.cat(xs), torch.cat(bs), torch.cat(ts), torch.cat(ns), (lr, lr)
+    out = (torch.cat(xs), torch.cat(bs), torch.cat(ts), torch.cat(ns), (lr, lr))
+    return out + (torch.cat(tails),) if keep_tail else out
 
 
 def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None):
     """Adam with cosine decay over ``epochs`` passes of ``data``."""
     import torch
-    x, blocks, targets, nu_t, shape = data
+    x, blocks, targets, nu_t, shape = data[:5]
     n = x.shape[0]
     g = torch.Generator(device=x.device)
     g.manual_seed(seed)
@@ -103,7 +122,7 @@ def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed:
 def recall(net, data, k: int = SHORTLIST):
     """Mean fraction of each block's target set found in its top-k logits."""
     import torch
-    x, blocks, targets, nu_t, shape = data
+    x, blocks, targets, nu_t, shape = data[:5]
     hits, total = 0, 0
     for i in range(0, x.shape[0], 8192):
         z = net.logits(x[i:i + 8192].contiguous(), blocks[i:i + 8192].contiguous(), shape)

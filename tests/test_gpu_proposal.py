@@ -286,3 +286,56 @@ def test_restricted_loop_with_repeated_candidates(rl):
     res = compare(g_hr, g_sel[blocks], o_hr, np.array(o_sel), np.array(o_gap), blocks, nbw, tol=1e-4, tie=1e-4)
     assert not res["fails"], res["fails"][:3]
     assert all(set(g_sel[b].tolist()) <= set(idx[b].tolist()) for b in blocks)
+
+
+def _key16(z):
+    """16-bit ranking key of FP32 logits: the upper half of the
+    order-preserving integer image (the logit truncated to bfloat16)."""
+    u = np.asarray(z, np.float32).view(np.uint32).astype(np.uint64)
+    k = np.where(u & 0x80000000, (~u) & 0xFFFFFFFF, u | 0x80000000)
+    return (k >> 16).astype(np.int64)
+
+
+def _bias_pattern(name, rng):
+    if name == "normal":
+        return rng.normal(-2.0, 1.5, 1025)
+    if name == "ties":                                # few distinct values: exact ties at the threshold
+        return rng.choice(np.array([-3.0, -1.0, 0.5, 2.0]), 1025, p=[0.6, 0.3, 0.06, 0.04])
+    if name == "below_bf16":                          # distinct FP32 values, equal after truncation
+        return 1.0 + 2.0 ** -20 * rng.integers(0, 64, 1025) - 2.0 * (rng.random(1025) < 0.9)
+    return np.full(1025, 0.25)                        # all equal: the 64 lowest indices
+
+
+@pytest.mark.parametrize("pattern", ["normal", "ties", "below_bf16", "equal"])
+def test_fused_selection_exact_on_bias_logits(rl, pattern):
+    """With a zero head matrix every block's logits are the head biases
+    exactly, so the fused head's shortlist must be the 64 largest biases by
+    their bfloat16-truncated keys, ties to the lower index, in increasing
+    index order, on every block; the iteration output is the bias of row
+    1024 exactly, and the left-out mass is the sum of sigmoid over the other
+    960 biases within the bound of its approximations (tanh.approx per term,
+    midpoint values of the selected keys)."""
+    import torch
+    f, mask, y = _image(40, 56, 2)
+    net = rl.Net(seed=4)
+    p = cnn_ref.unflatten(net.get_params())
+    b = _bias_pattern(pattern, np.random.default_rng(17))
+    p["head.w"][:] = 0.0
+    p["head.b"][:] = b
+    net.set_params(cnn_ref.flatten(p).astype(np.float32))
+    plan = rl.Plan(mask, rl.default_params(nu_max=10))
+    lr = torch.from_numpy(y).cuda()
+    nb = 20 * 28
+    idx, missing, nu_frac = rl.shortlist_view(plan.propose(net, lr), nb)
+    plan.check()
+    b32 = b.astype(np.float32)
+    k = _key16(b32[:1024])
+    order = np.lexsort((np.arange(1024), -k))         # key descending, then index ascending
+    want = np.sort(order[:64])
+    assert np.array_equal(idx.astype(np.int64), np.broadcast_to(want, (nb, 64)))
+    assert np.all(nu_frac == b32[1024])
+    rest = np.setdiff1d(np.arange(1024), want)
+    zr = b32.astype(np.float64)
+    ref = float(np.sum(1.0 / (1.0 + np.exp(-zr[rest]))))          # untrained network: offset 0
+    bound = 1024 * 2.5e-4 + float(np.sum(0.25 * np.abs(zr[want]) * 2.0 ** -8)) + 1e-3
+    assert np.all(np.abs(missing - ref) <= bound), (float(np.abs(missing - ref).max()), bound)
