@@ -445,18 +445,18 @@ def run_learned(args):
     # validation images (seeds apart from the training, held-out and test images)
     vals = []
     for i in range(2):
-        vm = np.ascontiguousarray(np.tile(mask[:4, :4], (384, 512)))
+        vm = np.ascontiguousarray(np.tile(mask[:4, :4], (192, 256)))          # 768 x 1024 L-pixels
         fv = synth.image(1536, 2048, 1024, 128, 7100 + i)
         vals.append(Image(fv, vm, synth.measure(fv, vm).astype(np.float32)))
     for v in vals:
         v.run_plain(nu_max, 1)
-    x, blocks, targets, _, shape, tails = data
+    x, blocks, targets, _, shape, mass, tails = data
     sweep = []
     best = None
     for eps in args.eps_sweep:
         net = rljsde.Net(seed=5)
         t1 = time.time()
-        losses = proposal.train(net, (x, blocks, targets, proposal.nu_targets(tails, eps, nu_max), shape),
+        losses = proposal.train(net, (x, blocks, targets, proposal.nu_targets(tails, eps, nu_max), shape, mass),
                                 epochs=args.epochs, lr=args.lr)
         pts = [v.run_learned(net, 1) for v in vals]
         ent = {"eps": eps, "train_s": time.time() - t1, "loss_first": losses[0], "loss_last": losses[-1],
@@ -470,7 +470,7 @@ def run_learned(args):
             best = (ent, net)
         else:
             net.close()
-    del data, x, blocks, targets, tails
+    del data, x, blocks, targets, tails, mass
     if best is None:                                  # no threshold kept the PSNR: the most conservative one
         best = (sweep[0], rljsde.Net(seed=5))
         proposal.train(best[1], held, epochs=1, lr=args.lr)

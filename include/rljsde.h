@@ -202,14 +202,15 @@ int rljsde_graph_launch(const rljsde_plan_t *plan, void *stream);
  * ---------------------------------------------------------------------- */
 typedef struct rljsde_net rljsde_net_t;   /* weights, Adam state, packed head weights */
 
-/* One block's proposal (device layout, 136 bytes): candidate indices
- * sigma * W + rho of the 64 largest logits z (ranked by z truncated to
- * bfloat16 precision, i.e. the upper 16 bits of its order-preserving integer
- * image; ties to the lower index; in increasing index order); `missing`, the
- * network's expected number of the plain loop's candidates left out: the sum
- * over the other candidates of the calibrated probability sigmoid(z - log w),
- * w the positive weight of the network's last training step (1 before any);
- * and its iteration output. */
+/* One block's proposal (device layout, 136 bytes):
+ *   idx: the 64 candidates sigma * W + rho with the largest logits z, ranked
+ *        by z on a fixed-point grid of step 2^-10 over [-32, 32) (rounded
+ *        down, clamped), ties to the lower index, in increasing index order;
+ *   missing: the network's gate, sigmoid of head row 1025: its prediction of
+ *        the share of the plain loop's coefficient mass (sum of |gamma delta|
+ *        per candidate over nu_max iterations, Eq. 15) that falls on
+ *        candidates outside idx;
+ *   nu_frac: its iteration output (head row 1024), a fraction of nu_max. */
 typedef struct {
     uint16_t idx[64];
     float missing;
@@ -221,7 +222,8 @@ int rljsde_net_create(rljsde_net_t **out, uint64_t seed);
 void rljsde_net_destroy(rljsde_net_t *net);
 int rljsde_net_num_params(void);
 /* Copy all parameters (FP32, fixed order: conv1.w, conv1.b, conv2.w,
- * conv2.b, conv3.w, conv3.b, head.w (1025 x 288), head.b) to / from host. */
+ * conv2.b, conv3.w, conv3.b, head.w (1026 x 288), head.b (1026)) to / from
+ * host.  Head rows: 1024 candidate logits, the iteration output, the gate. */
 int rljsde_net_get_params(const rljsde_net_t *net, float *host);
 int rljsde_net_set_params(rljsde_net_t *net, const float *host);
 /* Training patches: x (device, n x 5 x 16 x 16) for blocks (device int32
@@ -229,17 +231,22 @@ int rljsde_net_set_params(rljsde_net_t *net, const float *host);
 int rljsde_net_patches(const float *lr, size_t lr_pitch, const uint8_t *mask, int lr_h, int lr_w,
                        const int32_t *blocks, int n, float *x, void *stream);
 /* Loss and gradient of n patches: targets (device, n x 1024 bytes, 1 = in
- * the block's reference shortlist), nu_t (device, n floats in [0, 1]).
- * grad_out (device, num_params floats) may be NULL; loss_host receives the
- * mean loss.  Synchronous. */
+ * the block's reference shortlist), nu_t (device, n floats in [0, 1]), mass
+ * (device, n x 1024 floats: the plain loop's |gamma delta| summed per
+ * candidate; NULL = no gate term).  Loss per patch: the logistic loss of the
+ * candidates (positives weigh pos_weight) averaged over the 1024, plus
+ * nu_weight (z_1024 - nu_t)^2, plus gate_weight (sigmoid(z_1025) - s)^2 with
+ * s the share of the mass outside the patch's own 64 largest logits (a
+ * target, not differentiated).  grad_out (device, num_params floats) may be
+ * NULL; loss_host receives the mean loss.  Synchronous. */
 int rljsde_net_gradient(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
-                        const uint8_t *targets, const float *nu_t, float pos_weight, float nu_weight,
-                        float *grad_out, float *loss_host, void *stream);
+                        const uint8_t *targets, const float *nu_t, const float *mass, float pos_weight,
+                        float nu_weight, float gate_weight, float *grad_out, float *loss_host, void *stream);
 /* The same followed by one Adam step with learning rate lr.  Synchronous. */
 int rljsde_net_train_step(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
-                          const uint8_t *targets, const float *nu_t, float pos_weight, float nu_weight, float lr,
-                          float *loss_host, void *stream);
-/* Logits including bias (device, n x 1025) of n patches.  Synchronous. */
+                          const uint8_t *targets, const float *nu_t, const float *mass, float pos_weight,
+                          float nu_weight, float gate_weight, float lr, float *loss_host, void *stream);
+/* Logits including bias (device, n x 1026) of n patches.  Synchronous. */
 int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
                       float *z_out, void *stream);
 /* Device workspace bytes rljsde_propose needs for a single-image plan. */

@@ -19,19 +19,22 @@ Network (one training sample = a 16x16 patch of L-pixels, LR rows/cols
   is what zero padding gives when the network runs over the whole image;
 * head: the 3x3 block-grid neighbourhood of conv3 at the patch centre (block
   grid index (4, 4)), 288 features in the order c * 9 + (dy + 1) * 3 + (dx + 1),
-  times W_h (1025 x 288) plus b_h: 1024 candidate logits and one iteration
-  output;
+  times W_h (1026 x 288) plus b_h: 1024 candidate logits, one iteration
+  output and one gate;
 * weights enter the forward pass rounded to bfloat16 (round to nearest even);
 * loss, averaged over samples: mean over candidates of
   w(t) * (softplus(z) - t z), w = pos_weight for t = 1, else 1; plus
-  nu_weight * (z_1024 - nu_target)^2.
+  nu_weight * (z_1024 - nu_target)^2; plus, given the sample's mass vector m
+  (the plain loop's |gamma delta| per candidate), gate_weight *
+  (sigmoid(z_1025) - s)^2 where s is the share of m outside the sample's
+  own 64 largest candidate logits (a target: not differentiated).
 """
 from __future__ import annotations
 
 import numpy as np
 
 C = 32
-N_OUT = 1025
+N_OUT = 1026
 SHAPES = [("conv1.w", (C, 5, 3, 3)), ("conv1.b", (C,)), ("conv2.w", (C, C, 3, 3)), ("conv2.b", (C,)),
           ("conv3.w", (C, C, 3, 3)), ("conv3.b", (C,)), ("head.w", (N_OUT, 9 * C)), ("head.b", (N_OUT,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
@@ -116,14 +119,14 @@ def forward(params, x, origin, lr_shape, bf16=True):
     return z, (p, x, m1, m2, a1, a2, a3, f)
 
 
-def loss_and_grads(params, xs, origins, lr_shape, targets, nu_targets, pos_weight=8.0, nu_weight=0.1,
-                   bf16=True):
+def loss_and_grads(params, xs, origins, lr_shape, targets, nu_targets, masses=None, pos_weight=8.0,
+                   nu_weight=0.1, gate_weight=1.0, bf16=True):
     """Mean loss over samples and its gradient w.r.t. every parameter (with
     respect to the bf16-rounded weights, as the GPU computes it)."""
     n = len(xs)
     grads = {k: np.zeros_like(np.asarray(v, np.float64)) for k, v in params.items()}
     total = 0.0
-    for x, o, t, nt in zip(xs, origins, targets, nu_targets):
+    for i, (x, o, t, nt) in enumerate(zip(xs, origins, targets, nu_targets)):
         z, (p, x, m1, m2, a1, a2, a3, f) = forward(params, x, o, lr_shape, bf16)
         zc, t = z[:1024], np.asarray(t, np.float64)
         w = np.where(t > 0.5, pos_weight, 1.0)
@@ -132,6 +135,13 @@ def loss_and_grads(params, xs, origins, lr_shape, targets, nu_targets, pos_weigh
         gz = np.zeros(N_OUT)
         gz[:1024] = w * (1.0 / (1.0 + np.exp(-zc)) - t) / 1024.0
         gz[1024] = 2.0 * nu_weight * (z[1024] - nt)
+        if masses is not None:
+            m = np.asarray(masses[i], np.float64)
+            inside = zc >= np.sort(zc)[-64]                    # the 64 largest (ties count as in)
+            share = m[~inside].sum() / m.sum() if m.sum() > 0 else 0.0
+            sg = 1.0 / (1.0 + np.exp(-z[1025]))
+            total += gate_weight * (sg - share) ** 2
+            gz[1025] = 2.0 * gate_weight * (sg - share) * sg * (1.0 - sg)
         gz /= n
         grads["head.w"] += np.outer(gz, f)
         grads["head.b"] += gz

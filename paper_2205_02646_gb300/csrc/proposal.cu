@@ -35,7 +35,7 @@ namespace rljsde {
 namespace net {
 
 constexpr int kC = 32;
-constexpr int kOut = 1025;
+constexpr int kOut = 1026;      // 1024 candidate logits, iteration output, gate
 constexpr int kHeadIn = 9 * kC;
 // flat parameter layout
 constexpr int kW1 = 0, kB1 = kW1 + kC * 5 * 9, kW2 = kB1 + kC, kB2 = kW2 + kC * kC * 9, kW3 = kB2 + kC,
@@ -316,32 +316,97 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
         }
 }
 
-// Loss (mean over samples) and its gradient w.r.t. z = logits (+bias added here).
-__global__ void loss_kernel(float *z, const float *bias, const uint8_t *t, const float *nu_t, int n, float pos_w,
-                            float nu_w, float *gz, float *loss)
+// Order-preserving unsigned image of a float.
+__device__ __forceinline__ uint32_t order_key(float v)
+{
+    const uint32_t u = __float_as_uint(v);
+    return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
+}
+
+// Loss (mean over samples) and its gradient w.r.t. z = logits (+bias added
+// here).  Per sample (one CTA of 256 threads):
+//   candidates k < 1024: logistic loss, positives weighted pos_w, / 1024;
+//   row 1024 (iteration output): nu_w (z - nu_t)^2;
+//   row 1025 (gate), if mass is given: gate_w (sigmoid(z) - s)^2 with s the
+//   share of the sample's mass (the plain loop's |gamma delta| per candidate)
+//   that falls outside the network's own 64 largest logits; s is a target,
+//   not differentiated.  Candidates tied with the 64th largest count as in.
+__global__ void __launch_bounds__(256) loss_kernel(float *z, const float *bias, const uint8_t *t, const float *nu_t,
+                                                   const float *mass, int n, float pos_w, float nu_w, float gate_w,
+                                                   float *gz, float *loss)
 {
     const int s = blockIdx.x;
     if (s >= n) return;
     __shared__ float red[256];
+    __shared__ float red2[256];
     float l = 0.f;
+    float *zs = z + (size_t)s * kOut;
     for (int k = threadIdx.x; k < kOut; k += blockDim.x) {
-        const float zk = z[(size_t)s * kOut + k] + bias[k];
-        z[(size_t)s * kOut + k] = zk;
-        float g;
+        const float zk = zs[k] + bias[k];
+        zs[k] = zk;
         if (k < 1024) {
             const float tk = t[(size_t)s * 1024 + k] ? 1.f : 0.f;
             const float w = tk > 0.5f ? pos_w : 1.f;
             const float sp = fmaxf(zk, 0.f) + log1pf(expf(-fabsf(zk)));
             l += w * (sp - tk * zk) / 1024.f;
-            g = w * (1.f / (1.f + expf(-zk)) - tk) / 1024.f;
-        } else {
+            gz[(size_t)s * kOut + k] = w * (1.f / (1.f + expf(-zk)) - tk) / 1024.f / n;
+        } else if (k == 1024) {
             const float d = zk - nu_t[s];
             l += nu_w * d * d;
-            g = 2.f * nu_w * d;
+            gz[(size_t)s * kOut + k] = 2.f * nu_w * d / n;
         }
-        gz[(size_t)s * kOut + k] = g / n;
     }
-    red[threadIdx.x] = l;
+    __syncthreads();
+    float gg = 0.f;
+    if (mass != nullptr) {
+        // 64th largest candidate logit by bisection on the order keys
+        uint32_t key[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) key[j] = order_key(zs[threadIdx.x + 256 * j]);
+        uint32_t thr = 0;
+        for (int bit = 31; bit >= 0; --bit) {
+            const uint32_t cand = thr | (1u << bit);
+            int c = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c += key[j] >= cand;
+            red[threadIdx.x] = (float)c;
+            __syncthreads();
+            for (int o = 128; o > 0; o >>= 1) {
+                if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+                __syncthreads();
+            }
+            if (red[0] >= (float)kShortlist) thr = cand;
+            __syncthreads();
+        }
+        float out_m = 0.f, all_m = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float m = mass[(size_t)s * 1024 + threadIdx.x + 256 * j];
+            all_m += m;
+            if (key[j] < thr) out_m += m;
+        }
+        red[threadIdx.x] = out_m;
+        red2[threadIdx.x] = all_m;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                red[threadIdx.x] += red[threadIdx.x + o];
+                red2[threadIdx.x] += red2[threadIdx.x + o];
+            }
+            __syncthreads();
+        }
+        const float share = red2[0] > 0.f ? red[0] / red2[0] : 0.f;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const float sg = 1.f / (1.f + expf(-zs[1025]));
+            const float d = sg - share;
+            gg = gate_w * d * d;
+            gz[(size_t)s * kOut + 1025] = 2.f * gate_w * d * sg * (1.f - sg) / n;
+        }
+    } else if (threadIdx.x == 0) {
+        gz[(size_t)s * kOut + 1025] = 0.f;
+    }
+    red[threadIdx.x] = l + gg;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -567,9 +632,8 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
 //     N 32, K 16) into one of two 32-column accumulators in tensor memory;
 //   - four consumer warps (warp w owns tensor-memory lanes 32w .. 32w + 31,
 //     one block per lane) read each chunk's logits, add the bias, and keep
-//     only a 16-bit order key per candidate: the upper half of the
-//     order-preserving integer image of the FP32 logit, i.e. the logit
-//     truncated to bfloat16 precision.  Two keys share a 32-bit word; the
+//     only a 16-bit ranking key per candidate: the logit on a fixed-point
+//     grid of step 2^-10 over [-32, 32).  Two keys share a 32-bit word; the
 //     keys of chunks 0..27 go back into tensor memory (columns 0..447), the
 //     last four chunks' into shared memory.
 // Once a tile's logits are in, each consumer thread finds its block's 64th
@@ -577,10 +641,9 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
 // compares), starting from the bracket given by the chunks' second-largest
 // keys, and writes the candidates above it plus, of those equal to it, the
 // lowest indices.  The 1024 x 4-byte logits of a block never leave the SM.
-// `missing` sums sigmoid(z - offset) over the candidates left out: the sum
-// over all candidates (exact FP32 logits, accumulated as the chunks arrive)
-// minus that over the selected ones (their truncated logits).  The iteration
-// output (head row 1024) is kept in FP32.
+// The iteration output (head row 1024) and the gate (row 1025, whose sigmoid
+// is the predicted share of the plain loop's coefficient mass the shortlist
+// leaves out) are kept in FP32.
 //
 // Waits are bounded (about 2 s each); a wait that gives up sets bit 2 of the
 // status word, makes the other roles leave their loops, and the CTA drains
@@ -683,9 +746,9 @@ __device__ __forceinline__ void ld32_nw(uint32_t taddr, uint32_t (&r)[32])
 }
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void ld1(uint32_t taddr, uint32_t &r)
+__device__ __forceinline__ void ld2(uint32_t taddr, uint32_t &r0, uint32_t &r1)
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr) : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -697,25 +760,13 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16])
                  : "memory");
 }
 
-__device__ __forceinline__ float tanh_approx(float x)
-{
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// 16-bit key: upper half of the order-preserving image of a float
+// 16-bit ranking key of a logit: z on a fixed-point grid of step 2^-10
+// over [-32, 32), rounded down and clamped (NaN to 0), so keys order like
+// the logits up to that step.
 __device__ __forceinline__ uint32_t key16(float z)
 {
-    const uint32_t u = __float_as_uint(z);
-    return (u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u)) >> 16;
-}
-// the midpoint of the floats whose key is k (lower 16 bits 0x8000): within
-// half a bfloat16 step of each of them, and not biased to either side
-__device__ __forceinline__ float key16_value(uint32_t k)
-{
-    const uint32_t u = (k << 16) | 0x8000u;
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+    const float t = fminf(fmaxf((z + 32.f) * 1024.f, 0.f), 65535.f);
+    return __float2uint_rd(t);
 }
 
 // Number of this lane's block's keys >= cand (all 32 lanes of the warp call
@@ -744,7 +795,7 @@ __device__ __forceinline__ uint32_t count_ge(uint32_t trow, const uint32_t *skey
 // bias: 1025 FP32; out: one Shortlist per block.
 __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a3, int nbh, int nbw,
                                                                   const unsigned char *packed, const float *bias,
-                                                                  float offset, Shortlist *out, int *status)
+                                                                  Shortlist *out, int *status)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *A = sm;
@@ -777,7 +828,6 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
     const uint32_t tmem = *tslot;
     const long long nb = (long long)nbh * nbw;
     const long long n_tiles = (nb + kM - 1) / kM;
-    const float half_off = 0.5f * offset;
 
     if (warp < 4) {
         // ------------------------------------------------ consumers --
@@ -790,18 +840,19 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
             const long long b = tile * kM + r;
             const bool valid = b < nb;
             uint32_t lo = 0xFFFFu, hi = 0;
-            float tsum = 0.f, nu = 0.f;
+            float nu = 0.f, gate = 0.f;
             for (int c = 0; c < kChunksPerTile; ++c, ++g) {
                 const int ab = (int)(g & 1);
                 const bool got = wait(bar(kBarAccFull + ab), (uint32_t)((g >> 1) & 1), abort);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (c == kChunks) {
-                    uint32_t v0;
-                    ld1(trow + kAccCol + 32 * ab, v0);
+                    uint32_t v0, v1;
+                    ld2(trow + kAccCol + 32 * ab, v0, v1);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     arrive(bar(kBarAccEmpty + ab));
                     nu = __uint_as_float(v0) + bias_s[1024];
+                    gate = __uint_as_float(v1) + bias_s[1025];
                     continue;
                 }
                 uint32_t v[32];
@@ -811,9 +862,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
                 uint32_t pk[16], m1 = 0, m2 = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float z = __uint_as_float(v[j]) + bias_s[kNC * c + j];
-                    tsum += tanh_approx(fmaf(0.5f, z, -half_off));
-                    const uint32_t k = key16(z);
+                    const uint32_t k = key16(__uint_as_float(v[j]) + bias_s[kNC * c + j]);
                     m2 = max(m2, min(m1, k));
                     m1 = max(m1, k);
                     if (j < 16) pk[j] = k;
@@ -848,7 +897,6 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
             const uint32_t n_above = count_ge(trow, skeys, thr < 0xFFFFu ? thr + 1 : 0x10000u);
             int eq_left = kShortlist - (int)(thr < 0xFFFFu ? n_above : 0u);
             int pos = 0;
-            float tsel = 0.f;
             Shortlist *sl = out + b;
             auto take = [&](uint32_t k, int idx) {
                 const bool t = k > thr || (k == thr && eq_left > 0);
@@ -856,7 +904,6 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
                     if (k == thr) --eq_left;
                     if (valid && pos < kShortlist) sl->idx[pos] = (uint16_t)idx;
                     ++pos;
-                    tsel += tanh_approx(fmaf(0.5f, key16_value(k), -half_off));
                 }
             };
 #pragma unroll 1
@@ -878,7 +925,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
                 for (int j = 0; j < 16; ++j) take(w[j] >> 16, kNC * c + 16 + j);
             }
             if (valid) {
-                sl->missing = 0.5f * (tsum - tsel) + 0.5f * (float)(1024 - kShortlist);
+                sl->missing = 1.f / (1.f + __expf(-gate));
                 sl->nu_frac = nu;
             }
             // the key columns are read; the next tile's chunks may overwrite them
@@ -1044,7 +1091,6 @@ struct rljsde_net {
     unsigned char *head_packed = nullptr;   // head weights for head_select_kernel (bfloat16, 599,040 B)
     int step = 0;
     int sm_count = 1;                    // SMs of the device the network lives on
-    float logit_offset = 0.f;            // log of the positive weight of the last training step
     // training buffers, sized for `cap` samples
     int cap = 0;
     float *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *g1 = nullptr, *g2 = nullptr, *g3 = nullptr;
@@ -1163,8 +1209,7 @@ int propose_pass(const rljsde_plan_t *plan, const rljsde_net_t *net, const float
     const long long tiles = ((long long)nb + hd::kM - 1) / hd::kM;
     const int grid = (int)(tiles < sms ? tiles : sms);             // one CTA per SM (all of tensor memory)
     hd::head_select_kernel<<<grid, hd::kThreads, hd::kSmem, s>>>(a3, nbh, nbw, net->head_packed, b + kBh,
-                                                                 net->logit_offset, static_cast<Shortlist *>(shortlists),
-                                                                 plan->d_status);
+                                                                 static_cast<Shortlist *>(shortlists), plan->d_status);
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
 
@@ -1210,6 +1255,7 @@ int rljsde_net_create(rljsde_net_t **out, uint64_t seed)
     fill(kWh, kBh - kWh, 288.0 * 8.0);
     for (int k = 0; k < 1024; ++k) h[kBh + k] = -3.0f;     // start near the ~6% positive rate
     h[kBh + 1024] = 1.0f;
+    h[kBh + 1025] = -2.0f;                                   // gate: sigmoid(-2) = 0.12 of the mass left out
     if (cudaMemcpy(n->master, h.data(), b, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(n->m, 0, b) != cudaSuccess || cudaMemset(n->v, 0, b) != cudaSuccess) {
         rljsde_net_destroy(n);
@@ -1262,8 +1308,8 @@ int rljsde_net_patches(const float *lr, size_t lr_pitch, const uint8_t *mask, in
 // [n][2] (bi, bj) of the image lr_h x lr_w they come from).  grad (device,
 // num_params) receives the gradient; *loss_host the mean loss.
 static int loss_grad(rljsde_net *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
-                     const uint8_t *targets, const float *nu_t, float pos_w, float nu_w, float *loss_host,
-                     cudaStream_t s)
+                     const uint8_t *targets, const float *nu_t, const float *mass, float pos_w, float nu_w,
+                     float gate_w, float *loss_host, cudaStream_t s)
 {
     int st = ensure_train(net, n);
     if (st) return st;
@@ -1272,7 +1318,8 @@ static int loss_grad(rljsde_net *net, const float *x, const int32_t *blocks, int
     forward_patches(net, n, lr_h, lr_w, s);
     cudaMemsetAsync(net->loss, 0, 4, s);
     const float *r = net->rounded;
-    loss_kernel<<<n, 256, 0, s>>>(net->z, net->master + kBh, targets, nu_t, n, pos_w, nu_w, net->gz, net->loss);
+    loss_kernel<<<n, 256, 0, s>>>(net->z, net->master + kBh, targets, nu_t, mass, n, pos_w, nu_w, gate_w, net->gz,
+                                  net->loss);
     cudaMemsetAsync(net->grad, 0, (size_t)kParams * 4, s);
     // head: gWh[k][j] = sum_s gz[s][k] f[s][j]; gbh = sum_s gz; gf[s][j] = sum_k gz[s][k] Wh[k][j]
     dim3 gw((kHeadIn + 63) / 64, (kOut + 63) / 64);
@@ -1297,12 +1344,12 @@ static int loss_grad(rljsde_net *net, const float *x, const int32_t *blocks, int
 }
 
 int rljsde_net_gradient(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
-                        const uint8_t *targets, const float *nu_t, float pos_w, float nu_w, float *grad_out,
-                        float *loss_host, void *stream)
+                        const uint8_t *targets, const float *nu_t, const float *mass, float pos_w, float nu_w,
+                        float gate_w, float *grad_out, float *loss_host, void *stream)
 {
     if (!net || !x || !blocks || !targets || !nu_t || n < 1) return RLJSDE_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    int st = loss_grad(net, x, blocks, n, lr_h, lr_w, targets, nu_t, pos_w, nu_w, loss_host, s);
+    int st = loss_grad(net, x, blocks, n, lr_h, lr_w, targets, nu_t, mass, pos_w, nu_w, gate_w, loss_host, s);
     if (st) return st;
     if (grad_out && cudaMemcpyAsync(grad_out, net->grad, (size_t)kParams * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return RLJSDE_ERR_CUDA;
@@ -1310,15 +1357,14 @@ int rljsde_net_gradient(rljsde_net_t *net, const float *x, const int32_t *blocks
 }
 
 int rljsde_net_train_step(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
-                          const uint8_t *targets, const float *nu_t, float pos_w, float nu_w, float lr,
-                          float *loss_host, void *stream)
+                          const uint8_t *targets, const float *nu_t, const float *mass, float pos_w, float nu_w,
+                          float gate_w, float lr, float *loss_host, void *stream)
 {
     if (!net || !x || !blocks || !targets || !nu_t || n < 1 || !(lr > 0.f)) return RLJSDE_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    int st = loss_grad(net, x, blocks, n, lr_h, lr_w, targets, nu_t, pos_w, nu_w, loss_host, s);
+    int st = loss_grad(net, x, blocks, n, lr_h, lr_w, targets, nu_t, mass, pos_w, nu_w, gate_w, loss_host, s);
     if (st) return st;
     net->step += 1;
-    net->logit_offset = std::log(pos_w > 0.f ? pos_w : 1.f);
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
     adam_kernel<<<grid_for(kParams, 256), 256, 0, s>>>(net->master, net->grad, net->m, net->v, kParams, lr, b1, b2,
@@ -1328,7 +1374,7 @@ int rljsde_net_train_step(rljsde_net_t *net, const float *x, const int32_t *bloc
     return cudaStreamSynchronize(s) == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
 
-// Logits (+bias) of n patches: z_out device [n][1025].
+// Logits (+bias) of n patches: z_out device [n][1026].
 int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, int n, int lr_h, int lr_w,
                       float *z_out, void *stream)
 {

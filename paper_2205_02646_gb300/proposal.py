@@ -38,6 +38,17 @@ def nu_targets(tail, eps: float, nu_max: int):
     return (tail >= eps).sum(1).float() / nu_max
 
 
+def mass_from_trace(sel, dc):
+    """Per block and candidate, the plain loop's coefficient mass: the sum of
+    |gamma delta| over the iterations that selected it ((n, 1024) float)."""
+    import torch
+    n = sel.shape[0]
+    mag = torch.sqrt(dc[..., 0] ** 2 + dc[..., 1] ** 2)
+    out = torch.zeros((n, 1024), dtype=torch.float32, device=sel.device)
+    out.scatter_add_(1, sel.long() & 0xFFFF, mag)
+    return out
+
+
 def labels_from_trace(sel, dc, nu_max: int, k: int = SHORTLIST, eps: float = 0.2):
     """Targets (n, 1024) uint8 and iteration fractions (n,) from a trace."""
     import torch
@@ -59,9 +70,10 @@ def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu
     """Patches, block coordinates, targets and iteration targets for
     ``blocks_per_image`` random blocks of each of ``n_images`` synthetic
     size x size images (mask tiles cycled from ``tiles``).  With
-    ``keep_tail`` a sixth entry holds every sample's tail |gamma delta| sums
+    ``keep_tail`` a last entry holds every sample's tail |gamma delta| sums
     (n, nu_max), from which ``nu_targets`` gives the iteration targets of any
-    other threshold."""
+    other threshold.  Entries: patches, blocks, targets, iteration targets,
+    image shape, per-candidate mass (``mass_from_trace``), [tails]."""
     import torch
     lr = size // 2
     nb_side = lr // 2
@@ -74,7 +86,7 @@ def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu
     hr = torch.empty((size, size), device=device)
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    xs, bs, ts, ns, tails = [], [], [], [], []
+    xs, bs, ts, ns, ms, tails = [], [], [], [], [], []
     for i in range(n_images):
         t = i % len(tiles)
         f = synth.image_torch(size, size, n_sin, n_edges, seed * 100003 + i, 0.005, device)
@@ -82,7 +94,9 @@ def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu
         plans[t].reconstruct_trace(y, hr, sel, dc)
         pick = torch.randperm(nb, generator=g, device=device)[:blocks_per_image]
         dcp = dc.view(nb, nu_max, 2)[pick]
-        tg, nu_t = labels_from_trace(sel.view(nb, nu_max)[pick], dcp, nu_max, eps=eps)
+        selp = sel.view(nb, nu_max)[pick]
+        tg, nu_t = labels_from_trace(selp, dcp, nu_max, eps=eps)
+        ms.append(mass_from_trace(selp, dcp))
         blk = torch.stack([pick // nb_side, pick % nb_side], 1).int().contiguous()
         xs.append(rljsde.Net.patches(y, masks_d[t], blk))
         bs.append(blk)
@@ -92,14 +106,16 @@ def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu
             tails.append(tail_mass(dcp))
     for p in plans:
         p.check()
-    out = (torch.cat(xs), torch.cat(bs), torch.cat(ts), torch.cat(ns), (lr, lr))
+    out = (torch.cat(xs), torch.cat(bs), torch.cat(ts), torch.cat(ns), (lr, lr), torch.cat(ms))
     return out + (torch.cat(tails),) if keep_tail else out
 
 
-def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None):
-    """Adam with cosine decay over ``epochs`` passes of ``data``."""
+def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None,
+          gate_weight: float = 1.0):
+    """Adam with cosine decay over ``epochs`` passes of ``data`` (patches,
+    blocks, targets, iteration targets, shape, mass)."""
     import torch
-    x, blocks, targets, nu_t, shape = data[:5]
+    x, blocks, targets, nu_t, shape, mass = data[:6]
     n = x.shape[0]
     g = torch.Generator(device=x.device)
     g.manual_seed(seed)
@@ -112,7 +128,8 @@ def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed:
             idx = perm[i:i + batch]
             rate = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps))
             losses.append(net.train_step(x[idx].contiguous(), blocks[idx].contiguous(), shape,
-                                         targets[idx].contiguous(), nu_t[idx].contiguous(), lr=rate))
+                                         targets[idx].contiguous(), nu_t[idx].contiguous(), mass[idx].contiguous(),
+                                         lr=rate, gate_weight=gate_weight))
             step += 1
         if log:
             log("epoch %d loss %.4f" % (e, float(np.mean(losses[-max(1, n // batch):]))))

@@ -101,8 +101,8 @@ def _lib():
         lib.rljsde_net_get_params.argtypes = [vp, vp]
         lib.rljsde_net_set_params.argtypes = [vp, vp]
         lib.rljsde_net_patches.argtypes = [vp, sz, vp, i, i, i32p, i, vp, vp]
-        lib.rljsde_net_gradient.argtypes = [vp, vp, i32p, i, i, i, vp, vp, f, f, vp, ctypes.POINTER(f), vp]
-        lib.rljsde_net_train_step.argtypes = [vp, vp, i32p, i, i, i, vp, vp, f, f, f, ctypes.POINTER(f), vp]
+        lib.rljsde_net_gradient.argtypes = [vp, vp, i32p, i, i, i, vp, vp, vp, f, f, f, vp, ctypes.POINTER(f), vp]
+        lib.rljsde_net_train_step.argtypes = [vp, vp, i32p, i, i, i, vp, vp, vp, f, f, f, f, ctypes.POINTER(f), vp]
         lib.rljsde_net_logits.argtypes = [vp, vp, i32p, i, i, i, vp, vp]
         lib.rljsde_propose_workspace.argtypes = [vp]
         lib.rljsde_propose_workspace.restype = ctypes.c_size_t
@@ -368,25 +368,30 @@ class Net:
             "rljsde_net_patches")
         return x
 
-    def gradient(self, x, blocks, lr_shape, targets, nu_t, pos_weight=8.0, nu_weight=0.1, stream=None):
+    def gradient(self, x, blocks, lr_shape, targets, nu_t, mass=None, pos_weight=8.0, nu_weight=0.1,
+                 gate_weight=1.0, stream=None):
         import torch
         g = torch.empty(self.num_params(), dtype=torch.float32, device=x.device)
         loss = ctypes.c_float()
         _ok(_lib().rljsde_net_gradient(self._h, x.data_ptr(), blocks.data_ptr(), x.shape[0], lr_shape[0],
-                                       lr_shape[1], targets.data_ptr(), nu_t.data_ptr(), pos_weight, nu_weight,
+                                       lr_shape[1], targets.data_ptr(), nu_t.data_ptr(),
+                                       None if mass is None else mass.data_ptr(), pos_weight, nu_weight, gate_weight,
                                        g.data_ptr(), ctypes.byref(loss), _stream_ptr(stream)), "rljsde_net_gradient")
         return g, loss.value
 
-    def train_step(self, x, blocks, lr_shape, targets, nu_t, lr=1e-3, pos_weight=8.0, nu_weight=0.1, stream=None):
+    def train_step(self, x, blocks, lr_shape, targets, nu_t, mass=None, lr=1e-3, pos_weight=8.0, nu_weight=0.1,
+                   gate_weight=1.0, stream=None):
         loss = ctypes.c_float()
         _ok(_lib().rljsde_net_train_step(self._h, x.data_ptr(), blocks.data_ptr(), x.shape[0], lr_shape[0],
-                                         lr_shape[1], targets.data_ptr(), nu_t.data_ptr(), pos_weight, nu_weight,
-                                         lr, ctypes.byref(loss), _stream_ptr(stream)), "rljsde_net_train_step")
+                                         lr_shape[1], targets.data_ptr(), nu_t.data_ptr(),
+                                         None if mass is None else mass.data_ptr(), pos_weight, nu_weight,
+                                         gate_weight, lr, ctypes.byref(loss), _stream_ptr(stream)),
+            "rljsde_net_train_step")
         return loss.value
 
     def logits(self, x, blocks, lr_shape, stream=None):
         import torch
-        z = torch.empty((x.shape[0], 1025), dtype=torch.float32, device=x.device)
+        z = torch.empty((x.shape[0], 1026), dtype=torch.float32, device=x.device)
         _ok(_lib().rljsde_net_logits(self._h, x.data_ptr(), blocks.data_ptr(), x.shape[0], lr_shape[0],
                                      lr_shape[1], z.data_ptr(), _stream_ptr(stream)), "rljsde_net_logits")
         return z

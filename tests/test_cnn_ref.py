@@ -17,23 +17,26 @@ def _setup(seed=0, n=2):
     xs, origins = zip(*[cnn_ref.patch(y, mask, bi, bj) for bi, bj in blocks])
     targets = [(rng.random(1024) < 0.08).astype(float) for _ in blocks]
     nus = rng.random(len(blocks))
-    return params, list(xs), list(origins), mask.shape, targets, nus
+    masses = [rng.random(1024) * (rng.random(1024) < 0.1) for _ in blocks]
+    return params, list(xs), list(origins), mask.shape, targets, nus, masses
 
 
 def test_gradients_match_finite_differences():
-    params, xs, origins, shape, targets, nus = _setup()
-    loss, g = cnn_ref.loss_and_grads(params, xs, origins, shape, targets, nus, bf16=False)
+    params, xs, origins, shape, targets, nus, masses = _setup()
+    loss, g = cnn_ref.loss_and_grads(params, xs, origins, shape, targets, nus, masses, bf16=False)
     rng = np.random.default_rng(1)
     eps = 1e-6
     for name, shp in cnn_ref.SHAPES:
         for _ in range(6):
             idx = tuple(int(rng.integers(0, s)) for s in shp)
+            if name.startswith("head") and _ == 0:
+                idx = (1025,) + idx[1:]                      # the gate row
             p1 = {k: v.copy() for k, v in params.items()}
             p2 = {k: v.copy() for k, v in params.items()}
             p1[name][idx] += eps
             p2[name][idx] -= eps
-            l1, _ = cnn_ref.loss_and_grads(p1, xs, origins, shape, targets, nus, bf16=False)
-            l2, _ = cnn_ref.loss_and_grads(p2, xs, origins, shape, targets, nus, bf16=False)
+            l1, _ = cnn_ref.loss_and_grads(p1, xs, origins, shape, targets, nus, masses, bf16=False)
+            l2, _ = cnn_ref.loss_and_grads(p2, xs, origins, shape, targets, nus, masses, bf16=False)
             num = (l1 - l2) / (2 * eps)
             assert abs(num - g[name][idx]) <= 1e-6 + 1e-5 * abs(num), (name, idx, num, g[name][idx])
 
@@ -41,7 +44,7 @@ def test_gradients_match_finite_differences():
 def test_patch_equals_full_image_pass():
     """The head features of a block computed on its patch equal those of one
     pass of the same layers over the whole (zero-padded) image."""
-    params, xs, origins, shape, targets, nus = _setup(n=3)
+    params, xs, origins, shape, targets, nus, _ = _setup(n=3)
     rng = np.random.default_rng(2)
     f = synth.image(48, 48, 16, 2, 77)
     mask = synth.recurrent_mask(24, 24, 4, 3)

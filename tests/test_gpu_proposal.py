@@ -38,7 +38,7 @@ def test_gradients_match_fp64_reference(rl):
     rng = np.random.default_rng(0)
     params = net.get_params()
     # larger head weights than the init so every term of the gradient matters
-    params[cnn_ref.N_PARAMS - 1025 - 1025 * 288:cnn_ref.N_PARAMS - 1025] = rng.normal(0, 0.05, 1025 * 288)
+    params[cnn_ref.N_PARAMS - 1026 - 1026 * 288:cnn_ref.N_PARAMS - 1026] = rng.normal(0, 0.05, 1026 * 288)
     net.set_params(params)
     blocks = np.array([[0, 0], [5, 7], [11, 2], [6, 11]], np.int32)
     lr = torch.from_numpy(y).cuda()
@@ -47,11 +47,14 @@ def test_gradients_match_fp64_reference(rl):
     x = rl.Net.patches(lr, md, bd)
     targets = (rng.random((4, 1024)) < 0.07).astype(np.uint8)
     nus = rng.random(4).astype(np.float32)
-    g, loss = net.gradient(x, bd, mask.shape, torch.from_numpy(targets).cuda(), torch.from_numpy(nus).cuda())
+    mass = (rng.random((4, 1024)) * (rng.random((4, 1024)) < 0.1)).astype(np.float32)
+    g, loss = net.gradient(x, bd, mask.shape, torch.from_numpy(targets).cuda(), torch.from_numpy(nus).cuda(),
+                           torch.from_numpy(mass).cuda())
     xs, origins = zip(*[cnn_ref.patch(y, mask, int(bi), int(bj)) for bi, bj in blocks])
     np.testing.assert_allclose(x.cpu().numpy(), np.array(xs), rtol=0, atol=1e-7)
     ref_loss, ref_g = cnn_ref.loss_and_grads(cnn_ref.unflatten(params), list(xs), list(origins), mask.shape,
-                                             list(targets.astype(float)), list(nus.astype(float)))
+                                             list(targets.astype(float)), list(nus.astype(float)),
+                                             list(mass.astype(float)))
     assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss)
     got = cnn_ref.unflatten(g.cpu().numpy())
     for name, _ in cnn_ref.SHAPES:
@@ -207,7 +210,7 @@ def test_training_lowers_the_loss(rl):
     td = torch.from_numpy(targets).cuda()
     nud = torch.ones(nb, device="cuda")
     net = rl.Net(seed=1)
-    losses = [net.train_step(x, bd, mask.shape, td, nud, lr=2e-3) for _ in range(40)]
+    losses = [net.train_step(x, bd, mask.shape, td, nud, lr=2e-3) for _ in range(40)]      # no gate term
     assert losses[-1] < 0.8 * losses[0], losses[::8]
 
 
@@ -289,32 +292,32 @@ def test_restricted_loop_with_repeated_candidates(rl):
 
 
 def _key16(z):
-    """16-bit ranking key of FP32 logits: the upper half of the
-    order-preserving integer image (the logit truncated to bfloat16)."""
-    u = np.asarray(z, np.float32).view(np.uint32).astype(np.uint64)
-    k = np.where(u & 0x80000000, (~u) & 0xFFFFFFFF, u | 0x80000000)
-    return (k >> 16).astype(np.int64)
+    """16-bit ranking key of FP32 logits: z on a fixed-point grid of step
+    2^-10 over [-32, 32), rounded down and clamped."""
+    t = np.clip((np.asarray(z, np.float32) + np.float32(32.0)) * np.float32(1024.0), 0.0, 65535.0)
+    return np.floor(t).astype(np.int64)
 
 
 def _bias_pattern(name, rng):
     if name == "normal":
-        return rng.normal(-2.0, 1.5, 1025)
+        return rng.normal(-2.0, 1.5, 1026)
     if name == "ties":                                # few distinct values: exact ties at the threshold
-        return rng.choice(np.array([-3.0, -1.0, 0.5, 2.0]), 1025, p=[0.6, 0.3, 0.06, 0.04])
-    if name == "below_bf16":                          # distinct FP32 values, equal after truncation
-        return 1.0 + 2.0 ** -20 * rng.integers(0, 64, 1025) - 2.0 * (rng.random(1025) < 0.9)
-    return np.full(1025, 0.25)                        # all equal: the 64 lowest indices
+        return rng.choice(np.array([-3.0, -1.0, 0.5, 2.0]), 1026, p=[0.6, 0.3, 0.06, 0.04])
+    if name == "below_step":                          # distinct FP32 values within one 2^-10 key step
+        return 1.0 + 2.0 ** -20 * rng.integers(0, 64, 1026) - 2.0 * (rng.random(1026) < 0.9)
+    if name == "clamped":                             # beyond the key range: ties at its ends
+        return np.where(rng.random(1026) < 0.1, 40.0 + rng.random(1026), -40.0 - rng.random(1026))
+    return np.full(1026, 0.25)                        # all equal: the 64 lowest indices
 
 
-@pytest.mark.parametrize("pattern", ["normal", "ties", "below_bf16", "equal"])
+@pytest.mark.parametrize("pattern", ["normal", "ties", "below_step", "clamped", "equal"])
 def test_fused_selection_exact_on_bias_logits(rl, pattern):
     """With a zero head matrix every block's logits are the head biases
     exactly, so the fused head's shortlist must be the 64 largest biases by
-    their bfloat16-truncated keys, ties to the lower index, in increasing
-    index order, on every block; the iteration output is the bias of row
-    1024 exactly, and the left-out mass is the sum of sigmoid over the other
-    960 biases within the bound of its approximations (tanh.approx per term,
-    midpoint values of the selected keys)."""
+    their 16-bit keys (fixed-point step 2^-10 over [-32, 32)), ties to the
+    lower index, in increasing index order, on every block; the iteration
+    output is the bias of row 1024 exactly, and the gate the sigmoid of the
+    bias of row 1025."""
     import torch
     f, mask, y = _image(40, 56, 2)
     net = rl.Net(seed=4)
@@ -334,8 +337,5 @@ def test_fused_selection_exact_on_bias_logits(rl, pattern):
     want = np.sort(order[:64])
     assert np.array_equal(idx.astype(np.int64), np.broadcast_to(want, (nb, 64)))
     assert np.all(nu_frac == b32[1024])
-    rest = np.setdiff1d(np.arange(1024), want)
-    zr = b32.astype(np.float64)
-    ref = float(np.sum(1.0 / (1.0 + np.exp(-zr[rest]))))          # untrained network: offset 0
-    bound = 1024 * 2.5e-4 + float(np.sum(0.25 * np.abs(zr[want]) * 2.0 ** -8)) + 1e-3
-    assert np.all(np.abs(missing - ref) <= bound), (float(np.abs(missing - ref).max()), bound)
+    gate = 1.0 / (1.0 + np.exp(-np.float64(b32[1025])))
+    np.testing.assert_allclose(missing, gate, rtol=1e-5, atol=1e-7)
