@@ -630,17 +630,18 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
 //     core-matrix layout, 32 rows per chunk) through a ring of shared-memory
 //     slots with bulk copies and issues, per chunk, 18 tcgen05.mma (M 128,
 //     N 32, K 16) into one of two 32-column accumulators in tensor memory;
-//   - four consumer warps (warp w owns tensor-memory lanes 32w .. 32w + 31,
-//     one block per lane) read each chunk's logits, add the bias, and keep
-//     only a 16-bit ranking key per candidate: the logit on a fixed-point
-//     grid of step 2^-10 over [-32, 32).  Two keys share a 32-bit word; the
-//     keys of chunks 0..27 go back into tensor memory (columns 0..447), the
-//     last four chunks' into shared memory.
-// Once a tile's logits are in, each consumer thread finds its block's 64th
-// largest key by bisection over the key bits (counting with packed 16-bit
-// compares), starting from the bracket given by the chunks' second-largest
-// keys, and writes the candidates above it plus, of those equal to it, the
-// lowest indices.  The 1024 x 4-byte logits of a block never leave the SM.
+//   - eight consumer warps (two per tensor-memory lane quadrant, one block
+//     per lane) read each chunk's logits, add the bias, and keep only a
+//     15-bit ranking key per candidate: the logit on a fixed-point grid of
+//     step 2^-9 over [-32, 32).  Two keys share a 32-bit word; most go back
+//     into tensor memory (columns 0..447), four chunks' into shared memory.
+// Once a tile's logits are in, each block's 64th largest key is found by
+// bisection over the key bits, starting from the bracket given by the
+// chunks' second-largest keys; the two warps of a lane quadrant count one
+// half of the candidates each (eight packed keys per popc) and add their
+// counts through shared memory.  The candidates above it plus, of those
+// equal to it, the lowest indices form the shortlist.  The 1024 x 4-byte
+// logits of a block never leave the SM.
 // The iteration output (head row 1024) and the gate (row 1025, whose sigmoid
 // is the predicted share of the plain loop's coefficient mass the shortlist
 // leaves out) are kept in FP32.
@@ -653,12 +654,14 @@ constexpr int kM = 128;                                   // blocks per tile (MM
 constexpr int kNC = 32;                                   // candidates per chunk (MMA N)
 constexpr int kChunks = 1024 / kNC;                       // 32 candidate chunks
 constexpr int kChunksPerTile = kChunks + 1;               // + head rows 1024..1039 (N = 16)
-constexpr int kTmemKeyChunks = 28;                        // chunks whose keys stay in tensor memory
 constexpr int kKeyWords = kNC / 2;                        // 16 words of two 16-bit keys per chunk
-constexpr uint32_t kAccCol = kTmemKeyChunks * kKeyWords;  // 448: accumulators at 448 and 480
+constexpr int kHalfTmemChunks = 14;                       // per half: chunks whose keys stay in tensor memory
+constexpr uint32_t kHalfTmemWords = kHalfTmemChunks * kKeyWords;   // 224
+constexpr uint32_t kAccCol = 2 * kHalfTmemWords;          // 448: accumulators at 448 and 480
 constexpr uint32_t kTmemCols = 512;
-constexpr int kSmemKeyWords = (kChunks - kTmemKeyChunks) * kKeyWords;   // 64 per block
-constexpr int kSmemKeyStride = kSmemKeyWords + 1;                       // 65: rows start in distinct banks
+constexpr int kHalfSmemWords = 2 * kKeyWords;             // per half: two chunks' keys in shared memory
+constexpr int kSmemKeyStride = 2 * kHalfSmemWords + 1;    // 65: rows start in distinct banks
+constexpr uint32_t kGuard = 0x80008000u;                  // bit 15 of both key halves
 constexpr uint32_t kLBO = 128, kSBO = (kHeadIn / 8) * 128;              // 4608
 constexpr uint32_t kABytes = (kM / 8) * kSBO;                           // 73,728
 constexpr uint32_t kBChunkBytes = (kNC / 8) * kSBO;                     // 18,432
@@ -669,16 +672,20 @@ constexpr int kBias = 1040;
 constexpr uint32_t kOffB = kABytes;
 constexpr uint32_t kOffKeys = kOffB + kSlots * kBChunkBytes;
 constexpr uint32_t kOffBias = kOffKeys + kM * kSmemKeyStride * 4;
-constexpr uint32_t kOffBar = kOffBias + kBias * 4;
+constexpr uint32_t kOffX = kOffBias + kBias * 4;                        // consumer exchange: 8 x 2 x 128 ints
+constexpr uint32_t kOffBar = kOffX + 8 * 2 * kM * 4;
 // barriers: a_full, a_free, b_full[4], b_empty[4], acc_full[2], acc_empty[2]
 constexpr int kBarAFull = 0, kBarAFree = 1, kBarBFull = 2, kBarBEmpty = 2 + kSlots, kBarAccFull = 2 + 2 * kSlots,
               kBarAccEmpty = kBarAccFull + 2, kNumBars = kBarAccEmpty + 2;
 constexpr uint32_t kOffMisc = kOffBar + kNumBars * 8;     // tensor-memory address, abort flag
 constexpr uint32_t kSmem = kOffMisc + 16;
 static_assert(kSmem <= 227 * 1024, "fused head operands must fit in shared memory");
-static_assert(kOffB % 128 == 0 && kOffKeys % 16 == 0 && kOffBias % 16 == 0 && kOffBar % 8 == 0, "alignment");
-constexpr int kConsumers = 128, kGatherers = 128;
-constexpr int kThreads = kConsumers + kGatherers + 32;   // + the issuer warp
+static_assert(kOffB % 128 == 0 && kOffKeys % 16 == 0 && kOffBias % 16 == 0 && kOffX % 16 == 0 && kOffBar % 8 == 0,
+              "alignment");
+constexpr int kSet = 128;                                 // consumer threads per set (four warps, one per lane quadrant)
+constexpr int kConsumers = 2 * kSet, kGatherers = 128;
+constexpr int kThreads = kConsumers + kGatherers + 32;    // + the issuer warp: 416
+
 // D FP32, A and B bfloat16, both K-major, M = 128, N = n
 __host__ __device__ constexpr uint32_t idesc(int n)
 {
@@ -760,39 +767,69 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16])
                  : "memory");
 }
 
-// 16-bit ranking key of a logit: z on a fixed-point grid of step 2^-10
-// over [-32, 32), rounded down and clamped (NaN to 0), so keys order like
-// the logits up to that step.
-__device__ __forceinline__ uint32_t key16(float z)
+// 15-bit ranking key of a logit: z on a fixed-point grid of step 2^-9 over
+// [-32, 32), rounded down and clamped (NaN to 0), so keys order like the
+// logits up to that step.  Stored with bit 15 set (a guard bit, see
+// count_half).
+__device__ __forceinline__ uint32_t key15(float z)
 {
-    const float t = fminf(fmaxf((z + 32.f) * 1024.f, 0.f), 65535.f);
+    const float t = fminf(fmaxf((z + 32.f) * 512.f, 0.f), 32767.f);
     return __float2uint_rd(t);
 }
 
-// Number of this lane's block's keys >= cand (all 32 lanes of the warp call
-// it together: the tensor-memory loads are warp-collective).
-__device__ __forceinline__ uint32_t count_ge(uint32_t trow, const uint32_t *skeys, uint32_t cand)
+__device__ __forceinline__ void pair_sync(int quadrant)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + quadrant) : "memory");
+}
+
+// Sum over 8 key words of the halves >= cand.  Every half holds key | 0x8000,
+// so w - (cand | cand << 16) borrows in neither half (cand < 0x8000) and
+// leaves bit 15 (bit 31) set iff the low (high) key is >= cand; the eight
+// words' flag bits are shifted into distinct positions and counted at once.
+__device__ __forceinline__ uint32_t count8(const uint32_t *w, uint32_t c2)
+{
+    uint32_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x |= ((w[i] - c2) >> i) & (kGuard >> i);
+    return __popc(x);
+}
+
+// Keys >= cand in one half of this lane's block (all 32 lanes of the warp
+// call it together: the tensor-memory loads are warp-collective).
+__device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *skeys, uint32_t cand)
 {
     const uint32_t c2 = cand | (cand << 16);
-    uint32_t acc = 0;
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
 #pragma unroll 1
-    for (int i = 0; i < kTmemKeyChunks / 2; i += 2) {
-        uint32_t v[32], u[32];
-        ld32_nw(trow + 32 * i, v);
-        ld32_nw(trow + 32 * i + 32, u);
-        wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc = __vsub2(acc, __vcmpgeu2(v[j], c2));
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc = __vsub2(acc, __vcmpgeu2(u[j], c2));
+    for (int i = 0; i < kHalfTmemChunks / 2; ++i) {
+        uint32_t v[32];
+        ld32(tcol + 32 * i, v);
+        n0 += count8(v, c2);
+        n1 += count8(v + 8, c2);
+        n2 += count8(v + 16, c2);
+        n3 += count8(v + 24, c2);
     }
-#pragma unroll 8
-    for (int j = 0; j < kSmemKeyWords; ++j) acc = __vsub2(acc, __vcmpgeu2(skeys[j], c2));
-    return (acc & 0xFFFFu) + (acc >> 16);
+    uint32_t s[32];
+#pragma unroll
+    for (int j = 0; j < kHalfSmemWords; ++j) s[j] = skeys[j];
+    n0 += count8(s, c2);
+    n1 += count8(s + 8, c2);
+    n2 += count8(s + 16, c2);
+    n3 += count8(s + 24, c2);
+    return (n0 + n1) + (n2 + n3);
 }
 
 // a3: conv3 output [32][nbh][nbw]; packed: head weights (see pack_head_kernel);
-// bias: 1025 FP32; out: one Shortlist per block.
+// bias: 1026 FP32; out: one Shortlist per block.
+//
+// Consumers: warp w (0..7) reads tensor-memory lane quadrant q = w % 4 (the
+// blocks 32 q .. 32 q + 31 of a tile) and belongs to set s = w / 4.  Set s
+// converts the chunks that land in accumulator s (every other chunk), and
+// owns candidates 512 s .. 512 s + 511 for the selection: their keys sit in
+// tensor-memory columns 224 s .. 224 s + 223 (chunks 16 s .. 16 s + 13) and
+// shared-memory words 32 s .. 32 s + 31 of the block's row (the last two
+// chunks of the half).  The two warps of a quadrant add their counts through
+// shared memory and a named barrier, so both take the same bisection steps.
 __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a3, int nbh, int nbw,
                                                                   const unsigned char *packed, const float *bias,
                                                                   Shortlist *out, int *status)
@@ -801,6 +838,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
     unsigned char *A = sm;
     uint32_t *skeys_all = reinterpret_cast<uint32_t *>(sm + kOffKeys);
     float *bias_s = reinterpret_cast<float *>(sm + kOffBias);
+    uint32_t *xch = reinterpret_cast<uint32_t *>(sm + kOffX);          // [8][2][128]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kOffMisc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + kOffMisc + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -810,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
     for (int i = tid; i < kBias; i += blockDim.x) bias_s[i] = i < kOut ? bias[i] : 0.f;
     if (tid == 0) {
         for (int i = 0; i < kNumBars; ++i) {
-            const uint32_t count = i == kBarAFull ? kGatherers : i >= kBarAccEmpty ? kConsumers : 1u;
+            const uint32_t count = i == kBarAFull ? kGatherers : i >= kBarAccEmpty ? kSet : 1u;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(count) : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -829,74 +867,98 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
     const long long nb = (long long)nbh * nbw;
     const long long n_tiles = (nb + kM - 1) / kM;
 
-    if (warp < 4) {
+    if (warp < 8) {
         // ------------------------------------------------ consumers --
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-        const int r = 32 * warp + lane;
-        uint32_t *skeys = skeys_all + r * kSmemKeyStride;
-        long long g = 0;
+        const int q = warp & 3, set = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        const int r = 32 * q + lane;
+        uint32_t *srow = skeys_all + r * kSmemKeyStride;
+        auto X = [&](int slot, int s) -> uint32_t & { return xch[(slot * 2 + s) * kM + r]; };
         bool ok = true;
-        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        long long it = 0;
+        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
             const long long b = tile * kM + r;
             const bool valid = b < nb;
-            uint32_t lo = 0xFFFFu, hi = 0;
-            float nu = 0.f, gate = 0.f;
-            for (int c = 0; c < kChunksPerTile; ++c, ++g) {
-                const int ab = (int)(g & 1);
-                const bool got = wait(bar(kBarAccFull + ab), (uint32_t)((g >> 1) & 1), abort);
+            uint32_t lo = 0x7FFFu, hi = 0;
+            for (int c = 0; c < kChunksPerTile; ++c) {
+                const long long g = it * kChunksPerTile + c;
+                if ((int)(g & 1) != set) continue;                      // the other set's accumulator
+                const bool got = wait(bar(kBarAccFull + set), (uint32_t)((g >> 1) & 1), abort);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (c == kChunks) {
                     uint32_t v0, v1;
-                    ld2(trow + kAccCol + 32 * ab, v0, v1);
+                    ld2(trow + kAccCol + 32 * set, v0, v1);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    arrive(bar(kBarAccEmpty + ab));
-                    nu = __uint_as_float(v0) + bias_s[1024];
-                    gate = __uint_as_float(v1) + bias_s[1025];
+                    arrive(bar(kBarAccEmpty + set));
+                    if (valid) {
+                        out[b].nu_frac = __uint_as_float(v0) + bias_s[1024];
+                        out[b].missing = 1.f / (1.f + __expf(-(__uint_as_float(v1) + bias_s[1025])));
+                    }
                     continue;
                 }
                 uint32_t v[32];
-                ld32(trow + kAccCol + 32 * ab, v);
+                ld32(trow + kAccCol + 32 * set, v);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                arrive(bar(kBarAccEmpty + ab));
+                arrive(bar(kBarAccEmpty + set));
                 uint32_t pk[16], m1 = 0, m2 = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const uint32_t k = key16(__uint_as_float(v[j]) + bias_s[kNC * c + j]);
+                    const uint32_t k = key15(__uint_as_float(v[j]) + bias_s[kNC * c + j]);
                     m2 = max(m2, min(m1, k));
                     m1 = max(m1, k);
                     if (j < 16) pk[j] = k;
                     else pk[j - 16] |= k << 16;
                 }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pk[j] |= kGuard;
                 lo = min(lo, m2);
                 hi = max(hi, m2);
-                if (c < kTmemKeyChunks) {
-                    st16(trow + kKeyWords * c, pk);
+                const int h = c >> 4, cq = c & 15;
+                if (cq < kHalfTmemChunks) {
+                    st16(trow + kHalfTmemWords * h + kKeyWords * cq, pk);
                 } else {
 #pragma unroll
-                    for (int w = 0; w < 16; ++w) skeys[(c - kTmemKeyChunks) * kKeyWords + w] = pk[w];
+                    for (int j = 0; j < 16; ++j) srow[kHalfSmemWords * h + kKeyWords * (cq - kHalfTmemChunks) + j] = pk[j];
                 }
             }
             if (!ok) break;
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            // the bracket from both sets' chunks: 64 keys >= lo, the 64th largest <= hi
+            X(0, set) = lo;
+            X(1, set) = hi;
+            pair_sync(q);
+            lo = min(X(0, 0), X(0, 1));
+            hi = max(X(1, 0), X(1, 1));
+            const uint32_t tcol = trow + kHalfTmemWords * set;
+            const uint32_t *shalf = srow + kHalfSmemWords * set;
             // bisection for the 64th largest key in [lo, hi]
             const uint32_t diff = hi ^ lo;
             const int top = diff ? 31 - __clz(diff) : -1;
             uint32_t thr = top < 0 ? hi : (hi & ~((2u << top) - 1u));
-            int bit = top;
+            int bit = top, step = 0;
             bool active = top >= 0;
             while (__any_sync(0xffffffffu, active)) {
                 const uint32_t cand = active ? (thr | (1u << bit)) : 0u;
-                const uint32_t cnt = count_ge(trow, skeys, cand);
+                const int slot = 2 + (step & 1);
+                X(slot, set) = count_half(tcol, shalf, cand);
+                pair_sync(q);
+                const uint32_t cnt = X(slot, 0) + X(slot, 1);
+                ++step;
                 if (active) {
                     if (cnt >= (uint32_t)kShortlist) thr = cand;
                     if (cnt == (uint32_t)kShortlist || --bit < 0) active = false;
                 }
             }
-            // candidates above thr, then those equal to it by increasing index
-            const uint32_t n_above = count_ge(trow, skeys, thr < 0xFFFFu ? thr + 1 : 0x10000u);
-            int eq_left = kShortlist - (int)(thr < 0xFFFFu ? n_above : 0u);
-            int pos = 0;
+            // per half: keys > thr and keys >= thr; the lower half's equal keys come first
+            X(4, set) = thr < 0x7FFFu ? count_half(tcol, shalf, thr + 1) : 0u;
+            X(5, set) = count_half(tcol, shalf, thr);
+            pair_sync(q);
+            const uint32_t gt0 = X(4, 0), gt1 = X(4, 1), eq0 = X(5, 0) - gt0;
+            const int quota = kShortlist - (int)(gt0 + gt1);
+            const int take0 = min((int)eq0, quota);
+            int eq_left = set == 0 ? take0 : quota - take0;
+            int pos = set == 0 ? 0 : (int)gt0 + take0;
             Shortlist *sl = out + b;
             auto take = [&](uint32_t k, int idx) {
                 const bool t = k > thr || (k == thr && eq_left > 0);
@@ -906,34 +968,32 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
                     ++pos;
                 }
             };
+            const int base = 512 * set;
 #pragma unroll 1
-            for (int i = 0; i < kTmemKeyChunks / 2; ++i) {
+            for (int i = 0; i < kHalfTmemChunks / 2; ++i) {
                 uint32_t v[32];
-                ld32(trow + 32 * i, v);
+                ld32(tcol + 32 * i, v);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {        // chunk 2i + h: words 16h .. 16h + 15
+                for (int hh = 0; hh < 2; ++hh) {      // chunk 2i + hh of the half: words 16 hh .. 16 hh + 15
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) take(v[16 * h + j] & 0xFFFFu, 64 * i + 32 * h + j);
+                    for (int j = 0; j < 16; ++j) take(v[16 * hh + j] & 0x7FFFu, base + 64 * i + 32 * hh + j);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) take(v[16 * h + j] >> 16, 64 * i + 32 * h + 16 + j);
+                    for (int j = 0; j < 16; ++j) take((v[16 * hh + j] >> 16) & 0x7FFFu, base + 64 * i + 32 * hh + 16 + j);
                 }
             }
 #pragma unroll 1
-            for (int c = kTmemKeyChunks; c < kChunks; ++c) {
-                const uint32_t *w = skeys + (c - kTmemKeyChunks) * kKeyWords;
-                for (int j = 0; j < 16; ++j) take(w[j] & 0xFFFFu, kNC * c + j);
-                for (int j = 0; j < 16; ++j) take(w[j] >> 16, kNC * c + 16 + j);
+            for (int cq = kHalfTmemChunks; cq < 16; ++cq) {
+                const uint32_t *w = shalf + kKeyWords * (cq - kHalfTmemChunks);
+                for (int j = 0; j < 16; ++j) take(w[j] & 0x7FFFu, base + kNC * cq + j);
+                for (int j = 0; j < 16; ++j) take((w[j] >> 16) & 0x7FFFu, base + kNC * cq + 16 + j);
             }
-            if (valid) {
-                sl->missing = 1.f / (1.f + __expf(-gate));
-                sl->nu_frac = nu;
-            }
-            // the key columns are read; the next tile's chunks may overwrite them
+            // every key of the tile is read before either set converts the next tile's chunks
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            pair_sync(q);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         if (!ok) *abort = 1;
-    } else if (warp < 8) {
+    } else if (warp < 12) {
         // -------------------------------------------------- gatherers --
         const int p = tid - kConsumers;
         const long long plane = nb;
@@ -1032,9 +1092,9 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// Head weights (FP32 [1025][288], feature index ci * 9 + t) -> bfloat16 in
+// Head weights (FP32 [1026][288], feature index ci * 9 + t) -> bfloat16 in
 // the core-matrix layout of head_select_kernel: chunk c of 32 rows (the
-// last one 16 rows: 1024..1039, zero beyond 1024), K index t * 32 + ci.
+// last one 16 rows: 1024..1039, zero beyond 1025), K index t * 32 + ci.
 __global__ void pack_head_kernel(const float *wh, unsigned char *packed)
 {
     const int total = (kChunks * kNC + 16) * kHeadIn;
