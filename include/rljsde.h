@@ -253,15 +253,15 @@ int rljsde_net_logits(rljsde_net_t *net, const float *x, const int32_t *blocks, 
 size_t rljsde_propose_workspace(const rljsde_plan_t *plan);
 /* Run the network over the whole image and write one rljsde_shortlist per
  * block (device, n_blocks entries, block order bi * (2 lr_w / 4) + bj):
- * conv1 on the CUDA cores, conv2 and conv3 on the tensor cores (bfloat16
- * input taps, FP32 accumulation), then one kernel that gathers each block's
- * head features, multiplies them by the head on the tensor cores (bfloat16
- * operands, FP32 accumulation in tensor memory) and selects the 64 largest
- * logits on the SM, so the logits never reach device memory.  A tensor-core
- * or copy wait that gives up is reported by rljsde_check.  Asynchronous; the
- * caller owns shortlists and workspace (rljsde_propose_workspace bytes:
- * 212 bytes per L-pixel).  The network reads opaque-sub-pixel codes: plans
- * of the three-quarter layout only. */
+ * conv1 on the CUDA cores straight from lr and the plan's mask, conv2 and
+ * conv3 on the tensor cores (bfloat16 activations, FP32 accumulation), then
+ * one kernel that gathers each block's head features, multiplies them by the
+ * head on the tensor cores (bfloat16 operands, FP32 accumulation in tensor
+ * memory) and selects the 64 largest logits on the SM, so the logits never
+ * reach device memory.  A tensor-core or copy wait that gives up is reported
+ * by rljsde_check.  Asynchronous; the caller owns shortlists and workspace
+ * (rljsde_propose_workspace bytes: 96 bytes per L-pixel).  The network reads
+ * opaque-sub-pixel codes: plans of the three-quarter layout only. */
 int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
                    void *shortlists, void *workspace, size_t workspace_bytes, void *stream);
 /*
@@ -275,8 +275,8 @@ int rljsde_propose(const rljsde_plan_t *plan, const rljsde_net_t *net, const flo
  * The scratch is one fixed 32 MiB array inside the library, so every GPU
  * that loads the library holds it until the process exits.  Images whose
  * working set does not fit are rejected with RLJSDE_ERR_BAD_SHAPE: about
- * 158,000 L-pixels at most (212 bytes each; for example 396 x 396 L-pixels,
- * a 792 x 792 HR image).  The first call on a device looks the array's
+ * 349,000 L-pixels at most (96 bytes each; for example 590 x 590 L-pixels,
+ * a 1180 x 1180 HR image).  The first call on a device looks the array's
  * address up (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array: two calls whose work overlaps on
  * the GPU (different streams, or different host threads) race and corrupt

@@ -73,21 +73,62 @@ __global__ void patches_kernel(const float *lr, long long lr_pitch, const uint8_
     }
 }
 
-// Input planes of a whole image: x[5][lr_h][lr_w].
-__global__ void image_input_kernel(const float *lr, long long lr_pitch, const uint8_t *mask, int lr_h, int lr_w,
-                                   float *x)
+// conv1 over a whole image, straight from the measurements: out[P][Q][co]
+// (bfloat16, channels innermost) = relu(b[co] + sum over the 3x3 taps of
+// w[co][0][t] y/3 + w[co][1 + code][t]), the one-hot code input reduced to
+// the one weight its code selects; taps outside the image contribute
+// nothing.  FP32 arithmetic on the bfloat16-rounded weights; the output is
+// rounded to bfloat16, the precision conv2 reads it at.  Each thread
+// computes all 32 channels of one position, weights read four channels at a
+// time from shared memory.
+__global__ void __launch_bounds__(128, 4) conv1_image_kernel(const float *lr, long long lr_pitch, const uint8_t *mask,
+                                                          int lr_h, int lr_w, const float *w, const float *b,
+                                                          __nv_bfloat16 *out)
 {
+    __shared__ float4 wt[5][9][kC / 4];          // [input channel][tap][output channels 4j .. 4j + 3]
+    __shared__ float bs[kC];
+    for (int i = threadIdx.x; i < 5 * 9 * kC; i += blockDim.x) {
+        const int ci = i / (9 * kC), t = (i / kC) % 9, co = i % kC;
+        reinterpret_cast<float *>(&wt[ci][t][0])[co] = w[(co * 5 + ci) * 9 + t];
+    }
+    for (int i = threadIdx.x; i < kC; i += blockDim.x) bs[i] = b[i];
+    __syncthreads();
     const long long plane = (long long)lr_h * lr_w;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
          i += (long long)gridDim.x * blockDim.x) {
         const int P = (int)(i / lr_w), Q = (int)(i % lr_w);
-        const float yv = lr[(long long)P * lr_pitch + Q];
-        const int c = mask[i];
-        x[i] = isfinite(yv) ? yv / 3.0f : 0.f;
-        x[plane + i] = c == 0;
-        x[2 * plane + i] = c == 1;
-        x[3 * plane + i] = c == 2;
-        x[4 * plane + i] = c == 3;
+        float acc[kC];
+#pragma unroll
+        for (int co = 0; co < kC; ++co) acc[co] = bs[co];
+#pragma unroll 1
+        for (int t = 0; t < 9; ++t) {
+            const int y = P + t / 3 - 1, x = Q + t % 3 - 1;
+            if (y < 0 || y >= lr_h || x < 0 || x >= lr_w) continue;
+            const float yv = lr[(long long)y * lr_pitch + x];
+            const float v = isfinite(yv) ? yv / 3.0f : 0.f;
+            const int code = mask[(long long)y * lr_w + x] & 3;
+#pragma unroll
+            for (int j = 0; j < kC / 4; ++j) {
+                const float4 a = wt[0][t][j], c = wt[1 + code][t][j];
+                acc[4 * j] = fmaf(a.x, v, acc[4 * j]) + c.x;
+                acc[4 * j + 1] = fmaf(a.y, v, acc[4 * j + 1]) + c.y;
+                acc[4 * j + 2] = fmaf(a.z, v, acc[4 * j + 2]) + c.z;
+                acc[4 * j + 3] = fmaf(a.w, v, acc[4 * j + 3]) + c.w;
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(out + i * kC);
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {
+            uint4 u;
+            uint32_t *pu = reinterpret_cast<uint32_t *>(&u);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(fmaxf(acc[cg * 8 + 2 * e], 0.f)));
+                const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(fmaxf(acc[cg * 8 + 2 * e + 1], 0.f)));
+                pu[e] = lo | (hi << 16);
+            }
+            dst[cg] = u;
+        }
     }
 }
 
@@ -506,10 +547,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return a | (b << 16);
 }
 
-// in: [32][hi][wi] FP32; out: [32][ho][wo] FP32; w: [32][32][9] (bfloat16-rounded), b: [32].
-__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const float *w, const float *bias,
-                                                         float *out, int hi, int wi, int ho, int wo, int stride,
-                                                         int *status)
+// in: [hi][wi][32] bfloat16; out: [ho][wo][32] bfloat16 (relu(acc + b) rounded);
+// w: [32][32][9] (bfloat16-rounded), b: [32].
+__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in, const float *w, const float *bias,
+                                                         __nv_bfloat16 *out, int hi, int wi, int ho, int wo,
+                                                         int stride, int *status)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *A = sm, *B = sm + kABytes;
@@ -554,20 +596,15 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
         const bool valid = pos < total;
         const int oy = valid ? (int)(pos / wo) : 0, ox = valid ? (int)(pos % wo) : 0;
         unsigned char *arow = A + (tid >> 3) * kSBO + (tid & 7) * 16;
-        const long long plane = (long long)hi * wi;
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int y = stride * oy + t / 3 - 1, x = stride * ox + t % 3 - 1;
             const bool inb = valid && y >= 0 && y < hi && x >= 0 && x < wi;
-            const float *src = in + (inb ? (long long)y * wi + x : 0);
+            // the tap's 32 channels: 64 contiguous bytes, one core-matrix row per 8 channels
+            const uint4 *src = reinterpret_cast<const uint4 *>(in + (inb ? ((long long)y * wi + x) * kC : 0));
 #pragma unroll
             for (int cg = 0; cg < 4; ++cg) {
-                float v[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = inb ? src[(cg * 8 + e) * plane] : 0.f;
-                uint4 u;
-                u.x = pack_bf16(v[0], v[1]); u.y = pack_bf16(v[2], v[3]);
-                u.z = pack_bf16(v[4], v[5]); u.w = pack_bf16(v[6], v[7]);
+                const uint4 u = inb ? src[cg] : make_uint4(0u, 0u, 0u, 0u);
                 *reinterpret_cast<uint4 *>(arow + (t * 4 + cg) * kLBO) = u;
             }
         }
@@ -601,9 +638,17 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const float *in, const 
                      : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (valid) {
+            uint4 *dst = reinterpret_cast<uint4 *>(out + pos * kC);
 #pragma unroll
-            for (int co = 0; co < kC; ++co)
-                out[(long long)co * total + pos] = fmaxf(__uint_as_float(r[co]) + bias[co], 0.f);
+            for (int cg = 0; cg < 4; ++cg) {
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = fmaxf(__uint_as_float(r[cg * 8 + e]) + bias[cg * 8 + e], 0.f);
+                uint4 u;
+                u.x = pack_bf16(v[0], v[1]); u.y = pack_bf16(v[2], v[3]);
+                u.z = pack_bf16(v[4], v[5]); u.w = pack_bf16(v[6], v[7]);
+                dst[cg] = u;
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         (void)lane;
@@ -800,10 +845,25 @@ __device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *sk
 {
     const uint32_t c2 = cand | (cand << 16);
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    static_assert(kHalfTmemChunks / 2 == 7, "seven 32-column loads per half");
 #pragma unroll 1
-    for (int i = 0; i < kHalfTmemChunks / 2; ++i) {
+    for (int i = 0; i < 6; i += 2) {              // two loads in flight
+        uint32_t v[32], u[32];
+        ld32_nw(tcol + 32 * i, v);
+        ld32_nw(tcol + 32 * i + 32, u);
+        wait_ld();
+        n0 += count8(v, c2);
+        n1 += count8(v + 8, c2);
+        n2 += count8(v + 16, c2);
+        n3 += count8(v + 24, c2);
+        n0 += count8(u, c2);
+        n1 += count8(u + 8, c2);
+        n2 += count8(u + 16, c2);
+        n3 += count8(u + 24, c2);
+    }
+    {
         uint32_t v[32];
-        ld32(tcol + 32 * i, v);
+        ld32(tcol + 32 * 6, v);
         n0 += count8(v, c2);
         n1 += count8(v + 8, c2);
         n2 += count8(v + 16, c2);
@@ -819,7 +879,7 @@ __device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *sk
     return (n0 + n1) + (n2 + n3);
 }
 
-// a3: conv3 output [32][nbh][nbw]; packed: head weights (see pack_head_kernel);
+// a3: conv3 output [nbh][nbw][32] bfloat16; packed: head weights (see pack_head_kernel);
 // bias: 1026 FP32; out: one Shortlist per block.
 //
 // Consumers: warp w (0..7) reads tensor-memory lane quadrant q = w % 4 (the
@@ -830,7 +890,7 @@ __device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *sk
 // shared-memory words 32 s .. 32 s + 31 of the block's row (the last two
 // chunks of the half).  The two warps of a quadrant add their counts through
 // shared memory and a named barrier, so both take the same bisection steps.
-__global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a3, int nbh, int nbw,
+__global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfloat16 *a3, int nbh, int nbw,
                                                                   const unsigned char *packed, const float *bias,
                                                                   Shortlist *out, int *status)
 {
@@ -923,11 +983,15 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
                 }
             }
             if (!ok) break;
+            // keys this set stored are read by the other set too: complete the
+            // stores and order them before the barrier, the reads after it
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             // the bracket from both sets' chunks: 64 keys >= lo, the 64th largest <= hi
             X(0, set) = lo;
             X(1, set) = hi;
             pair_sync(q);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             lo = min(X(0, 0), X(0, 1));
             hi = max(X(1, 0), X(1, 1));
             const uint32_t tcol = trow + kHalfTmemWords * set;
@@ -937,28 +1001,44 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
             const int top = diff ? 31 - __clz(diff) : -1;
             uint32_t thr = top < 0 ? hi : (hi & ~((2u << top) - 1u));
             int bit = top, step = 0;
-            bool active = top >= 0;
+            bool active = top >= 0, exact = false;
+            uint32_t ge0 = 0;                     // the lower half's keys >= thr, once exact
             while (__any_sync(0xffffffffu, active)) {
                 const uint32_t cand = active ? (thr | (1u << bit)) : 0u;
                 const int slot = 2 + (step & 1);
                 X(slot, set) = count_half(tcol, shalf, cand);
                 pair_sync(q);
-                const uint32_t cnt = X(slot, 0) + X(slot, 1);
+                const uint32_t c0 = X(slot, 0), cnt = c0 + X(slot, 1);
                 ++step;
                 if (active) {
                     if (cnt >= (uint32_t)kShortlist) thr = cand;
-                    if (cnt == (uint32_t)kShortlist || --bit < 0) active = false;
+                    if (cnt == (uint32_t)kShortlist) { exact = true; ge0 = c0; active = false; }
+                    else if (--bit < 0) active = false;
                 }
             }
-            // per half: keys > thr and keys >= thr; the lower half's equal keys come first
-            X(4, set) = thr < 0x7FFFu ? count_half(tcol, shalf, thr + 1) : 0u;
-            X(5, set) = count_half(tcol, shalf, thr);
-            pair_sync(q);
-            const uint32_t gt0 = X(4, 0), gt1 = X(4, 1), eq0 = X(5, 0) - gt0;
-            const int quota = kShortlist - (int)(gt0 + gt1);
-            const int take0 = min((int)eq0, quota);
-            int eq_left = set == 0 ? take0 : quota - take0;
-            int pos = set == 0 ? 0 : (int)gt0 + take0;
+            // Exactly 64 keys >= thr: take them all; the lower half's come first.
+            // Otherwise per half the keys > thr and >= thr, and of the keys
+            // equal to thr the lowest indices (the lower half's first).
+            int eq_left, pos;
+            if (__all_sync(0xffffffffu, exact)) {
+                eq_left = kShortlist;
+                pos = set == 0 ? 0 : (int)ge0;
+            } else {
+                const uint32_t c_gt = count_half(tcol, shalf, thr < 0x7FFFu ? thr + 1 : 0x7FFFu);
+                X(4, set) = thr < 0x7FFFu ? c_gt : 0u;
+                X(5, set) = count_half(tcol, shalf, thr);
+                pair_sync(q);
+                if (exact) {
+                    eq_left = kShortlist;
+                    pos = set == 0 ? 0 : (int)ge0;
+                } else {
+                    const uint32_t gt0 = X(4, 0), gt1 = X(4, 1), eq0 = X(5, 0) - gt0;
+                    const int quota = kShortlist - (int)(gt0 + gt1);
+                    const int take0 = min((int)eq0, quota);
+                    eq_left = set == 0 ? take0 : quota - take0;
+                    pos = set == 0 ? 0 : (int)gt0 + take0;
+                }
+            }
             Shortlist *sl = out + b;
             auto take = [&](uint32_t k, int idx) {
                 const bool t = k > thr || (k == thr && eq_left > 0);
@@ -996,7 +1076,6 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
     } else if (warp < 12) {
         // -------------------------------------------------- gatherers --
         const int p = tid - kConsumers;
-        const long long plane = nb;
         unsigned char *arow = A + (p >> 3) * kSBO + (p & 7) * 16;
         long long it = 0;
         for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
@@ -1008,15 +1087,10 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const float *a
             for (int t = 0; t < 9; ++t) {
                 const int y = by + t / 3 - 1, x = bx + t % 3 - 1;
                 const bool inb = valid && y >= 0 && y < nbh && x >= 0 && x < nbw;
-                const float *src = a3 + (inb ? (long long)y * nbw + x : 0);
+                const uint4 *src = reinterpret_cast<const uint4 *>(a3 + (inb ? ((long long)y * nbw + x) * kC : 0));
 #pragma unroll
                 for (int cg = 0; cg < 4; ++cg) {
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = inb ? src[(cg * 8 + e) * plane] : 0.f;
-                    uint4 u;
-                    u.x = tc::pack_bf16(v[0], v[1]); u.y = tc::pack_bf16(v[2], v[3]);
-                    u.z = tc::pack_bf16(v[4], v[5]); u.w = tc::pack_bf16(v[6], v[7]);
+                    const uint4 u = inb ? src[cg] : make_uint4(0u, 0u, 0u, 0u);
                     *reinterpret_cast<uint4 *>(arow + (t * 4 + cg) * kLBO) = u;
                 }
             }
@@ -1194,7 +1268,8 @@ int grid_for(long long work, int threads)
 }
 
 // conv2 / conv3 of a whole image on the tensor cores (tc::conv_tc_kernel).
-int conv_tc(const float *in, const float *w, const float *b, float *out, int hi, int wi, int ho, int wo, int stride,
+int conv_tc(const __nv_bfloat16 *in, const float *w, const float *b, __nv_bfloat16 *out, int hi, int wi, int ho, int wo,
+            int stride,
             int sm_count, int *status, cudaStream_t s)
 {
     if (cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem) !=
@@ -1230,17 +1305,19 @@ void forward_patches(rljsde_net *net, int n, int lr_h, int lr_w, cudaStream_t s)
     gemm_kernel<<<gg, 256, 0, s>>>(n, kOut, kHeadIn, net->f, kHeadIn, 1, r + kWh, 1, kHeadIn, net->z, kOut, 0.f);
 }
 
-// Device bytes of the whole-image pass: input planes, conv1 output (both on
-// the L-pixel grid), conv2 and conv3 outputs (block grid), 256-byte aligned.
+// Device bytes of the whole-image pass: conv1 output on the L-pixel grid,
+// conv2 and conv3 outputs on the block grid, each 32 bfloat16 channels per
+// position (64 bytes), 256-byte aligned.
 size_t propose_bytes(size_t P, size_t nb)
 {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    return al(5 * P * 4) + al(kC * P * 4) + 2 * al(kC * nb * 4);
+    return al(P * kC * 2) + 2 * al(nb * kC * 2);
 }
 
 // The whole-image pass over `ws` (propose_bytes of it): conv1 on the CUDA
-// cores, conv2 and conv3 on the tensor cores, then the fused head and
-// top-64 selection (hd::head_select_kernel), which writes the shortlists.
+// cores straight from the measurements, conv2 and conv3 on the tensor cores,
+// then the fused head and top-64 selection (hd::head_select_kernel), which
+// writes the shortlists.  Activations are bfloat16 with channels innermost.
 int propose_pass(const rljsde_plan_t *plan, const rljsde_net_t *net, const float *lr, size_t lr_pitch,
                  void *shortlists, void *ws, cudaStream_t s)
 {
@@ -1248,17 +1325,15 @@ int propose_pass(const rljsde_plan_t *plan, const rljsde_net_t *net, const float
     const size_t P = (size_t)lr_h * lr_w, nb = (size_t)plan->n_blocks;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     char *w = static_cast<char *>(ws);
-    float *x = reinterpret_cast<float *>(w);   w += al(5 * P * 4);
-    float *a1 = reinterpret_cast<float *>(w);  w += al(kC * P * 4);
-    float *a2 = reinterpret_cast<float *>(w);  w += al(kC * nb * 4);
-    float *a3 = reinterpret_cast<float *>(w);
+    __nv_bfloat16 *a1 = reinterpret_cast<__nv_bfloat16 *>(w);  w += al(P * kC * 2);
+    __nv_bfloat16 *a2 = reinterpret_cast<__nv_bfloat16 *>(w);  w += al(nb * kC * 2);
+    __nv_bfloat16 *a3 = reinterpret_cast<__nv_bfloat16 *>(w);
     const float *r = net->rounded, *b = net->master;
     const int sms = plan->sm_count > 0 ? plan->sm_count : 1;
     const int cap = 8 * sms;                                   // 8 CTAs per SM at most
     auto gcap = [&](long long work, int threads) { int g = grid_for(work, threads); return g < cap ? g : cap; };
-    image_input_kernel<<<gcap((long long)P, 256), 256, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w, x);
-    ConvGeom g1{1, 5, lr_h, lr_w, lr_h, lr_w, 1, 1, nullptr, lr_h, lr_w};
-    conv_fwd_kernel<5><<<gcap((long long)P, 128), 128, 0, s>>>(x, r + kW1, b + kB1, a1, g1);
+    conv1_image_kernel<<<gcap((long long)P, 128), 128, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w,
+                                                               r + kW1, b + kB1, a1);
     // conv2 (stride 2, onto the block grid) and conv3 on the tensor cores
     int cst = conv_tc(a1, r + kW2, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, sms, plan->d_status, s);
     if (cst == RLJSDE_OK) cst = conv_tc(a2, r + kW3, b + kB3, a3, nbh, nbw, nbh, nbw, 1, sms, plan->d_status, s);
