@@ -204,7 +204,7 @@ typedef struct rljsde_net rljsde_net_t;   /* weights, Adam state, packed head we
 
 /* One block's proposal (device layout, 136 bytes):
  *   idx: the 64 candidates sigma * W + rho with the largest logits z, ranked
- *        by z on a fixed-point grid of step 2^-10 over [-32, 32) (rounded
+ *        by z on a fixed-point grid of step 2^-9 over [-32, 32) (rounded
  *        down, clamped), ties to the lower index, in increasing index order;
  *   missing: the network's gate, sigmoid of head row 1025: its prediction of
  *        the share of the plain loop's coefficient mass (sum of |gamma delta|

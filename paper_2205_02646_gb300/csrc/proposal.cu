@@ -818,7 +818,9 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16])
 // count_half).
 __device__ __forceinline__ uint32_t key15(float z)
 {
-    const float t = fminf(fmaxf((z + 32.f) * 512.f, 0.f), 32767.f);
+    // fmaf(z, 512, 16384) rounds 512 (z + 32) once, which equals (z + 32) * 512
+    // in FP32: scaling by a power of two commutes with the rounding
+    const float t = fminf(fmaxf(fmaf(z, 512.f, 16384.f), 0.f), 32767.f);
     return __float2uint_rd(t);
 }
 
@@ -996,48 +998,67 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
             hi = max(X(1, 0), X(1, 1));
             const uint32_t tcol = trow + kHalfTmemWords * set;
             const uint32_t *shalf = srow + kHalfSmemWords * set;
-            // bisection for the 64th largest key in [lo, hi]
-            const uint32_t diff = hi ^ lo;
-            const int top = diff ? 31 - __clz(diff) : -1;
-            uint32_t thr = top < 0 ? hi : (hi & ~((2u << top) - 1u));
-            int bit = top, step = 0;
-            bool active = top >= 0, exact = false;
-            uint32_t ge0 = 0;                     // the lower half's keys >= thr, once exact
+            // The 64th largest key T: count(L) >= 64 > count(H) with L = lo, H = hi + 1
+            // at the start.  Each step counts at x strictly inside (L, H): by
+            // interpolating the two known counts when the last step at least
+            // halved the interval, else at the midpoint (so at most about twice
+            // the bisection's steps, usually far fewer); x becomes L or H.  It
+            // ends when a count is exactly 64 (the keys >= x are the shortlist)
+            // or H = L + 1 (then T = L).  Counts at L and H, total and lower
+            // half, are kept for the tie rule.
+            uint32_t L = lo, H = hi + 1u;
+            int cL = -1, cH = -1, cL0 = 0, cH0 = 0;          // -1: not counted yet
+            bool active = H > L + 1u, exact = false, halved = true;
+            int step = 0;
             while (__any_sync(0xffffffffu, active)) {
-                const uint32_t cand = active ? (thr | (1u << bit)) : 0u;
+                uint32_t x = 0u;
+                if (active) {
+                    x = (L + H) >> 1;
+                    if (halved && cL >= 0 && cH >= 0 && cL > cH) {
+                        const uint32_t num = (uint32_t)(cL - kShortlist) * (H - L) + (uint32_t)(cL - cH) / 2u;
+                        x = L + num / (uint32_t)(cL - cH);
+                        x = min(max(x, L + 1u), H - 1u);
+                    }
+                }
                 const int slot = 2 + (step & 1);
-                X(slot, set) = count_half(tcol, shalf, cand);
+                X(slot, set) = count_half(tcol, shalf, x);
                 pair_sync(q);
-                const uint32_t c0 = X(slot, 0), cnt = c0 + X(slot, 1);
+                const int c0 = (int)X(slot, 0), c = c0 + (int)X(slot, 1);
                 ++step;
                 if (active) {
-                    if (cnt >= (uint32_t)kShortlist) thr = cand;
-                    if (cnt == (uint32_t)kShortlist) { exact = true; ge0 = c0; active = false; }
-                    else if (--bit < 0) active = false;
+                    const uint32_t width = H - L;
+                    if (c >= kShortlist) { L = x; cL = c; cL0 = c0; }
+                    else { H = x; cH = c; cH0 = c0; }
+                    halved = 2u * (H - L) <= width;
+                    if (c == kShortlist) { exact = true; active = false; }
+                    else if (H == L + 1u) active = false;
                 }
             }
-            // Exactly 64 keys >= thr: take them all; the lower half's come first.
-            // Otherwise per half the keys > thr and >= thr, and of the keys
-            // equal to thr the lowest indices (the lower half's first).
-            int eq_left, pos;
-            if (__all_sync(0xffffffffu, exact)) {
-                eq_left = kShortlist;
-                pos = set == 0 ? 0 : (int)ge0;
-            } else {
-                const uint32_t c_gt = count_half(tcol, shalf, thr < 0x7FFFu ? thr + 1 : 0x7FFFu);
-                X(4, set) = thr < 0x7FFFu ? c_gt : 0u;
-                X(5, set) = count_half(tcol, shalf, thr);
+            const uint32_t thr = L;
+            // Exactly 64 keys >= thr: take them all, the lower half's first.
+            // Otherwise thr is the 64th largest key: take the keys > thr, and of
+            // those equal to it the lowest indices (the lower half's first).
+            if (!__all_sync(0xffffffffu, exact || (cL >= 0 && cH >= 0))) {
+                // an end of the bracket that was never counted: count both per half
+                const uint32_t g1 = count_half(tcol, shalf, thr + 1u);
+                const uint32_t g0 = count_half(tcol, shalf, thr);
+                X(4, set) = g1;
+                X(5, set) = g0;
                 pair_sync(q);
-                if (exact) {
-                    eq_left = kShortlist;
-                    pos = set == 0 ? 0 : (int)ge0;
-                } else {
-                    const uint32_t gt0 = X(4, 0), gt1 = X(4, 1), eq0 = X(5, 0) - gt0;
-                    const int quota = kShortlist - (int)(gt0 + gt1);
-                    const int take0 = min((int)eq0, quota);
-                    eq_left = set == 0 ? take0 : quota - take0;
-                    pos = set == 0 ? 0 : (int)gt0 + take0;
+                if (!exact && (cL < 0 || cH < 0)) {
+                    cH0 = (int)X(4, 0); cH = cH0 + (int)X(4, 1);
+                    cL0 = (int)X(5, 0); cL = cL0 + (int)X(5, 1);
                 }
+            }
+            int eq_left, pos;
+            if (exact) {
+                eq_left = kShortlist;
+                pos = set == 0 ? 0 : cL0;
+            } else {
+                const int quota = kShortlist - cH;                  // keys > thr are cH
+                const int take0 = min(cL0 - cH0, quota);            // the lower half's keys == thr first
+                eq_left = set == 0 ? take0 : quota - take0;
+                pos = set == 0 ? 0 : cH0 + take0;
             }
             Shortlist *sl = out + b;
             auto take = [&](uint32_t k, int idx) {

@@ -291,10 +291,10 @@ def test_restricted_loop_with_repeated_candidates(rl):
     assert all(set(g_sel[b].tolist()) <= set(idx[b].tolist()) for b in blocks)
 
 
-def _key16(z):
-    """16-bit ranking key of FP32 logits: z on a fixed-point grid of step
-    2^-10 over [-32, 32), rounded down and clamped."""
-    t = np.clip((np.asarray(z, np.float32) + np.float32(32.0)) * np.float32(1024.0), 0.0, 65535.0)
+def _key15(z):
+    """15-bit ranking key of FP32 logits: z on a fixed-point grid of step
+    2^-9 over [-32, 32), rounded down and clamped."""
+    t = np.clip((np.asarray(z, np.float32) + np.float32(32.0)) * np.float32(512.0), 0.0, 32767.0)
     return np.floor(t).astype(np.int64)
 
 
@@ -303,7 +303,7 @@ def _bias_pattern(name, rng):
         return rng.normal(-2.0, 1.5, 1026)
     if name == "ties":                                # few distinct values: exact ties at the threshold
         return rng.choice(np.array([-3.0, -1.0, 0.5, 2.0]), 1026, p=[0.6, 0.3, 0.06, 0.04])
-    if name == "below_step":                          # distinct FP32 values within one 2^-10 key step
+    if name == "below_step":                          # distinct FP32 values within one 2^-9 key step
         return 1.0 + 2.0 ** -20 * rng.integers(0, 64, 1026) - 2.0 * (rng.random(1026) < 0.9)
     if name == "clamped":                             # beyond the key range: ties at its ends
         return np.where(rng.random(1026) < 0.1, 40.0 + rng.random(1026), -40.0 - rng.random(1026))
@@ -314,7 +314,7 @@ def _bias_pattern(name, rng):
 def test_fused_selection_exact_on_bias_logits(rl, pattern):
     """With a zero head matrix every block's logits are the head biases
     exactly, so the fused head's shortlist must be the 64 largest biases by
-    their 16-bit keys (fixed-point step 2^-10 over [-32, 32)), ties to the
+    their 15-bit keys (fixed-point step 2^-9 over [-32, 32)), ties to the
     lower index, in increasing index order, on every block; the iteration
     output is the bias of row 1024 exactly, and the gate the sigmoid of the
     bias of row 1025."""
@@ -332,7 +332,7 @@ def test_fused_selection_exact_on_bias_logits(rl, pattern):
     idx, missing, nu_frac = rl.shortlist_view(plan.propose(net, lr), nb)
     plan.check()
     b32 = b.astype(np.float32)
-    k = _key16(b32[:1024])
+    k = _key15(b32[:1024])
     order = np.lexsort((np.arange(1024), -k))         # key descending, then index ascending
     want = np.sort(order[:64])
     assert np.array_equal(idx.astype(np.int64), np.broadcast_to(want, (nb, 64)))
