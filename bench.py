@@ -442,11 +442,13 @@ def run_learned(args):
                     "max_abs_vs_plain": float((self.hr - self.hr_plain).abs().max()),
                     "mean_nu_hat": float(nu_hat.mean()) if nu_hat is not None else float(nu_max)}
 
-    # validation images (seeds apart from the training, held-out and test images)
+    # validation images: the test image's recipe (sinusoids, edges, tile) at a
+    # smaller size, with seeds apart from the training, held-out and test images
+    cfg = synth.workload_config("rljsde_4096x3072_t4")
     vals = []
     for i in range(2):
         vm = np.ascontiguousarray(np.tile(mask[:4, :4], (192, 256)))          # 768 x 1024 L-pixels
-        fv = synth.image(1536, 2048, 1024, 128, 7100 + i)
+        fv = synth.image(1536, 2048, cfg["n_sin"], cfg["n_edges"], 7100 + i)
         vals.append(Image(fv, vm, synth.measure(fv, vm).astype(np.float32)))
     for v in vals:
         v.run_plain(nu_max, 1)
@@ -464,16 +466,19 @@ def run_learned(args):
                "val_psnr_delta_db": float(np.max([q["psnr_delta_db"] for q in pts])),
                "val_mean_nu_hat": float(np.mean([q["mean_nu_hat"] for q in pts]))}
         sweep.append(ent)
-        if ent["val_psnr_delta_db"] <= 0.05 and (best is None or ent["val_mp_per_s"] > best[0]["val_mp_per_s"]):
+        # the fastest within 0.05 dB on validation; while none is, the smallest loss
+        def better(e, cur):
+            ok_e, ok_c = e["val_psnr_delta_db"] <= 0.05, cur["val_psnr_delta_db"] <= 0.05
+            if ok_e != ok_c:
+                return ok_e
+            return e["val_mp_per_s"] > cur["val_mp_per_s"] if ok_e else e["val_psnr_delta_db"] < cur["val_psnr_delta_db"]
+        if best is None or better(ent, best[0]):
             if best is not None:
                 best[1].close()
             best = (ent, net)
         else:
             net.close()
     del data, x, blocks, targets, tails, mass
-    if best is None:                                  # no threshold kept the PSNR: the most conservative one
-        best = (sweep[0], rljsde.Net(seed=5))
-        proposal.train(best[1], held, epochs=1, lr=args.lr)
     eps, net = best[0]["eps"], best[1]
     rec = proposal.recall(net, held)
 
@@ -499,7 +504,10 @@ def run_learned(args):
             "train": {"images": args.train_images, "samples": args.train_images * args.blocks_per_image,
                       "image_size": 512, "epochs": args.epochs, "data_s": t_data,
                       "heldout_recall_at_64": rec, "eps_chosen_on_validation": eps, "eps_sweep": sweep,
-                      "validation": "two 2048x1536 images (seeds 7100, 7101), the test image's 4x4 tile"},
+                      "eps_rule": "fastest learned path within 0.05 dB of the plain loop at nu_max on validation; "
+                                  "if none is, the smallest validation loss",
+                      "validation": "two 2048x1536 images of the test image's recipe (seeds 7100, 7101), its 4x4 tile",
+                      "validation_plain_psnr": [v.plain[nu_max]["psnr"] for v in vals]},
             "plain_nu_max": plain_full, "plain_uniform_nu": plain_pts,
             "learned": learned, "learned_nu_max_iterations": fixed_nu,
             "best_plain_within_0.05dB": best_plain, "smallest_uniform_nu_within_0.05dB": smallest_ok["nu"],

@@ -712,7 +712,8 @@ constexpr uint32_t kABytes = (kM / 8) * kSBO;                           // 73,72
 constexpr uint32_t kBChunkBytes = (kNC / 8) * kSBO;                     // 18,432
 constexpr uint32_t kBExtraBytes = 2 * kSBO;                             // 9,216: 16 rows
 constexpr uint32_t kPackedBytes = kChunks * kBChunkBytes + kBExtraBytes; // 599,040
-constexpr int kSlots = 4;
+constexpr int kSlots = 6;                                 // weight ring: shared-memory slots
+constexpr int kAhead = kSlots - 2;                        // chunks loaded ahead of the one multiplied
 constexpr int kBias = 1040;
 constexpr uint32_t kOffB = kABytes;
 constexpr uint32_t kOffKeys = kOffB + kSlots * kBChunkBytes;
@@ -1126,7 +1127,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
         long long loaded = 0, waited = 0, g = 0, it = 0;
         bool ok = true;
         if (n_tiles > blockIdx.x) {
-            for (; loaded < 2; ++loaded)
+            for (; loaded < kAhead; ++loaded)
                 bulk_load(b_addr + (uint32_t)(loaded % kSlots) * kBChunkBytes, chunk_src(loaded), chunk_bytes(loaded),
                           bar(kBarBFull + (int)(loaded % kSlots)));
         }
@@ -1134,8 +1135,9 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
             if (!wait(bar(kBarAFull), (uint32_t)(it & 1), abort)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int c = 0; c < kChunksPerTile; ++c, ++g) {
-                // keep two chunks in flight: chunk g + 2 goes into the slot of chunk g - 2
-                const long long h = g + 2;
+                // keep kAhead chunks in flight: chunk g + kAhead goes into the slot
+                // of chunk g - 2, whose multiply has had a whole chunk's time to finish
+                const long long h = g + kAhead;
                 if (h >= kSlots &&
                     !wait(bar(kBarBEmpty + (int)(h % kSlots)), (uint32_t)(((h - kSlots) / kSlots) & 1), abort)) {
                     ok = false;
