@@ -680,9 +680,10 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in
 //     15-bit ranking key per candidate: the logit on a fixed-point grid of
 //     step 2^-9 over [-32, 32).  Two keys share a 32-bit word; most go back
 //     into tensor memory (columns 0..447), four chunks' into shared memory.
-// Once a tile's logits are in, each block's 64th largest key is found by
-// bisection over the key bits, starting from the bracket given by the
-// chunks' second-largest keys; the two warps of a lane quadrant count one
+// Once a tile's logits are in, each block's 64th largest key is found by a
+// safeguarded interpolation search over the key range, starting from the
+// bracket given by the chunks' second-largest keys; the two warps of a lane
+// quadrant count one
 // half of the candidates each (eight packed keys per popc) and add their
 // counts through shared memory.  The candidates above it plus, of those
 // equal to it, the lowest indices form the shortlist.  The 1024 x 4-byte
@@ -722,7 +723,7 @@ constexpr uint32_t kOffX = kOffBias + kBias * 4;                        // consu
 constexpr uint32_t kOffBar = kOffX + 8 * 2 * kM * 4;
 // barriers: a_full, a_free, b_full[4], b_empty[4], acc_full[2], acc_empty[2]
 constexpr int kBarAFull = 0, kBarAFree = 1, kBarBFull = 2, kBarBEmpty = 2 + kSlots, kBarAccFull = 2 + 2 * kSlots,
-              kBarAccEmpty = kBarAccFull + 2, kNumBars = kBarAccEmpty + 2;
+              kBarAccEmpty = kBarAccFull + 2, kBarPair = kBarAccEmpty + 2, kNumBars = kBarPair + 4;
 constexpr uint32_t kOffMisc = kOffBar + kNumBars * 8;     // tensor-memory address, abort flag
 constexpr uint32_t kSmem = kOffMisc + 16;
 static_assert(kSmem <= 227 * 1024, "fused head operands must fit in shared memory");
@@ -825,10 +826,6 @@ __device__ __forceinline__ uint32_t key15(float z)
     return __float2uint_rd(t);
 }
 
-__device__ __forceinline__ void pair_sync(int quadrant)
-{
-    asm volatile("bar.sync %0, 64;" ::"r"(1 + quadrant) : "memory");
-}
 
 // Sum over 8 key words of the halves >= cand.  Every half holds key | 0x8000,
 // so w - (cand | cand << 16) borrows in neither half (cand < 0x8000) and
@@ -892,7 +889,7 @@ __device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *sk
 // tensor-memory columns 224 s .. 224 s + 223 (chunks 16 s .. 16 s + 13) and
 // shared-memory words 32 s .. 32 s + 31 of the block's row (the last two
 // chunks of the half).  The two warps of a quadrant add their counts through
-// shared memory and a named barrier, so both take the same bisection steps.
+// shared memory and an mbarrier with a bounded wait, so both take the same search steps.
 __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfloat16 *a3, int nbh, int nbw,
                                                                   const unsigned char *packed, const float *bias,
                                                                   Shortlist *out, int *status)
@@ -911,7 +908,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
     for (int i = tid; i < kBias; i += blockDim.x) bias_s[i] = i < kOut ? bias[i] : 0.f;
     if (tid == 0) {
         for (int i = 0; i < kNumBars; ++i) {
-            const uint32_t count = i == kBarAFull ? kGatherers : i >= kBarAccEmpty ? kSet : 1u;
+            const uint32_t count = i == kBarAFull ? kGatherers : i >= kBarPair ? 64u : i >= kBarAccEmpty ? kSet : 1u;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(count) : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -937,6 +934,16 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
         const int r = 32 * q + lane;
         uint32_t *srow = skeys_all + r * kSmemKeyStride;
         auto X = [&](int slot, int s) -> uint32_t & { return xch[(slot * 2 + s) * kM + r]; };
+        // The two warps of a quadrant meet on an mbarrier (64 arrivals per
+        // phase) with a bounded wait, so a warp that leaves on a timeout makes
+        // its partner time out too instead of blocking it.
+        uint32_t pphase = 0;
+        auto pair_sync = [&]() -> bool {
+            arrive(bar(kBarPair + q));
+            const bool got = wait(bar(kBarPair + q), pphase, abort);
+            pphase ^= 1u;
+            return __all_sync(0xffffffffu, got);
+        };
         bool ok = true;
         long long it = 0;
         for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
@@ -993,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
             // the bracket from both sets' chunks: 64 keys >= lo, the 64th largest <= hi
             X(0, set) = lo;
             X(1, set) = hi;
-            pair_sync(q);
+            if (!pair_sync()) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             lo = min(X(0, 0), X(0, 1));
             hi = max(X(1, 0), X(1, 1));
@@ -1023,7 +1030,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                 }
                 const int slot = 2 + (step & 1);
                 X(slot, set) = count_half(tcol, shalf, x);
-                pair_sync(q);
+                if (!pair_sync()) { ok = false; break; }
                 const int c0 = (int)X(slot, 0), c = c0 + (int)X(slot, 1);
                 ++step;
                 if (active) {
@@ -1035,6 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                     else if (H == L + 1u) active = false;
                 }
             }
+            if (!ok) break;
             const uint32_t thr = L;
             // Exactly 64 keys >= thr: take them all, the lower half's first.
             // Otherwise thr is the 64th largest key: take the keys > thr, and of
@@ -1045,7 +1053,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                 const uint32_t g0 = count_half(tcol, shalf, thr);
                 X(4, set) = g1;
                 X(5, set) = g0;
-                pair_sync(q);
+                if (!pair_sync()) { ok = false; break; }
                 if (!exact && (cL < 0 || cH < 0)) {
                     cH0 = (int)X(4, 0); cH = cH0 + (int)X(4, 1);
                     cL0 = (int)X(5, 0); cL = cL0 + (int)X(5, 1);
@@ -1091,7 +1099,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
             }
             // every key of the tile is read before either set converts the next tile's chunks
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            pair_sync(q);
+            if (!pair_sync()) { ok = false; break; }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         if (!ok) *abort = 1;
@@ -1156,15 +1164,16 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + kAccCol + 32u * (uint32_t)ab;
                 const uint32_t id = idesc(c == kChunks ? 16 : kNC);
-                const uint32_t bs = b_addr + (uint32_t)slot * kBChunkBytes;
-#pragma unroll 1
-                for (int j = 0; j < kHeadIn / 16; ++j) {
-                    const uint64_t da = sdesc(a_addr + j * 2 * kLBO), db = sdesc(bs + j * 2 * kLBO);
+                // K step j starts 2 core matrices (256 bytes) further: +16 in the
+                // descriptors' address field (addr >> 4, 14 bits: no carry out)
+                const uint64_t da0 = sdesc(a_addr), db0 = sdesc(b_addr + (uint32_t)slot * kBChunkBytes);
+#pragma unroll
+                for (int j = 0; j < kHeadIn / 16; ++j)
                     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                                 ::"r"(d), "l"(da), "l"(db), "r"(id), "r"(j)
+                                 ::"r"(d), "l"(da0 + (uint64_t)(16 * j)), "l"(db0 + (uint64_t)(16 * j)), "r"(id),
+                                 "r"(j)
                                  : "memory");
-                }
                 commit(bar(kBarAccFull + ab));
                 commit(bar(kBarBEmpty + slot));
                 if (c == kChunks) commit(bar(kBarAFree));
