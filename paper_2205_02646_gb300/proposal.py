@@ -111,9 +111,13 @@ def make_dataset(n_images: int, size: int = 512, blocks_per_image: int = 256, nu
 
 
 def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None,
-          gate_weight: float = 1.0):
+          gate_weight: float = 10.0):
     """Adam with cosine decay over ``epochs`` passes of ``data`` (patches,
-    blocks, targets, iteration targets, shape, mass)."""
+    blocks, targets, iteration targets, shape, mass).  The share the gate
+    predicts varies little across blocks (standard deviation about 0.04
+    around 0.26 on generator images), so its squared error weighs 10: at 1
+    the gate learned a constant (rank correlation with the share -0.04 on
+    held-out patches), at 10 it ranks them (0.20), at 50 it saturated."""
     import torch
     x, blocks, targets, nu_t, shape, mass = data[:6]
     n = x.shape[0]
@@ -134,6 +138,27 @@ def train(net, data, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed:
         if log:
             log("epoch %d loss %.4f" % (e, float(np.mean(losses[-max(1, n // batch):]))))
     return losses
+
+
+def gate_rank_correlation(net, data, k: int = SHORTLIST):
+    """Spearman correlation, over the samples of ``data``, between the gate
+    (sigmoid of head row 1025) and the share of the sample's mass that falls
+    outside the network's own top-k logits, the quantity it is trained to
+    predict."""
+    import torch
+    x, blocks, targets, nu_t, shape, mass = data[:6]
+    gs, ss = [], []
+    for i in range(0, x.shape[0], 8192):
+        z = net.logits(x[i:i + 8192].contiguous(), blocks[i:i + 8192].contiguous(), shape)
+        top = torch.topk(z[:, :1024], k, dim=1).indices
+        inside = torch.zeros_like(mass[i:i + 8192], dtype=torch.bool)
+        inside.scatter_(1, top, True)
+        m = mass[i:i + 8192]
+        ss.append(((m * (~inside)).sum(1) / m.sum(1).clamp_min(1e-12)).cpu().numpy())
+        gs.append(torch.sigmoid(z[:, 1025]).cpu().numpy())
+    g, s = np.concatenate(gs), np.concatenate(ss)
+    rg, rs = np.argsort(np.argsort(g)), np.argsort(np.argsort(s))
+    return float(np.corrcoef(rg, rs)[0, 1])
 
 
 def recall(net, data, k: int = SHORTLIST):
