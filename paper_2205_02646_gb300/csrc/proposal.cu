@@ -668,26 +668,28 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in
 // ------------------------------------------ fused head and shortlist --
 // The head and the top-64 selection of the whole-image pass in one kernel on
 // the 5th-gen tensor cores.  Per tile of 128 consecutive blocks:
-//   - four gather warps read each block's 3x3 block-grid neighbourhood of
-//     conv3 (288 features, K index t * 32 + ci as in conv_tc_kernel), round
-//     it to bfloat16 and store it in shared memory as the A operand;
+//   - four gather warps copy each block's 3x3 block-grid neighbourhood of
+//     conv3 (288 bfloat16 features, K index t * 32 + ci as in conv_tc_kernel)
+//     into shared memory as the A operand;
 //   - one issuer thread streams the head weights (bfloat16, pre-packed in the
-//     core-matrix layout, 32 rows per chunk) through a ring of shared-memory
-//     slots with bulk copies and issues, per chunk, 18 tcgen05.mma (M 128,
-//     N 32, K 16) into one of two 32-column accumulators in tensor memory;
+//     core-matrix layout, 64 rows per chunk) through two shared-memory slots
+//     with bulk copies and issues, per chunk, 18 tcgen05.mma (M 128, N 64,
+//     K 16) into one of two 64-column accumulators in tensor memory (an
+//     M 128 MMA costs about the same whatever its N up to 64, so wider chunks
+//     mean fewer of them and fewer hand-overs);
 //   - eight consumer warps (two per tensor-memory lane quadrant, one block
 //     per lane) read each chunk's logits, add the bias, and keep only a
 //     15-bit ranking key per candidate: the logit on a fixed-point grid of
-//     step 2^-9 over [-32, 32).  Two keys share a 32-bit word; most go back
-//     into tensor memory (columns 0..447), four chunks' into shared memory.
+//     step 2^-9 over [-32, 32).  Two keys share a 32-bit word; twelve
+//     chunks' go back into tensor memory (columns 0..383), four chunks' into
+//     shared memory.
 // Once a tile's logits are in, each block's 64th largest key is found by a
 // safeguarded interpolation search over the key range, starting from the
-// bracket given by the chunks' second-largest keys; the two warps of a lane
-// quadrant count one
-// half of the candidates each (eight packed keys per popc) and add their
-// counts through shared memory.  The candidates above it plus, of those
-// equal to it, the lowest indices form the shortlist.  The 1024 x 4-byte
-// logits of a block never leave the SM.
+// bracket given by the second-largest keys of each group of 32 candidates;
+// the two warps of a lane quadrant count one half of the candidates each
+// (eight packed keys per popc) and add their counts through shared memory.
+// The candidates above it plus, of those equal to it, the lowest indices form
+// the shortlist.  The 1024 x 4-byte logits of a block never leave the SM.
 // The iteration output (head row 1024) and the gate (row 1025, whose sigmoid
 // is the predicted share of the plain loop's coefficient mass the shortlist
 // leaves out) are kept in FP32.
@@ -697,24 +699,24 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in
 // its copies and tensor-core work in flight before freeing tensor memory.
 namespace hd {
 constexpr int kM = 128;                                   // blocks per tile (MMA M, tensor-memory lanes)
-constexpr int kNC = 32;                                   // candidates per chunk (MMA N)
-constexpr int kChunks = 1024 / kNC;                       // 32 candidate chunks
+constexpr int kNC = 64;                                   // candidates per chunk (MMA N)
+constexpr int kChunks = 1024 / kNC;                       // 16 candidate chunks
 constexpr int kChunksPerTile = kChunks + 1;               // + head rows 1024..1039 (N = 16)
-constexpr int kKeyWords = kNC / 2;                        // 16 words of two 16-bit keys per chunk
-constexpr int kHalfTmemChunks = 14;                       // per half: chunks whose keys stay in tensor memory
-constexpr uint32_t kHalfTmemWords = kHalfTmemChunks * kKeyWords;   // 224
-constexpr uint32_t kAccCol = 2 * kHalfTmemWords;          // 448: accumulators at 448 and 480
+constexpr int kKeyWords = kNC / 2;                        // 32 words of two 16-bit keys per chunk
+constexpr int kHalfChunks = kChunks / 2;                  // 8 chunks (512 candidates) per half
+constexpr int kHalfTmemChunks = 6;                        // per half: chunks whose keys stay in tensor memory
+constexpr uint32_t kHalfTmemWords = kHalfTmemChunks * kKeyWords;   // 192
+constexpr uint32_t kAccCol = 2 * kHalfTmemWords;          // 384: accumulators at 384 and 448
 constexpr uint32_t kTmemCols = 512;
-constexpr int kHalfSmemWords = 2 * kKeyWords;             // per half: two chunks' keys in shared memory
-constexpr int kSmemKeyStride = 2 * kHalfSmemWords + 1;    // 65: rows start in distinct banks
+constexpr int kHalfSmemWords = (kHalfChunks - kHalfTmemChunks) * kKeyWords;   // per half: two chunks' keys, 64 words
+constexpr int kSmemKeyStride = 2 * kHalfSmemWords + 1;    // 129: rows start in distinct banks
 constexpr uint32_t kGuard = 0x80008000u;                  // bit 15 of both key halves
 constexpr uint32_t kLBO = 128, kSBO = (kHeadIn / 8) * 128;              // 4608
 constexpr uint32_t kABytes = (kM / 8) * kSBO;                           // 73,728
-constexpr uint32_t kBChunkBytes = (kNC / 8) * kSBO;                     // 18,432
+constexpr uint32_t kBChunkBytes = (kNC / 8) * kSBO;                     // 36,864
 constexpr uint32_t kBExtraBytes = 2 * kSBO;                             // 9,216: 16 rows
 constexpr uint32_t kPackedBytes = kChunks * kBChunkBytes + kBExtraBytes; // 599,040
-constexpr int kSlots = 6;                                 // weight ring: shared-memory slots
-constexpr int kAhead = kSlots - 2;                        // chunks loaded ahead of the one multiplied
+constexpr int kSlots = 2;                                 // weight ring: the chunk multiplied and the next
 constexpr int kBias = 1040;
 constexpr uint32_t kOffB = kABytes;
 constexpr uint32_t kOffKeys = kOffB + kSlots * kBChunkBytes;
@@ -806,13 +808,16 @@ __device__ __forceinline__ void ld2(uint32_t taddr, uint32_t &r0, uint32_t &r1)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16])
+__device__ __forceinline__ void st32(uint32_t taddr, const uint32_t (&r)[32])
 {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
                  ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+                 "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+                 "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
                  : "memory");
 }
+
 
 // 15-bit ranking key of a logit: z on a fixed-point grid of step 2^-9 over
 // [-32, 32), rounded down and clamped (NaN to 0), so keys order like the
@@ -845,9 +850,9 @@ __device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *sk
 {
     const uint32_t c2 = cand | (cand << 16);
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-    static_assert(kHalfTmemChunks / 2 == 7, "seven 32-column loads per half");
+    static_assert(kHalfTmemChunks % 2 == 0 && kHalfSmemWords == 64, "pairs of 32-column loads, 64 shared words");
 #pragma unroll 1
-    for (int i = 0; i < 6; i += 2) {              // two loads in flight
+    for (int i = 0; i < kHalfTmemChunks; i += 2) {   // two loads in flight
         uint32_t v[32], u[32];
         ld32_nw(tcol + 32 * i, v);
         ld32_nw(tcol + 32 * i + 32, u);
@@ -861,21 +866,16 @@ __device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *sk
         n2 += count8(u + 16, c2);
         n3 += count8(u + 24, c2);
     }
-    {
-        uint32_t v[32];
-        ld32(tcol + 32 * 6, v);
-        n0 += count8(v, c2);
-        n1 += count8(v + 8, c2);
-        n2 += count8(v + 16, c2);
-        n3 += count8(v + 24, c2);
-    }
-    uint32_t s[32];
 #pragma unroll
-    for (int j = 0; j < kHalfSmemWords; ++j) s[j] = skeys[j];
-    n0 += count8(s, c2);
-    n1 += count8(s + 8, c2);
-    n2 += count8(s + 16, c2);
-    n3 += count8(s + 24, c2);
+    for (int h = 0; h < 2; ++h) {
+        uint32_t t[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) t[j] = skeys[32 * h + j];
+        n0 += count8(t, c2);
+        n1 += count8(t + 8, c2);
+        n2 += count8(t + 16, c2);
+        n3 += count8(t + 24, c2);
+    }
     return (n0 + n1) + (n2 + n3);
 }
 
@@ -886,10 +886,11 @@ __device__ __forceinline__ uint32_t count_half(uint32_t tcol, const uint32_t *sk
 // blocks 32 q .. 32 q + 31 of a tile) and belongs to set s = w / 4.  Set s
 // converts the chunks that land in accumulator s (every other chunk), and
 // owns candidates 512 s .. 512 s + 511 for the selection: their keys sit in
-// tensor-memory columns 224 s .. 224 s + 223 (chunks 16 s .. 16 s + 13) and
-// shared-memory words 32 s .. 32 s + 31 of the block's row (the last two
+// tensor-memory columns 192 s .. 192 s + 191 (chunks 8 s .. 8 s + 5) and
+// shared-memory words 64 s .. 64 s + 63 of the block's row (the last two
 // chunks of the half).  The two warps of a quadrant add their counts through
-// shared memory and an mbarrier with a bounded wait, so both take the same search steps.
+// shared memory and an mbarrier with a bounded wait, so both take the same
+// search steps.
 __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfloat16 *a3, int nbh, int nbw,
                                                                   const unsigned char *packed, const float *bias,
                                                                   Shortlist *out, int *status)
@@ -956,9 +957,10 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                 const bool got = wait(bar(kBarAccFull + set), (uint32_t)((g >> 1) & 1), abort);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = trow + kAccCol + (uint32_t)(kNC * set);
                 if (c == kChunks) {
                     uint32_t v0, v1;
-                    ld2(trow + kAccCol + 32 * set, v0, v1);
+                    ld2(acc, v0, v1);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     arrive(bar(kBarAccEmpty + set));
                     if (valid) {
@@ -967,29 +969,33 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                     }
                     continue;
                 }
-                uint32_t v[32];
-                ld32(trow + kAccCol + 32 * set, v);
+                uint32_t v[32], u[32];
+                ld32_nw(acc, v);
+                ld32_nw(acc + 32, u);
+                wait_ld();
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 arrive(bar(kBarAccEmpty + set));
-                uint32_t pk[16], m1 = 0, m2 = 0;
+                // word j: the keys of candidates 64 c + j (low half) and 64 c + 32 + j
+                // (high half); second-largest keys per group of 32 for the bracket
+                uint32_t pk[32], a1 = 0, a2 = 0, b1 = 0, b2 = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const uint32_t k = key15(__uint_as_float(v[j]) + bias_s[kNC * c + j]);
-                    m2 = max(m2, min(m1, k));
-                    m1 = max(m1, k);
-                    if (j < 16) pk[j] = k;
-                    else pk[j - 16] |= k << 16;
+                    const uint32_t ka = key15(__uint_as_float(v[j]) + bias_s[kNC * c + j]);
+                    const uint32_t kb = key15(__uint_as_float(u[j]) + bias_s[kNC * c + 32 + j]);
+                    a2 = max(a2, min(a1, ka));
+                    a1 = max(a1, ka);
+                    b2 = max(b2, min(b1, kb));
+                    b1 = max(b1, kb);
+                    pk[j] = ka | (kb << 16) | kGuard;
                 }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) pk[j] |= kGuard;
-                lo = min(lo, m2);
-                hi = max(hi, m2);
-                const int h = c >> 4, cq = c & 15;
+                lo = min(lo, min(a2, b2));
+                hi = max(hi, max(a2, b2));
+                const int h = c / kHalfChunks, cq = c % kHalfChunks;
                 if (cq < kHalfTmemChunks) {
-                    st16(trow + kHalfTmemWords * h + kKeyWords * cq, pk);
+                    st32(trow + kHalfTmemWords * h + kKeyWords * cq, pk);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) srow[kHalfSmemWords * h + kKeyWords * (cq - kHalfTmemChunks) + j] = pk[j];
+                    for (int j = 0; j < 32; ++j) srow[kHalfSmemWords * h + kKeyWords * (cq - kHalfTmemChunks) + j] = pk[j];
                 }
             }
             if (!ok) break;
@@ -1080,22 +1086,19 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
             };
             const int base = 512 * set;
 #pragma unroll 1
-            for (int i = 0; i < kHalfTmemChunks / 2; ++i) {
+            for (int i = 0; i < kHalfTmemChunks; ++i) {
                 uint32_t v[32];
                 ld32(tcol + 32 * i, v);
 #pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {      // chunk 2i + hh of the half: words 16 hh .. 16 hh + 15
+                for (int j = 0; j < 32; ++j) take(v[j] & 0x7FFFu, base + kNC * i + j);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) take(v[16 * hh + j] & 0x7FFFu, base + 64 * i + 32 * hh + j);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) take((v[16 * hh + j] >> 16) & 0x7FFFu, base + 64 * i + 32 * hh + 16 + j);
-                }
+                for (int j = 0; j < 32; ++j) take((v[j] >> 16) & 0x7FFFu, base + kNC * i + 32 + j);
             }
 #pragma unroll 1
-            for (int cq = kHalfTmemChunks; cq < 16; ++cq) {
+            for (int cq = kHalfTmemChunks; cq < kHalfChunks; ++cq) {
                 const uint32_t *w = shalf + kKeyWords * (cq - kHalfTmemChunks);
-                for (int j = 0; j < 16; ++j) take(w[j] & 0x7FFFu, base + kNC * cq + j);
-                for (int j = 0; j < 16; ++j) take((w[j] >> 16) & 0x7FFFu, base + kNC * cq + 16 + j);
+                for (int j = 0; j < 32; ++j) take(w[j] & 0x7FFFu, base + kNC * cq + j);
+                for (int j = 0; j < 32; ++j) take((w[j] >> 16) & 0x7FFFu, base + kNC * cq + 32 + j);
             }
             // every key of the tile is read before either set converts the next tile's chunks
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1135,25 +1138,13 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
         long long loaded = 0, waited = 0, g = 0, it = 0;
         bool ok = true;
         if (n_tiles > blockIdx.x) {
-            for (; loaded < kAhead; ++loaded)
-                bulk_load(b_addr + (uint32_t)(loaded % kSlots) * kBChunkBytes, chunk_src(loaded), chunk_bytes(loaded),
-                          bar(kBarBFull + (int)(loaded % kSlots)));
+            bulk_load(b_addr, chunk_src(0), chunk_bytes(0), bar(kBarBFull));
+            loaded = 1;
         }
         for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
             if (!wait(bar(kBarAFull), (uint32_t)(it & 1), abort)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int c = 0; c < kChunksPerTile; ++c, ++g) {
-                // keep kAhead chunks in flight: chunk g + kAhead goes into the slot
-                // of chunk g - 2, whose multiply has had a whole chunk's time to finish
-                const long long h = g + kAhead;
-                if (h >= kSlots &&
-                    !wait(bar(kBarBEmpty + (int)(h % kSlots)), (uint32_t)(((h - kSlots) / kSlots) & 1), abort)) {
-                    ok = false;
-                    break;
-                }
-                bulk_load(b_addr + (uint32_t)(h % kSlots) * kBChunkBytes, chunk_src(h), chunk_bytes(h),
-                          bar(kBarBFull + (int)(h % kSlots)));
-                loaded = h + 1;
                 const int slot = (int)(g % kSlots), ab = (int)(g & 1);
                 if (!wait(bar(kBarBFull + slot), (uint32_t)((g / kSlots) & 1), abort)) { ok = false; break; }
                 waited = g + 1;
@@ -1162,7 +1153,7 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t d = tmem + kAccCol + 32u * (uint32_t)ab;
+                const uint32_t d = tmem + kAccCol + (uint32_t)(kNC * ab);
                 const uint32_t id = idesc(c == kChunks ? 16 : kNC);
                 // K step j starts 2 core matrices (256 bytes) further: +16 in the
                 // descriptors' address field (addr >> 4, 14 bits: no carry out)
@@ -1177,6 +1168,18 @@ __global__ void __launch_bounds__(kThreads, 1) head_select_kernel(const __nv_bfl
                 commit(bar(kBarAccFull + ab));
                 commit(bar(kBarBEmpty + slot));
                 if (c == kChunks) commit(bar(kBarAFree));
+                // the next chunk goes into the other slot once the previous chunk's
+                // multiply is done with it; it lands while this chunk multiplies
+                const long long h = g + 1;
+                if (h >= kSlots &&
+                    !wait(bar(kBarBEmpty + (int)(h % kSlots)), (uint32_t)(((h - kSlots) / kSlots) & 1), abort)) {
+                    ok = false;
+                    ++g;
+                    break;
+                }
+                bulk_load(b_addr + (uint32_t)(h % kSlots) * kBChunkBytes, chunk_src(h), chunk_bytes(h),
+                          bar(kBarBFull + (int)(h % kSlots)));
+                loaded = h + 1;
             }
         }
         if (!ok) *abort = 1;
