@@ -33,8 +33,32 @@ DEFAULT_WORKLOAD = "rljsde_4096x3072"
 REFERENCE_BAND_BLOCKS = 16384      # blocks per step of the reference arm (a few seconds of oracle time)
 
 
+def algorithmic_flops_per_block(nu: int) -> int:
+    """The method's work per 4x4 block as the paper states it (Sec. IV): the
+    dense initial projection 4 L_w K (L_w = 256 window L-pixels, K = 1024),
+    13 K flops per iteration (|R|^2 3, times q/D 1, compare 1, the complex
+    multiply-add of Eq. 17 8) and 64 for the synthesis of Eq. 18.  The
+    roofline's numerator: independent of how the library computes it."""
+    return 4 * 256 * 1024 + 13 * 1024 * nu + 64 * nu
+
+
+def algorithmic_phase_flops(nu: int):
+    """(initial projection + first iteration, the nu - 1 later iterations) of
+    algorithmic_flops_per_block."""
+    return 4 * 256 * 1024 + 13 * 1024 + 64, (nu - 1) * (13 * 1024 + 64)
+
+
+def stored_flops_per_block(nu: int) -> int:
+    """Arithmetic the stored-C loop executes per block: the factored initial
+    projection (as below), its transform to R once, scores 4 flops per
+    candidate and iteration, and the update of Eq. 17 with the stored column,
+    8 flops per candidate and later iteration."""
+    dft = 256 * (7 * 4 + 2 * 1) + 4 * 16 * (56 + 56 + 42) + 4 * 256 * 2
+    return dft + 256 * 46 + nu * 1024 * 4 + (nu - 1) * 1024 * 8 + 64 * nu
+
+
 def flops_per_block(nu: int) -> int:
-    """Arithmetic of the factored RL-JSDE path per 4x4 block (FMA = 2 flops,
+    """Arithmetic the factored loop executes per 4x4 block (FMA = 2 flops,
     multiplications by structural zeros not counted)."""
     # row DFTs of the real window, Hermitian half only (k2 = 1..7 complex,
     # k2 = 0 and 8 real); column DFTs as 8-point FFTs per parity half (56
@@ -44,13 +68,6 @@ def flops_per_block(nu: int) -> int:
     per_iter = 256 * 94                                       # update 32 + transform 46 + scores 16 per kappa
     scalar = 64                                               # delta, h_t(uv), g_t, synthesis
     return dft + first + (nu - 1) * per_iter + nu * scalar
-
-
-def phase_flops(nu: int):
-    """(initial projection + first iteration, the nu - 1 later iterations)
-    of flops_per_block."""
-    dft = 256 * (7 * 4 + 2 * 1) + 4 * 16 * (56 + 56 + 42) + 4 * 256 * 2
-    return dft + 256 * 62 + 64, (nu - 1) * (256 * 94 + 64)
 
 
 def fp32_nominal_tflops() -> float:
@@ -283,7 +300,7 @@ def run_batch(args, rank, world):
     stream.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     info = plan.info()
-    flops = flops_per_block(args.nu_max) * info["n_blocks"]
+    flops = algorithmic_flops_per_block(args.nu_max) * info["n_blocks"]
     achieved = flops / (total_ms / args.steps / 1e3) / 1e12
     pk = fp32_peak(rljsde, stream, 0)
     peak = pk["tflops"]
@@ -301,7 +318,11 @@ def run_batch(args, rank, world):
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "peak_basis": pk["basis"],
-                     "peak_nominal": fp32_nominal_tflops()},
+                     "peak_nominal": fp32_nominal_tflops(),
+                     "flops_per_block": algorithmic_flops_per_block(args.nu_max),
+                     "flops_basis": "algorithmic (dense initial projection 4 L_w K, 13 K per iteration, "
+                                    "64 per iteration of synthesis)",
+                     "stored_c_blocks_frac": info["n_stored_c_blocks"] / info["n_blocks"]},
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -643,6 +664,71 @@ def run_pairs(args):
     print(json.dumps(out), flush=True)
 
 
+def run_c_supply(args):
+    """Where the loop's Gram column comes from (params.c_supply): the factored
+    form rebuilt from 16 KB of tables per local matrix, the paper's stored C
+    (Table I: 8 MiB per local matrix, one 8 KiB column read per block and
+    iteration) for every table set, and the automatic choice (stored for the
+    much-used table sets only), by default on the 1024x1024 workload and the
+    4096x3072 one (144 local matrices), L2 flushed before every timed launch;
+    plan-creation times, the outputs' agreement between the two uniform
+    supplies and the measured L2 read rate."""
+    import torch
+    from paper_2205_02646_gb300 import build, rljsde, synth
+    build.build()
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"study": "c-supply", "nu_max": args.nu_max, "points": []}
+    clocks = Clocks(0)
+    clocks.start()
+    for wl in args.study_workloads:
+        f, mask, y = synth.workload(wl)
+        lr = torch.from_numpy(y).cuda()
+        hrs = {}
+        for supply in (2, 1, 0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan = rljsde.Plan(mask, rljsde.default_params(nu_max=args.nu_max, c_supply=supply))
+            torch.cuda.synchronize()
+            plan_s = time.perf_counter() - t0
+            hr = torch.empty((2 * mask.shape[0], 2 * mask.shape[1]), device="cuda")
+            plan.reconstruct(lr, hr)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                plan.reconstruct(lr, hr)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            plan.check()
+            info = plan.info()
+            ms = float(np.median(times))
+            nb = info["n_blocks"]
+            pt = {"workload": wl, "c_supply": {0: "auto", 1: "stored", 2: "factored"}[supply], "ms": ms,
+                  "mp_per_s": 4 * mask.size / 1e6 / (ms / 1e3), "tables": info["n_tables"],
+                  "stored_tables": info["n_stored_c_tables"], "stored_blocks": info["n_stored_c_blocks"],
+                  "device_c_bytes": info["device_c_bytes"], "plan_s": plan_s,
+                  "launch": [info["warps_per_cta"], info["ctas_per_sm"]]}
+            if info["n_stored_c_blocks"]:
+                col = info["n_stored_c_blocks"] * (args.nu_max - 1) * 8192
+                pt["column_bytes_per_launch"] = col
+                pt["column_read_gbs"] = col / (ms / 1e3) / 1e9
+            out["points"].append(pt)
+            hrs[supply] = hr.cpu().numpy()
+            del plan
+        d = np.abs(hrs[1].astype(np.float64) - hrs[2])
+        blk = d.reshape(mask.shape[0] // 2, 4, mask.shape[1] // 2, 4).max(axis=(1, 3))
+        out["points"][-2]["vs_factored"] = {"max_abs": float(d.max()),
+                                            "blocks_above_1e-4": int((blk > 1e-4).sum()),
+                                            "blocks": int(blk.size)}
+    out["clocks"] = clocks.stop()
+    out["l2_read_peak_gbs"] = rljsde.l2_read_peak(reps=5)["gbs"]
+    print(json.dumps(out), flush=True)
+
+
 def run_cpu_baseline(args):
     """The FP64 oracle on the host cores, as it stands: the recurrent CPU
     form over every block of the 1024x1024 image (tables once per local mask,
@@ -708,7 +794,9 @@ def main():
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--study", default=None,
                     choices=[None, "precision", "learned-launch", "random-mask", "layouts", "pairs",
-                             "cpu-baseline"])
+                             "cpu-baseline", "c-supply"])
+    ap.add_argument("--study-workloads", nargs="+", default=["rljsde_1024x1024", "rljsde_4096x3072"],
+                    help="workloads of --study c-supply")
     ap.add_argument("--train-images", type=int, default=20000)
     ap.add_argument("--blocks-per-image", type=int, default=32)
     ap.add_argument("--epochs", type=int, default=6)
@@ -741,6 +829,9 @@ def main():
         return
     if args.study == "cpu-baseline":
         run_cpu_baseline(args)
+        return
+    if args.study == "c-supply":
+        run_c_supply(args)
         return
     if args.workload == "rljsde_learned":
         run_learned(args)
@@ -835,11 +926,22 @@ def main():
     e2e_val = world * mp_per_step * args.steps / (e2e_ms / 1e3)
 
     n_blocks = info["n_blocks"]
-    flops = flops_per_block(args.nu_max) * n_blocks
+    flops = algorithmic_flops_per_block(args.nu_max) * n_blocks
     mean_s = total_ms / args.steps / 1e3
     achieved = flops / mean_s / 1e12
     pk = fp32_peak(rljsde, stream, dev.index)
     peak = pk["tflops"]
+    # the flops the kernels execute (stored-C blocks and factored blocks)
+    n_st = info["n_stored_c_blocks"]
+    executed = (stored_flops_per_block(args.nu_max) * n_st + flops_per_block(args.nu_max) * (n_blocks - n_st))
+    # the stored-C loop's Gram-column reads against the measured L2 read rate
+    l2 = None
+    if n_st:
+        l2pk = rljsde.l2_read_peak(reps=5, stream=stream)
+        col = n_st * (args.nu_max - 1) * 8192
+        l2 = {"column_bytes_per_launch": col, "achieved_gbs": col / mean_s / 1e9, "peak_gbs": l2pk["gbs"],
+              "frac": col / mean_s / 1e9 / l2pk["gbs"],
+              "peak_basis": "measured in this run: rljsde_l2_read_peak (32 MiB L2-resident buffer, every SM)"}
 
     # Per-phase split (outside the timed region): the same image with one
     # iteration per block times the initial projection and first iteration;
@@ -858,7 +960,7 @@ def main():
         t1 += a_.elapsed_time(b_) / 5
     plan1.check(stream)
     plan1.close()
-    f_init, f_loop = phase_flops(args.nu_max)
+    f_init, f_loop = algorithmic_phase_flops(args.nu_max)
     t_loop = max(total_ms / args.steps - t1, 1e-6)
     phases = {"init": {"ms": t1, "tflops": f_init * n_blocks / (t1 / 1e3) / 1e12},
               "loop": {"ms": t_loop, "tflops": f_loop * n_blocks / (t_loop / 1e3) / 1e12}}
@@ -893,6 +995,9 @@ def main():
                    "gamma_odc": params.gamma_odc, "rho_decay": params.rho_decay, "q": "default",
                    "mask_tile_lr": synth.workload_config(args.workload)["tile"], "tables": info["n_tables"],
                    "blocks": n_blocks, "launch": [info["grid"], info["warps_per_cta"]],
+                   "c_supply": "auto: stored for %d of %d table sets (%d of %d blocks, %.2f GB), factored for "
+                               "the rest" % (info["n_stored_c_tables"], info["n_tables"], n_st, n_blocks,
+                                             info["device_c_bytes"] / 1e9),
                    "l2": "flushed between steps", "parallelism": "independent images per GPU"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(lr_host.numel() * 4),
                 "d2h_bytes_per_step": int(hr_host.numel() * 4)},
@@ -901,7 +1006,11 @@ def main():
                      "frac": achieved / peak, "traffic": kernel_traffic(args.workload),
                      "peak_basis": pk["basis"], "peak_sm_mhz": pk["clocks"].get("sm_mhz"),
                      "peak_nominal": fp32_nominal_tflops(), "frac_of_nominal": achieved / fp32_nominal_tflops(),
-                     "flops_per_block": flops_per_block(args.nu_max), "phases": phases},
+                     "flops_per_block": algorithmic_flops_per_block(args.nu_max),
+                     "flops_basis": "algorithmic (dense initial projection 4 L_w K, 13 K per iteration, "
+                                    "64 per iteration of synthesis)",
+                     "executed_tflops": executed / mean_s / 1e12, "executed_frac": executed / mean_s / 1e12 / peak,
+                     "phases": phases, "l2_columns": l2},
         "clocks": clk,
     }
     if near is not None:

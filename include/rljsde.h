@@ -100,6 +100,25 @@ typedef struct {
                              and each selection adds gamma delta to c_k and its
                              conjugate to c_-k (once if k = -k), so model and
                              residual stay real.  Not with the learned proposal */
+    int c_supply;         /* where the loop's Gram column C_{k,uv} of Eq. 17 comes
+                             from, per table set (distinct local matrix):
+                             1 = stored, the paper's recurrent form (Table I):
+                             the whole C of Eq. 14, built in FP64 on the device
+                             and stored FP32 (8 MiB per table set), one 8 KiB
+                             column read per block and iteration; 2 = factored,
+                             rebuilt every iteration from 16 KB of tables with
+                             no memory traffic; 0 = auto (default): stored for
+                             each table set at least 256 blocks use, the most
+                             used first, while the matrices fit in an eighth of
+                             the free device memory, factored for the others
+                             and for FP64 loops and paths 2 and 3.  1 needs the
+                             FP32 loop on path 1 (RLJSDE_ERR_UNSUPPORTED
+                             otherwise, also when auto would choose path 2 or
+                             3) and fails with RLJSDE_ERR_OUT_OF_MEMORY when the
+                             matrices do not fit.  Stored C runs with 4 warps
+                             per CTA only (rljsde_set_launch with 8 warps:
+                             RLJSDE_ERR_UNSUPPORTED).  The learned proposal's
+                             loops always use the factored form                 */
 } rljsde_params;
 
 /* Fill *p with the defaults above.  Returns RLJSDE_ERR_INVALID_ARG on NULL. */
@@ -311,6 +330,19 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
  */
 int rljsde_fp32_peak(int reps, void *stream, double *tflops_out, float *ms_out);
 
+/*
+ * Measurement helper (this library's).  The stored-C loop (c_supply) reads
+ * one 8 KiB Gram column per block and iteration (Eq. 17 with C stored, Table
+ * I), mostly from the L2; this times the L2 read bandwidth: every SM reads a
+ * 32 MiB buffer (resident in the L2 after a warm-up launch) 128 times with
+ * 16-byte non-coherent loads, reps timed launches (reps 1..1000) with CUDA
+ * events on `stream`.  *gbs_out gets the best rate in GB/s, *ms_out (may be
+ * NULL) that launch's duration.  Synchronous; allocates and frees 32 MiB of
+ * device memory.  Errors: RLJSDE_ERR_INVALID_ARG, RLJSDE_ERR_OUT_OF_MEMORY,
+ * RLJSDE_ERR_CUDA.
+ */
+int rljsde_l2_read_peak(int reps, void *stream, double *gbs_out, float *ms_out);
+
 typedef struct {
     int n_images;
     int n_blocks;           /* target blocks over all images                  */
@@ -324,6 +356,9 @@ typedef struct {
     int64_t paper_D_bytes;        /* n_tables x 1024 x 8 B                    */
     int path;                     /* path in effect: 1, 2 or 3 (rljsde_params) */
     int n_apertures;              /* distinct non-empty apertures in the masks  */
+    int n_stored_c_tables;        /* table sets whose C is stored (c_supply)     */
+    int n_stored_c_blocks;        /* blocks that use them                       */
+    int64_t device_c_bytes;       /* their stored C on the device               */
 } rljsde_plan_info_t;
 
 int rljsde_plan_info(const rljsde_plan_t *plan, rljsde_plan_info_t *out);

@@ -128,6 +128,8 @@ struct Args {
     const unsigned char *records;
     uint32_t record_bytes;
     const unsigned char *records_short;    // RecordShortF32 per table (shortlist loop)
+    const float4 *cstore;                  // stored Gram matrices (c_supply), kStoredCBytes each
+    const int *cslot;                      // per table set: its stored matrix, or -1 (factored)
     const Consts *consts;
     ImageDesc single;          // used when descs == nullptr
     const ImageDesc *descs;
@@ -576,6 +578,74 @@ __device__ __forceinline__ CP rot(float2 c, float2 s, float2 ns, CP z)
 }
 __device__ __forceinline__ float2 energy(float2 q, CP r) { return mul2(q, fma2(r.im, r.im, mul2(r.re, r.re))); }
 
+// R_k at the lane's 16 candidates of frequency pair jj from the factored
+// state Yj (R_k = sum_t conj(h_t(k)) Y_t(k mod 16)): per sub-pixel s the sum
+// Z_s of Y_t over the slots holding it (three-quarter: S - Y_s), then a 2x2
+// butterfly over the sub-pixel phases.  R[2a + b] holds k = (kap1 + 16a,
+// kap2 + 16b) for kap1 = 8h + 2jj (low half of each f32x2) and kap1 + 1
+// (high half).
+template <int LAY>
+__device__ __forceinline__ void state_to_R(const Args &a, const CP (&Yj)[4], const int h, const int jj,
+                                           const int k2, const float2 e1c, const float2 e1s, const float2 e1n,
+                                           const PairTables &pt, CP (&R)[4])
+{
+    const int k1 = 8 * h + 2 * jj;
+    CP Z[4];
+    if constexpr (LAY == kLaySingle) {
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) Z[sp] = Yj[sp];
+    } else if constexpr (LAY == kLayGeneral) {
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            Z[sp] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if ((a.slot_ap >> (4 * t + sp)) & 1u) Z[sp] = addc(Z[sp], Yj[t]);
+        }
+    } else {
+        // Z_s = S - Y_s as the sum of the other three: 6 additions, no cancellation
+        const CP P01 = addc(Yj[0], Yj[1]), P23 = addc(Yj[2], Yj[3]);
+        Z[0] = addc(Yj[1], P23);
+        Z[1] = addc(Yj[0], P23);
+        Z[2] = addc(P01, Yj[3]);
+        Z[3] = addc(P01, Yj[2]);
+    }
+    const CP Z0 = Z[0];
+    const CP U = rot(e1c, e1s, e1n, Z[1]);
+    const float4 e2 = lds4(&pt.e2[4 * h + jj]);
+    const CP V = rot(f2(e2.x, e2.y), f2(e2.z, e2.w), lds2(&pt.e2n[4 * h + jj]), Z[2]);
+    const float4 e12 = lds4(&pt.e12[k1 + k2]);
+    const CP X = rot(f2(e12.x, e12.y), f2(e12.z, e12.w), lds2(&pt.e12n[k1 + k2]), Z[3]);
+    const CP pp = addc(Z0, U), mm = subc(Z0, U), ss = addc(V, X), dd = subc(V, X);
+    R[0] = addc(pp, ss);
+    R[1] = addc(mm, dd);
+    R[2] = subc(pp, ss);
+    R[3] = subc(mm, dd);
+}
+
+// Scores q_k |R_k|^2 / D_k (Eq. 11) of the 16 candidates of pair jj, kept
+// in two running maxima (rows kap1 < 16 and kap1 >= 16), each fed in
+// increasing index order.
+__device__ __forceinline__ void score_pair(const RecordF32 &rec, const CP (&R)[4], const int h, const int jj,
+                                           const int k2, float &bs0, int &bk0, float &b0re, float &b0im,
+                                           float &bs1, int &bk1, float &b1re, float &b1im)
+{
+    const int k1 = 8 * h + 2 * jj;
+    const float4 q0 = lds4(rec.qDP[4 * h + jj][0][k2]);
+    const float4 q1 = lds4(rec.qDP[4 * h + jj][1][k2]);
+    const float2 s00 = energy(f2(q0.x, q0.y), R[0]), s01 = energy(f2(q0.z, q0.w), R[1]);
+    const float2 s10 = energy(f2(q1.x, q1.y), R[2]), s11 = energy(f2(q1.z, q1.w), R[3]);
+    const int ka = k1 * kW + k2, kb = ka + kW;
+    keep_best(s00.x, ka, R[0].re.x, R[0].im.x, bs0, bk0, b0re, b0im);
+    keep_best(s01.x, ka + 16, R[1].re.x, R[1].im.x, bs0, bk0, b0re, b0im);
+    keep_best(s00.y, kb, R[0].re.y, R[0].im.y, bs0, bk0, b0re, b0im);
+    keep_best(s01.y, kb + 16, R[1].re.y, R[1].im.y, bs0, bk0, b0re, b0im);
+    keep_best(s10.x, ka + 512, R[2].re.x, R[2].im.x, bs1, bk1, b1re, b1im);
+    keep_best(s11.x, ka + 528, R[3].re.x, R[3].im.x, bs1, bk1, b1re, b1im);
+    keep_best(s10.y, kb + 512, R[2].re.y, R[2].im.y, bs1, bk1, b1re, b1im);
+    keep_best(s11.y, kb + 528, R[3].re.y, R[3].im.y, bs1, bk1, b1re, b1im);
+}
+
 template <int LAY = kLayThreeQuarter, bool PAIRS = false>
 __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &rec, const C2<float> *om,
                                                 const C2<float> *omc, const PairTables &pt, const WorkEntry we,
@@ -648,49 +718,9 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
         }
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-            const int k1 = 8 * h + 2 * jj;
-            // Z_s = sum of Y_t over the slots holding sub-pixel s (three-quarter: S - Y_s)
-            CP Z[4];
-            if constexpr (LAY == kLaySingle) {
-#pragma unroll
-                for (int sp = 0; sp < 4; ++sp) Z[sp] = Y[jj][sp];
-            } else if constexpr (LAY == kLayGeneral) {
-#pragma unroll
-                for (int sp = 0; sp < 4; ++sp) {
-                    Z[sp] = {f2(0.f, 0.f), f2(0.f, 0.f)};
-#pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if ((a.slot_ap >> (4 * t + sp)) & 1u) Z[sp] = addc(Z[sp], Y[jj][t]);
-                }
-            } else {
-                // Z_s = S - Y_s as the sum of the other three: 6 additions, no cancellation
-                const CP P01 = addc(Y[jj][0], Y[jj][1]), P23 = addc(Y[jj][2], Y[jj][3]);
-                Z[0] = addc(Y[jj][1], P23);
-                Z[1] = addc(Y[jj][0], P23);
-                Z[2] = addc(P01, Y[jj][3]);
-                Z[3] = addc(P01, Y[jj][2]);
-            }
-            const CP Z0 = Z[0];
-            const CP U = rot(e1c, e1s, e1n, Z[1]);
-            const float4 e2 = lds4(&pt.e2[4 * h + jj]);
-            const CP V = rot(f2(e2.x, e2.y), f2(e2.z, e2.w), lds2(&pt.e2n[4 * h + jj]), Z[2]);
-            const float4 e12 = lds4(&pt.e12[k1 + k2]);
-            const CP X = rot(f2(e12.x, e12.y), f2(e12.z, e12.w), lds2(&pt.e12n[k1 + k2]), Z[3]);
-            const CP pp = addc(Z0, U), mm = subc(Z0, U), ss = addc(V, X), dd = subc(V, X);
-            const CP R00 = addc(pp, ss), R01 = addc(mm, dd), R10 = subc(pp, ss), R11 = subc(mm, dd);
-            const float4 q0 = lds4(rec.qDP[4 * h + jj][0][k2]);
-            const float4 q1 = lds4(rec.qDP[4 * h + jj][1][k2]);
-            const float2 s00 = energy(f2(q0.x, q0.y), R00), s01 = energy(f2(q0.z, q0.w), R01);
-            const float2 s10 = energy(f2(q1.x, q1.y), R10), s11 = energy(f2(q1.z, q1.w), R11);
-            const int ka = k1 * kW + k2, kb = ka + kW;
-            keep_best(s00.x, ka, R00.re.x, R00.im.x, bs0, bk0, b0re, b0im);
-            keep_best(s01.x, ka + 16, R01.re.x, R01.im.x, bs0, bk0, b0re, b0im);
-            keep_best(s00.y, kb, R00.re.y, R00.im.y, bs0, bk0, b0re, b0im);
-            keep_best(s01.y, kb + 16, R01.re.y, R01.im.y, bs0, bk0, b0re, b0im);
-            keep_best(s10.x, ka + 512, R10.re.x, R10.im.x, bs1, bk1, b1re, b1im);
-            keep_best(s11.x, ka + 528, R11.re.x, R11.im.x, bs1, bk1, b1re, b1im);
-            keep_best(s10.y, kb + 512, R10.re.y, R10.im.y, bs1, bk1, b1re, b1im);
-            keep_best(s11.y, kb + 528, R11.re.y, R11.im.y, bs1, bk1, b1re, b1im);
+            CP R[4];
+            state_to_R<LAY>(a, Y[jj], h, jj, k2, e1c, e1s, e1n, pt, R);
+            score_pair(rec, R, h, jj, k2, bs0, bk0, b0re, b0im, bs1, bk1, b1re, b1im);
         }
         if (bs1 > bs0) { bs0 = bs1; bk0 = bk1; b0re = b1re; b0im = b1im; }
         float bs = bs0;
@@ -701,6 +731,179 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
         const float Rim = __shfl_sync(0xffffffffu, b0im, wl);
         select_step<float, LAY, PAIRS>(a, om, rec.invD[bk], gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g,
                                        fpix, pw);
+    }
+    if (lane < 16) {
+        const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
+        const int yy = 4 * we.bi + (lane >> 2), xx = 4 * we.bj + (lane & 3);
+        img.hr[(long long)yy * img.hr_pitch + xx] = fpix;
+    }
+}
+
+// ----------------------------------------------- stored-C (paper) loop --
+// The iteration of Eqs. 11-17 in the paper's recurrent form (Table I): the
+// projected residual R itself is the loop state, and Eq. 17 subtracts
+// gamma delta times the column C_{., uv} of the Gram matrix (Eq. 14) stored
+// for the block's local measurement matrix: 8 KiB read per iteration, one
+// float4 per lane and register pair, 512 contiguous bytes per warp load.
+// R^0 comes from the same factored initial projection as the other loops,
+// and the scores, argmax and bookkeeping are the factored loop's.
+__device__ __forceinline__ float4 ldg_stream4(const float4 *p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+
+// R -= c C_{., l} over the lane's 32 candidates, column col (already loaded).
+__device__ __forceinline__ void sub_column(CP (&R)[4][4], const float4 (&col)[16], const C2<float> c)
+{
+    const float2 ncre = f2(-c.re, -c.re), cim = f2(c.im, c.im), ncim = f2(-c.im, -c.im);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        CP &r = R[i >> 2][i & 3];
+        const float2 Cre = f2(col[i].x, col[i].y), Cim = f2(col[i].z, col[i].w);
+        r.re = fma2(Cim, cim, fma2(Cre, ncre, r.re));
+        r.im = fma2(Cre, ncim, fma2(Cim, ncre, r.im));
+    }
+}
+
+__device__ __forceinline__ void load_column(const float4 *cs, const int l, const int lane, float4 (&col)[16])
+{
+    const float4 *p = cs + (size_t)l * 512 + lane;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) col[i] = ldg_stream4(p + 32 * i);
+}
+
+// The argmax of the stored-C loop tracks (score, slot) per lane, slot =
+// 16 a + 4 jj + 2 e + b in increasing index order, and reads the winner's R
+// from its registers afterwards by a switch on the warp-uniform slot: two
+// operations per candidate fewer than carrying R along (1.5x faster loop,
+// identical results).  Ties keep the lower slot, hence the lower index.
+__device__ __forceinline__ void keep_slot(const float s, const int i, float &bs, int &bi)
+{
+    if (s > bs) { bs = s; bi = i; }
+}
+
+__device__ __forceinline__ void score_pair_slot(const RecordF32 &rec, const CP (&R)[4], const int h, const int jj,
+                                                const int k2, float &bs0, int &bi0, float &bs1, int &bi1)
+{
+    const float4 q0 = lds4(rec.qDP[4 * h + jj][0][k2]);
+    const float4 q1 = lds4(rec.qDP[4 * h + jj][1][k2]);
+    const float2 s00 = energy(f2(q0.x, q0.y), R[0]), s01 = energy(f2(q0.z, q0.w), R[1]);
+    const float2 s10 = energy(f2(q1.x, q1.y), R[2]), s11 = energy(f2(q1.z, q1.w), R[3]);
+    keep_slot(s00.x, 4 * jj + 0, bs0, bi0);
+    keep_slot(s01.x, 4 * jj + 1, bs0, bi0);
+    keep_slot(s00.y, 4 * jj + 2, bs0, bi0);
+    keep_slot(s01.y, 4 * jj + 3, bs0, bi0);
+    keep_slot(s10.x, 4 * jj + 0, bs1, bi1);
+    keep_slot(s11.x, 4 * jj + 1, bs1, bi1);
+    keep_slot(s10.y, 4 * jj + 2, bs1, bi1);
+    keep_slot(s11.y, 4 * jj + 3, bs1, bi1);
+}
+
+// R of this lane's candidate in a slot (the same slot in every lane).
+template <int I>
+__device__ __forceinline__ void r_slot(const CP (&R)[4][4], float &re, float &im)
+{
+    const CP &r = R[(I >> 2) & 3][2 * (I >> 4) + (I & 1)];
+    re = ((I >> 1) & 1) ? r.re.y : r.re.x;
+    im = ((I >> 1) & 1) ? r.im.y : r.im.x;
+}
+
+__device__ __forceinline__ void r_at_slot(const CP (&R)[4][4], const int slot, float &re, float &im)
+{
+    switch (slot) {
+    case 0: r_slot<0>(R, re, im); break;
+    case 1: r_slot<1>(R, re, im); break;
+    case 2: r_slot<2>(R, re, im); break;
+    case 3: r_slot<3>(R, re, im); break;
+    case 4: r_slot<4>(R, re, im); break;
+    case 5: r_slot<5>(R, re, im); break;
+    case 6: r_slot<6>(R, re, im); break;
+    case 7: r_slot<7>(R, re, im); break;
+    case 8: r_slot<8>(R, re, im); break;
+    case 9: r_slot<9>(R, re, im); break;
+    case 10: r_slot<10>(R, re, im); break;
+    case 11: r_slot<11>(R, re, im); break;
+    case 12: r_slot<12>(R, re, im); break;
+    case 13: r_slot<13>(R, re, im); break;
+    case 14: r_slot<14>(R, re, im); break;
+    case 15: r_slot<15>(R, re, im); break;
+    case 16: r_slot<16>(R, re, im); break;
+    case 17: r_slot<17>(R, re, im); break;
+    case 18: r_slot<18>(R, re, im); break;
+    case 19: r_slot<19>(R, re, im); break;
+    case 20: r_slot<20>(R, re, im); break;
+    case 21: r_slot<21>(R, re, im); break;
+    case 22: r_slot<22>(R, re, im); break;
+    case 23: r_slot<23>(R, re, im); break;
+    case 24: r_slot<24>(R, re, im); break;
+    case 25: r_slot<25>(R, re, im); break;
+    case 26: r_slot<26>(R, re, im); break;
+    case 27: r_slot<27>(R, re, im); break;
+    case 28: r_slot<28>(R, re, im); break;
+    case 29: r_slot<29>(R, re, im); break;
+    case 30: r_slot<30>(R, re, im); break;
+    default: r_slot<31>(R, re, im); break;
+    }
+}
+
+template <int LAY = kLayThreeQuarter, bool PAIRS = false>
+__device__ __forceinline__ void greedy_loop_stored(const Args &a, const RecordF32 &rec, const float4 *cs,
+                                                   const C2<float> *om, const PairTables &pt, const WorkEntry we,
+                                                   const int lane, C2<float> (&Y0)[8][4])
+{
+    const int k2 = lane & 15, h = lane >> 4;
+    const float c1 = om[k2].re, s1 = om[k2].im;
+    const float2 e1c = f2(c1, c1), e1s = f2(s1, s1), e1n = f2(-s1, -s1);
+    CP R[4][4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        CP Yj[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            Yj[t] = {f2(Y0[2 * jj][t].re, Y0[2 * jj + 1][t].re), f2(Y0[2 * jj][t].im, Y0[2 * jj + 1][t].im)};
+        state_to_R<LAY>(a, Yj, h, jj, k2, e1c, e1s, e1n, pt, R[jj]);
+    }
+    const float gamma = (float)a.gamma;
+    const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
+    float fpix = 0.f, pw = 0.f;
+    int u = 0, v = 0;
+    C2<float> g[4];
+    const long long trow = (long long)we.ord * a.nu_max;
+
+    for (int it = 0; it < a.nu_max; ++it) {
+        float bs0 = -1.f, bs1 = -1.f;
+        int bi0 = 0, bi1 = 0;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) score_pair_slot(rec, R[jj], h, jj, k2, bs0, bi0, bs1, bi1);
+        if (bs1 > bs0) { bs0 = bs1; bi0 = bi1 + 16; }
+        float bs = bs0;
+        // slot -> k: a = slot >> 4, jj = (slot >> 2) & 3, e = (slot >> 1) & 1, b = slot & 1
+        int bk = (8 * h + 2 * ((bi0 >> 2) & 3) + ((bi0 >> 1) & 1) + 16 * (bi0 >> 4)) * kW + k2 + 16 * (bi0 & 1);
+        warp_argmax(bs, bk);
+        const bool more = it + 1 < a.nu_max;
+        float4 col[16];
+        if (more) load_column(cs, bk, lane, col);      // in flight during the bookkeeping
+        const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;
+        const int slot = ((bk >> 9) << 4) | (((bk >> 6) & 3) << 2) | (((bk >> 5) & 1) << 1) | ((bk >> 4) & 1);
+        float mre, mim;
+        r_at_slot(R, slot, mre, mim);
+        const float Rre = __shfl_sync(0xffffffffu, mre, wl);
+        const float Rim = __shfl_sync(0xffffffffu, mim, wl);
+        const float invD = rec.invD[bk];
+        select_step<float, LAY, PAIRS>(a, om, invD, gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix,
+                                       pw);
+        if (more) {
+            const C2<float> gd = {gamma * (Rre * invD), gamma * (Rim * invD)};   // as in select_step
+            sub_column(R, col, gd);
+            if constexpr (PAIRS) {
+                // the partner -uv gets conj(gamma delta) (none when uv = -uv)
+                load_column(cs, ((-u) & 31) * kW + ((-v) & 31), lane, col);
+                sub_column(R, col, C2<float>{pw * gd.re, -pw * gd.im});
+            }
+        }
     }
     if (lane < 16) {
         const ImageDesc img = a.descs ? a.descs[we.img] : a.single;
@@ -967,12 +1170,16 @@ __device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortli
 // of one does not constrain the other.  3 and 4 = mode 0 for other sensor
 // layouts: slot apertures from a.slot_ap (3), or one sub-pixel per slot (4).
 // Bit 3 (kModePairs) added to modes 0, 3, 4: the conjugate-pair update.
+// Bit 4 (kModeStoredC) added to those: the column of C read from the stored
+// Gram matrix instead of rebuilt from the factored tables.
 constexpr int kModePairs = 8;
+constexpr int kModeStoredC = 16;
 __host__ __device__ constexpr int lay_of(int mode)
 {
     return (mode & 7) == 3 ? kLayGeneral : (mode & 7) == 4 ? kLaySingle : kLayThreeQuarter;
 }
 __host__ __device__ constexpr bool pairs_of(int mode) { return (mode & kModePairs) != 0; }
+__host__ __device__ constexpr bool stored_of(int mode) { return (mode & kModeStoredC) != 0; }
 __host__ __device__ constexpr bool plain_of(int mode) { return (mode & 7) == 0 || (mode & 7) == 3 || (mode & 7) == 4; }
 
 template <typename T, int MODE> struct Loop;
@@ -980,9 +1187,16 @@ template <int MODE> struct Loop<float, MODE> {
     using Rec = typename RecOf<float, MODE>::type;
     static __device__ __forceinline__ void run(const Args &a, const Rec &rec, C2<float> *scratch,
                                                const C2<float> *om, const C2<float> *omc, const PairTables &pt,
-                                               const float *wt, const WorkEntry we, const int lane)
+                                               const float *wt, const WorkEntry we, const int lane,
+                                               const float4 *cs)
     {
-        if constexpr (plain_of(MODE)) {
+        if constexpr (stored_of(MODE)) {
+            // table sets without a stored matrix take the factored loop
+            C2<float> Y[8][4];
+            initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
+            if (cs != nullptr) greedy_loop_stored<lay_of(MODE), pairs_of(MODE)>(a, rec, cs, om, pt, we, lane, Y);
+            else greedy_loop_f32<lay_of(MODE), pairs_of(MODE)>(a, rec, om, omc, pt, we, lane, Y);
+        } else if constexpr (plain_of(MODE)) {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
             greedy_loop_f32<lay_of(MODE), pairs_of(MODE)>(a, rec, om, omc, pt, we, lane, Y);
@@ -1021,7 +1235,8 @@ template <int MODE> struct Loop<float, MODE> {
 template <int MODE> struct Loop<double, MODE> {
     static __device__ __forceinline__ void run(const Args &a, const Record<double> &rec, C2<double> *scratch,
                                                const C2<double> *om, const C2<double> *omc, const PairTables &,
-                                               const double *wt, const WorkEntry we, const int lane)
+                                               const double *wt, const WorkEntry we, const int lane,
+                                               const float4 *)
     {
         C2<double> Y[8][4];
         initial_projection<double>(a, rec, scratch, omc, wt, we, lane, Y);
@@ -1032,8 +1247,8 @@ template <int MODE> struct Loop<double, MODE> {
                                                     const PairTables &pt, const double *wt, const WorkEntry e0,
                                                     const WorkEntry e1, const int lane)
     {
-        if (e0.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e0, lane);
-        if (e1.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e1, lane);
+        if (e0.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e0, lane, nullptr);
+        if (e1.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e1, lane, nullptr);
     }
 };
 
@@ -1137,9 +1352,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
             const WorkEntry e1 = a.entries[(size_t)c * kChunk + warp + WARPS];
             Loop<T, MODE>::run_pair(a, *slot(s), scratch, om, omc, *pt, wt, e0, e1, lane);
         } else {
+            const float4 *cs = nullptr;       // this chunk's stored Gram matrix, if any
+            if constexpr (stored_of(MODE)) {
+                const int cl = a.cslot[a.chunk_table[c]];
+                if (cl >= 0) cs = a.cstore + (size_t)cl * (kStoredCBytes / 16);
+            }
             for (int e = warp; e < kChunk; e += WARPS) {
                 const WorkEntry we = a.entries[(size_t)c * kChunk + e];
-                if (we.img >= 0) Loop<T, MODE>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane);
+                if (we.img >= 0) Loop<T, MODE>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane, cs);
             }
         }
         __syncthreads();                       // every warp is done with slot s
@@ -1494,6 +1714,8 @@ const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 4), RLJSDE_VARIANT(float, 8, 2, 4), RLJSDE_VARIANT(double, 4, 1, 4),
     RLJSDE_VARIANT(float, 4, 3, 8), RLJSDE_VARIANT(float, 4, 3, 11), RLJSDE_VARIANT(float, 4, 3, 12),
     RLJSDE_VARIANT(double, 4, 1, 8), RLJSDE_VARIANT(double, 4, 1, 11), RLJSDE_VARIANT(double, 4, 1, 12),
+    RLJSDE_VARIANT(float, 4, 3, 16), RLJSDE_VARIANT(float, 4, 3, 19), RLJSDE_VARIANT(float, 4, 3, 20), RLJSDE_VARIANT(float, 4, 3, 24),
+    RLJSDE_VARIANT(float, 4, 3, 27), RLJSDE_VARIANT(float, 4, 3, 28),
 };
 #undef RLJSDE_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -1515,6 +1737,8 @@ Args make_args(const rljsde_plan *p)
     a.n_chunks = p->n_chunks;
     a.records = static_cast<const unsigned char *>(p->d_records);
     a.records_short = static_cast<const unsigned char *>(p->d_records_short);
+    a.cstore = static_cast<const float4 *>(p->d_cstore);
+    a.cslot = p->d_cslot;
     a.record_bytes = (uint32_t)p->record_bytes;
     a.consts = p->d_consts;
     a.descs = nullptr;
@@ -1560,7 +1784,68 @@ int launch_mode(const rljsde_plan *p, const Args &a, int mode, int warps, int mi
     return RLJSDE_ERR_UNSUPPORTED;
 }
 
+// Stored Gram matrix (c_supply) of Eq. 14 in the factored form of the
+// tables, C_{k,l} = sum_t conj(h_t(k)) h_t(l) G_t((l - k) mod 16), evaluated
+// in FP64 from the FP64 G_t and rounded to FP32 once, in the stored-C loop's
+// read order (float4 i * 32 + lane of column l: the candidates of lane's
+// register pair i).  One CTA per (column, stored table set), one thread per
+// float4.
+__device__ __forceinline__ C2<double> h64(const double2 *om, const uint32_t slot_ap, const int t, const int k1,
+                                          const int k2)
+{
+    const int ap = (int)(slot_ap >> (4 * t)) & 15;
+    C2<double> z = {0.0, 0.0};
+    for (int e = 0; e < 2; ++e)
+        for (int g = 0; g < 2; ++g)
+            if ((ap >> (2 * e + g)) & 1) {
+                const double2 w = om[(e * k1 + g * k2) & 31];
+                z.re += w.x;
+                z.im += w.y;
+            }
+    return z;
+}
+
+__global__ void __launch_bounds__(512) build_c_kernel(const double *g64, const Consts *consts,
+                                                      const uint32_t slot_ap, float4 *out)
+{
+    __shared__ double2 G[4][256];
+    __shared__ double2 om[32];
+    const int l = blockIdx.x, tab = blockIdx.y;
+    const double *src = g64 + (size_t)tab * 2048;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) G[i >> 8][i & 255] = make_double2(src[2 * i], src[2 * i + 1]);
+    if (threadIdx.x < 32) om[threadIdx.x] = make_double2(consts->om64[2 * threadIdx.x], consts->om64[2 * threadIdx.x + 1]);
+    __syncthreads();
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int jj = i >> 2, qa = (i >> 1) & 1, qb = i & 1;
+    const int l1 = l >> 5, l2 = l & 31, k2 = (lane & 15) + 16 * qb;
+    float re[2], im[2];
+    for (int e = 0; e < 2; ++e) {
+        const int k1 = 8 * (lane >> 4) + 2 * jj + e + 16 * qa;
+        const int d = ((l1 - k1) & 15) * 16 + ((l2 - k2) & 15);
+        double cre = 0.0, cim = 0.0;
+        for (int t = 0; t < 4; ++t) {
+            const C2<double> hk = h64(om, slot_ap, t, k1, k2), hl = h64(om, slot_ap, t, l1, l2);
+            const C2<double> z = cmul(cconj(hk), hl);
+            const double2 gt = G[t][d];
+            cre += z.re * gt.x - z.im * gt.y;
+            cim += z.re * gt.y + z.im * gt.x;
+        }
+        re[e] = (float)cre;
+        im[e] = (float)cim;
+    }
+    out[((size_t)tab * kK + l) * 512 + threadIdx.x] = make_float4(re[0], re[1], im[0], im[1]);
+}
+
 }  // namespace
+
+int build_stored_c(rljsde_plan *p, const double *d_g64)
+{
+    if (!p->d_cstore || p->n_stored < 1 || p->n_stored > 65535) return RLJSDE_ERR_INVALID_ARG;
+    build_c_kernel<<<dim3(kK, p->n_stored), 512>>>(d_g64, p->d_consts, p->slot_ap,
+                                                  static_cast<float4 *>(p->d_cstore));
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return RLJSDE_ERR_CUDA;
+    return RLJSDE_OK;
+}
 
 int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
 {
@@ -1594,7 +1879,8 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
     // Default: 4 warps per CTA, as many CTAs as the 168-register variant fits.
     if (warps == 0) { warps = 4; if (ctas_per_sm == 0) ctas_per_sm = 3; }
     const int fp64 = p->params.precision == 1;
-    const int mode = (p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0) | (p->params.pairs ? kModePairs : 0);
+    const int mode = (p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0) | (p->params.pairs ? kModePairs : 0) |
+                     (p->n_stored > 0 ? kModeStoredC : 0);
     // The variant with this precision and warp count whose register budget
     // admits the requested CTAs per SM (the largest one not above it).
     int best = -1, best_occ = 0;

@@ -171,10 +171,16 @@ void build_record64(const uint8_t *key, const double *w, const Cd *r32, uint32_t
 }
 
 void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap, bool pairs,
-                    const std::vector<double> &q, RecordF32 *rec, RecordShortF32 *sh)
+                    const std::vector<double> &q, RecordF32 *rec, RecordShortF32 *sh, double *g64)
 {
     static thread_local Tables T;
     build_tables(key, w, r32, slot_ap, T);
+    if (g64)     // FP64 G_t for the stored Gram matrix: [t][d] as (re, im)
+        for (int t = 0; t < 4; ++t)
+            for (int d = 0; d < 256; ++d) {
+                g64[(t * 256 + d) * 2] = T.Gre[t][d];
+                g64[(t * 256 + d) * 2 + 1] = T.Gim[t][d];
+            }
     for (int d = 0; d < 256; ++d) {
         float *a = sh->G01[d], *b = sh->G23[d];
         a[0] = (float)T.Gre[0][d]; a[1] = (float)T.Gre[1][d]; a[2] = (float)T.Gim[0][d]; a[3] = (float)T.Gim[1][d];
@@ -216,6 +222,8 @@ void release(rljsde_plan *p)
     if (p->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
     cudaFree(p->d_records);
     cudaFree(p->d_records_short);
+    cudaFree(p->d_cstore);
+    cudaFree(p->d_cslot);
     cudaFree(p->d_entries);
     cudaFree(p->d_chunk_table);
     cudaFree(p->d_consts);
@@ -244,6 +252,8 @@ int check_params(const rljsde_params *p)
         return RLJSDE_ERR_INVALID_ARG;
     if (p->pairs != 0 && p->pairs != 1) return RLJSDE_ERR_INVALID_ARG;
     if ((p->path == 2 || p->path == 3) && p->precision != 0) return RLJSDE_ERR_UNSUPPORTED;
+    if (p->c_supply < 0 || p->c_supply > 2) return RLJSDE_ERR_INVALID_ARG;
+    if (p->c_supply == 1 && (p->precision != 0 || p->path == 2 || p->path == 3)) return RLJSDE_ERR_UNSUPPORTED;
     return RLJSDE_OK;
 }
 
@@ -396,6 +406,10 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         if (p->onthefly)
             for (auto &t : table_of) t = 0;
     } else {
+        if (prm->c_supply == 1) {      // the direct path has no Gram matrix to store
+            release(p);
+            return RLJSDE_ERR_UNSUPPORTED;
+        }
         for (int i = 0; i < n_images; ++i) {
             p->ord_base[i] = ord;
             for (int bi = 0; bi < lr_h[i] / 2; ++bi)
@@ -406,6 +420,10 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         }
     }
     p->n_blocks = ord;
+    if (prm->c_supply == 1 && p->onthefly) {
+        release(p);
+        return RLJSDE_ERR_UNSUPPORTED;
+    }
 
     // Work list: blocks sorted by table, each table's run padded to whole
     // chunks so that every chunk uses exactly one table.
@@ -421,6 +439,31 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     std::vector<uint32_t> chunk_table(p->n_chunks);
     for (int g = 0; g < n_groups; ++g)
         for (int e = start[g]; e < start[g + 1]; e += kChunk) chunk_table[e / kChunk] = (uint32_t)g;
+
+    // Table sets whose Gram matrix is stored (c_supply): all of them (1), or
+    // (auto) those at least kStoredMinBlocks blocks use, the most used first,
+    // within an eighth of the free device memory.
+    if (!p->direct && !p->onthefly && prm->precision == 0 && prm->c_supply != 2) {
+        p->cslot.assign(p->n_tables, -1);
+        if (prm->c_supply == 1) {
+            for (int t = 0; t < p->n_tables; ++t) {
+                p->cslot[t] = p->n_stored++;
+                p->n_stored_blocks += count[t];
+            }
+        } else {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+            const size_t budget = free_b / 8;
+            std::vector<int> order(p->n_tables);
+            for (int t = 0; t < p->n_tables; ++t) order[t] = t;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return count[x] > count[y]; });
+            for (int t : order) {
+                if (count[t] < kStoredMinBlocks || (size_t)(p->n_stored + 1) * kStoredCBytes > budget) break;
+                p->cslot[t] = p->n_stored++;
+                p->n_stored_blocks += count[t];
+            }
+        }
+    }
 
     st = upload(&p->d_entries, entries.data(), entries.size() * sizeof(WorkEntry));
     if (!st) st = upload(&p->d_chunk_table, chunk_table.data(), chunk_table.size() * sizeof(uint32_t));
@@ -453,9 +496,11 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         // FP64 tables per distinct local matrix, stored in the loop's precision.
         p->record_bytes = prm->precision ? sizeof(Record<double>) : sizeof(RecordF32);
         std::vector<unsigned char> host, host_short;
+        std::vector<double> g64;
         try {
             host.resize(p->record_bytes * (size_t)p->n_tables);
             if (!prm->precision) host_short.resize(sizeof(RecordShortF32) * (size_t)p->n_tables);
+            if (p->n_stored) g64.resize((size_t)p->n_stored * 2048);
         } catch (...) {
             st = RLJSDE_ERR_OUT_OF_MEMORY;
         }
@@ -469,10 +514,26 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
                 else
                     build_record32(key, w64, r32, slot_ap, prm->pairs != 0, p->q,
                                    (RecordF32 *)(host.data() + p->record_bytes * t),
-                                   (RecordShortF32 *)(host_short.data() + sizeof(RecordShortF32) * t));
+                                   (RecordShortF32 *)(host_short.data() + sizeof(RecordShortF32) * t),
+                                   p->n_stored && p->cslot[t] >= 0 ? g64.data() + (size_t)2048 * p->cslot[t]
+                                                                   : nullptr);
             }
             st = upload(&p->d_records, host.data(), host.size());
             if (!st && !prm->precision) st = upload(&p->d_records_short, host_short.data(), host_short.size());
+            if (!st && p->n_stored) {
+                // the Gram matrices (Eq. 14) of the stored table sets, built on the device
+                double *d_g64 = nullptr;
+                p->cstore_bytes = kStoredCBytes * (size_t)p->n_stored;
+                if (cudaMalloc(&p->d_cstore, p->cstore_bytes) != cudaSuccess) {
+                    p->d_cstore = nullptr;
+                    cudaGetLastError();
+                    st = RLJSDE_ERR_OUT_OF_MEMORY;
+                }
+                if (!st) st = upload(&d_g64, g64.data(), g64.size() * sizeof(double));
+                if (!st) st = upload(&p->d_cslot, p->cslot.data(), p->cslot.size() * sizeof(int));
+                if (!st) st = build_stored_c(p, d_g64);
+                cudaFree(d_g64);
+            }
         }
     }
     if (!st && (p->direct || p->onthefly)) {
@@ -519,6 +580,7 @@ int rljsde_default_params(rljsde_params *p)
     p->path = 0;
     p->layout = RLJSDE_LAYOUT_THREE_QUARTER;
     p->pairs = 0;
+    p->c_supply = 0;
     return RLJSDE_OK;
 }
 
@@ -566,6 +628,9 @@ int rljsde_plan_info(const rljsde_plan_t *p, rljsde_plan_info_t *out)
     out->paper_D_bytes = (int64_t)p->n_tables * kK * 8;
     out->path = p->direct ? 2 : p->onthefly ? 3 : 1;
     out->n_apertures = p->n_apertures;
+    out->n_stored_c_tables = p->n_stored;
+    out->n_stored_c_blocks = p->n_stored_blocks;
+    out->device_c_bytes = (int64_t)p->cstore_bytes;
     return RLJSDE_OK;
 }
 

@@ -108,6 +108,16 @@ struct Shortlist {
 };
 static_assert(sizeof(Shortlist) == 136, "shortlist layout");
 
+// Stored Gram matrix of one table set (c_supply): 1024 columns of 8 KiB,
+// each as 16 x 32 float4 = (C_{k,l}.re, C_{k+32,l}.re, C_{k,l}.im,
+// C_{k+32,l}.im), entry i * 32 + lane holding the two candidates that lane
+// of the FP32 loop updates in its register pair i.
+constexpr size_t kStoredCBytes = (size_t)kK * kK * 8;
+// c_supply auto stores the matrix of a table set that at least this many
+// blocks use: below that its 8 MiB saves too little per reconstruction
+// (border table sets of a recurrent mask are used by few blocks each).
+constexpr int kStoredMinBlocks = 256;
+
 }  // namespace rljsde
 
 // The opaque plan object of the C ABI.
@@ -133,6 +143,12 @@ struct rljsde_plan {
     void *d_records = nullptr;        // n_tables records (float or double)
     size_t record_bytes = 0;
     void *d_records_short = nullptr;  // n_tables RecordShortF32 (FP32 plans)
+    int n_stored = 0;                 // table sets whose Gram matrix is stored (c_supply)
+    int n_stored_blocks = 0;          // blocks that use them
+    std::vector<int> cslot;           // per table set: its stored matrix, or -1 (factored)
+    int *d_cslot = nullptr;
+    void *d_cstore = nullptr;         // n_stored x kStoredCBytes, in the stored-C loop's read order
+    size_t cstore_bytes = 0;
     rljsde::WorkEntry *d_entries = nullptr;
     uint32_t *d_chunk_table = nullptr;
     rljsde::Consts *d_consts = nullptr;
@@ -149,5 +165,9 @@ struct rljsde_plan {
 namespace rljsde {
 // Implemented in kernels.cu.
 int choose_launch(rljsde_plan *plan, int warps, int ctas_per_sm);
+// Fill plan->d_cstore from the FP64 G_t of the stored table sets (device,
+// in stored order, per table 4 x 256 x (re, im) doubles, t-major);
+// synchronous.
+int build_stored_c(rljsde_plan *plan, const double *d_g64);
 const char *last_cuda_error();
 }  // namespace rljsde

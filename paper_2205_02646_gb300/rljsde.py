@@ -28,12 +28,13 @@ class RljsdeError(RuntimeError):
 
 class Params(ctypes.Structure):
     """``rljsde_params``: B, W, nu_max, gamma_odc, rho_decay, q_mode, q_table,
-    precision, path, layout, pairs (see the header for meanings and defaults)."""
+    precision, path, layout, pairs, c_supply (see the header for meanings and
+    defaults)."""
     _fields_ = [("block", ctypes.c_int), ("window", ctypes.c_int), ("nu_max", ctypes.c_int),
                 ("gamma_odc", ctypes.c_double), ("rho_decay", ctypes.c_double),
                 ("q_mode", ctypes.c_int), ("q_table", ctypes.POINTER(ctypes.c_double)),
                 ("precision", ctypes.c_int), ("path", ctypes.c_int), ("layout", ctypes.c_int),
-                ("pairs", ctypes.c_int)]
+                ("pairs", ctypes.c_int), ("c_supply", ctypes.c_int)]
 
 
 LAYOUT_THREE_QUARTER = 0   # mask code = opaque sub-pixel 2 * dy + dx
@@ -46,7 +47,8 @@ class PlanInfo(ctypes.Structure):
                 ("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("grid", ctypes.c_int),
                 ("device_table_bytes", ctypes.c_int64), ("paper_B_bytes", ctypes.c_int64),
                 ("paper_C_bytes", ctypes.c_int64), ("paper_D_bytes", ctypes.c_int64),
-                ("path", ctypes.c_int), ("n_apertures", ctypes.c_int)]
+                ("path", ctypes.c_int), ("n_apertures", ctypes.c_int), ("n_stored_c_tables", ctypes.c_int),
+                ("n_stored_c_blocks", ctypes.c_int), ("device_c_bytes", ctypes.c_int64)]
 
 
 class Image(ctypes.Structure):
@@ -61,7 +63,8 @@ EXPORTS = ["rljsde_default_params", "rljsde_plan_create", "rljsde_plan_create_ba
            "rljsde_graph_launch", "rljsde_net_create", "rljsde_net_destroy", "rljsde_net_num_params",
            "rljsde_net_get_params", "rljsde_net_set_params", "rljsde_net_patches", "rljsde_net_gradient",
            "rljsde_net_train_step", "rljsde_net_logits", "rljsde_propose_workspace", "rljsde_propose",
-           "rljsde_reconstruct_learned", "rljsde_propose_noalloc", "rljsde_fp32_peak"]
+           "rljsde_reconstruct_learned", "rljsde_propose_noalloc", "rljsde_fp32_peak",
+           "rljsde_l2_read_peak"]
 
 SHORTLIST_BYTES = 136
 
@@ -110,6 +113,7 @@ def _lib():
         lib.rljsde_reconstruct_learned.argtypes = [vp, vp, sz, vp, sz, vp, f, i, vp, vp, vp, vp]
         lib.rljsde_propose_noalloc.argtypes = [vp, vp, vp, sz, vp, vp]
         lib.rljsde_fp32_peak.argtypes = [i, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(f)]
+        lib.rljsde_l2_read_peak.argtypes = [i, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(f)]
         lib.rljsde_status_string.argtypes = [i]
         lib.rljsde_status_string.restype = ctypes.c_char_p
         _LIB = lib
@@ -308,6 +312,14 @@ def fp32_peak(reps=5, stream=None) -> dict:
     _ok(_lib().rljsde_fp32_peak(int(reps), _stream_ptr(stream), ctypes.byref(tf), ctypes.byref(ms)),
         "rljsde_fp32_peak")
     return dict(tflops=tf.value, ms=ms.value)
+
+
+def l2_read_peak(reps=5, stream=None) -> dict:
+    """L2 read bandwidth of the current device (``rljsde_l2_read_peak``)."""
+    gbs, ms = ctypes.c_double(), ctypes.c_float()
+    _ok(_lib().rljsde_l2_read_peak(int(reps), _stream_ptr(stream), ctypes.byref(gbs), ctypes.byref(ms)),
+        "rljsde_l2_read_peak")
+    return dict(gbs=gbs.value, ms=ms.value)
 
 
 def shortlist_view(buf, n_blocks):

@@ -36,8 +36,8 @@ def test_exports_every_declared_symbol(rl):
 def test_defaults_and_status_strings(rl):
     p = rl.default_params()
     assert (p.block, p.window, p.nu_max, p.gamma_odc, p.rho_decay, p.q_mode, p.precision, p.path, p.layout,
-            p.pairs) == \
-        (4, 32, 100, 0.5, 0.7, 0, 0, 0, 0, 0)
+            p.pairs, p.c_supply) == \
+        (4, 32, 100, 0.5, 0.7, 0, 0, 0, 0, 0, 0)
     lib = rl.load()
     for s in range(9):
         assert lib.rljsde_status_string(s)
@@ -69,6 +69,11 @@ def test_argument_errors_before_gpu(rl):
     # sensor layouts: aperture codes 0..15; paths that cannot hold the mask's apertures
     assert _create(rl, ok, layout=2) == 1
     assert _create(rl, ok, pairs=2) == 1
+    # stored Gram matrices: FP32 loop on host table sets only
+    assert _create(rl, ok, c_supply=3) == 1
+    assert _create(rl, ok, c_supply=1, precision=1) == 8
+    assert _create(rl, ok, c_supply=1, path=2) == 8
+    assert _create(rl, ok, c_supply=1, path=3) == 8
     assert _create(rl, np.full((8, 8), 16, np.uint8), layout=1) == 3
     quarter = np.tile(np.array([[1, 2], [4, 8]], np.uint8), (4, 4))
     assert _create(rl, quarter, layout=1, path=3) == 8            # in-kernel tables: three-quarter only
