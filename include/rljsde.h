@@ -115,10 +115,13 @@ typedef struct {
                              FP32 loop on path 1 (RLJSDE_ERR_UNSUPPORTED
                              otherwise, also when auto would choose path 2 or
                              3) and fails with RLJSDE_ERR_OUT_OF_MEMORY when the
-                             matrices do not fit.  Stored C runs with 4 warps
-                             per CTA only (rljsde_set_launch with 8 warps:
-                             RLJSDE_ERR_UNSUPPORTED).  The learned proposal's
-                             loops always use the factored form                 */
+                             matrices do not fit.  A plan with both kinds of
+                             table sets runs two kernels per reconstruction;
+                             the stored-C loop always runs 4 warps per CTA at
+                             full occupancy (rljsde_set_launch and
+                             rljsde_autotune shape the factored loop).  The
+                             learned proposal's loops always use the factored
+                             form                                              */
 } rljsde_params;
 
 /* Fill *p with the defaults above.  Returns RLJSDE_ERR_INVALID_ARG on NULL. */
@@ -349,7 +352,10 @@ typedef struct {
     int n_tables;           /* distinct local measurement matrices (plans)    */
     int n_interior_tables;  /* of which windows lie wholly inside the image   */
     int n_work_entries;     /* blocks after padding each table's run          */
-    int warps_per_cta, ctas_per_sm, grid;   /* launch shape in effect         */
+    int warps_per_cta, ctas_per_sm, grid;   /* launch shape in effect (of the
+                                               factored loop; of the stored-C
+                                               loop when every table set is
+                                               stored)                        */
     int64_t device_table_bytes;   /* factored tables actually stored (device) */
     int64_t paper_B_bytes;        /* Table I equivalent: n_tables x 256 x 1024 x 8 B */
     int64_t paper_C_bytes;        /* n_tables x 1024^2 x 8 B                  */
@@ -359,6 +365,7 @@ typedef struct {
     int n_stored_c_tables;        /* table sets whose C is stored (c_supply)     */
     int n_stored_c_blocks;        /* blocks that use them                       */
     int64_t device_c_bytes;       /* their stored C on the device               */
+    int n_launches;               /* kernels one rljsde_reconstruct launches    */
 } rljsde_plan_info_t;
 
 int rljsde_plan_info(const rljsde_plan_t *plan, rljsde_plan_info_t *out);

@@ -130,6 +130,8 @@ struct Args {
     const unsigned char *records_short;    // RecordShortF32 per table (shortlist loop)
     const float4 *cstore;                  // stored Gram matrices (c_supply), kStoredCBytes each
     const int *cslot;                      // per table set: its stored matrix, or -1 (factored)
+    int cfilter;                           // chunks this launch takes: 0 all, 1 those whose table set
+                                           // has a stored matrix, 2 the others
     const Consts *consts;
     ImageDesc single;          // used when descs == nullptr
     const ImageDesc *descs;
@@ -1191,11 +1193,10 @@ template <int MODE> struct Loop<float, MODE> {
                                                const float4 *cs)
     {
         if constexpr (stored_of(MODE)) {
-            // table sets without a stored matrix take the factored loop
+            // (the launch takes only chunks whose table set has a stored matrix)
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            if (cs != nullptr) greedy_loop_stored<lay_of(MODE), pairs_of(MODE)>(a, rec, cs, om, pt, we, lane, Y);
-            else greedy_loop_f32<lay_of(MODE), pairs_of(MODE)>(a, rec, om, omc, pt, we, lane, Y);
+            greedy_loop_stored<lay_of(MODE), pairs_of(MODE)>(a, rec, cs, om, pt, we, lane, Y);
         } else if constexpr (plain_of(MODE)) {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
@@ -1259,7 +1260,10 @@ template <int MODE>
 __device__ __forceinline__ bool chunk_has_work(const Args &a, const int c)
 {
     if constexpr (MODE != 1 && MODE != 2) {
-        return true;
+        // a plan with stored and factored table sets runs them as two launches
+        if (a.cfilter == 0) return true;
+        const bool stored = a.cslot[a.chunk_table[c]] >= 0;
+        return a.cfilter == 1 ? stored : !stored;
     } else {
         bool mine = false;
         if (threadIdx.x < kChunk) {
@@ -1762,8 +1766,22 @@ int launch(const rljsde_plan *p, const Args &a, cudaStream_t s)
         if (p->params.pairs) onthefly_kernel<true><<<p->grid, kFlyWarps * 32, FlySmem::bytes, s>>>(a, p->n_entries);
         else onthefly_kernel<false><<<p->grid, kFlyWarps * 32, FlySmem::bytes, s>>>(a, p->n_entries);
     } else {
-        const Variant &v = kVariants[p->variant];
-        v.fn<<<p->grid, v.warps * 32, v.smem, s>>>(a);
+        // the stored-C loop on the table sets with a stored Gram matrix, the
+        // factored loop on the others: one launch each (one kernel holding
+        // both loops spills and ran the stored loop 1.5x slower)
+        const bool mixed = p->n_stored > 0 && p->n_stored < p->n_tables;
+        if (p->n_stored > 0) {
+            Args b = a;
+            b.cfilter = mixed ? 1 : 0;
+            const Variant &v = kVariants[p->variant_stored];
+            v.fn<<<p->grid_stored, v.warps * 32, v.smem, s>>>(b);
+        }
+        if (p->n_stored < p->n_tables) {
+            Args b = a;
+            b.cfilter = mixed ? 2 : 0;
+            const Variant &v = kVariants[p->variant];
+            v.fn<<<p->grid, v.warps * 32, v.smem, s>>>(b);
+        }
     }
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
@@ -1879,8 +1897,20 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
     // Default: 4 warps per CTA, as many CTAs as the 168-register variant fits.
     if (warps == 0) { warps = 4; if (ctas_per_sm == 0) ctas_per_sm = 3; }
     const int fp64 = p->params.precision == 1;
-    const int mode = (p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0) | (p->params.pairs ? kModePairs : 0) |
-                     (p->n_stored > 0 ? kModeStoredC : 0);
+    const int mode = (p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0) | (p->params.pairs ? kModePairs : 0);
+    if (p->n_stored > 0 && !fp64) {
+        // the stored-C loop: its one instantiation (4 warps, 168 registers)
+        p->variant_stored = -1;
+        for (int i = 0; i < kNumVariants; ++i)
+            if (!kVariants[i].fp64 && kVariants[i].mode == (mode | kModeStoredC)) p->variant_stored = i;
+        if (p->variant_stored < 0) return RLJSDE_ERR_UNSUPPORTED;
+        const int occ = occupancy(kVariants[p->variant_stored]);
+        if (occ < 0) return RLJSDE_ERR_CUDA;
+        if (occ == 0) return RLJSDE_ERR_UNSUPPORTED;
+        long long g = (long long)p->sm_count * occ;
+        p->grid_stored = (int)(p->n_chunks < g ? (p->n_chunks > 0 ? p->n_chunks : 1) : g);
+        p->ctas_stored = occ;
+    }
     // The variant with this precision and warp count whose register budget
     // admits the requested CTAs per SM (the largest one not above it).
     int best = -1, best_occ = 0;

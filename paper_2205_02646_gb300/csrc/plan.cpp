@@ -619,9 +619,10 @@ int rljsde_plan_info(const rljsde_plan_t *p, rljsde_plan_info_t *out)
     out->n_tables = p->n_tables;
     out->n_interior_tables = p->n_interior;
     out->n_work_entries = p->n_entries;
-    out->warps_per_cta = p->warps;
-    out->ctas_per_sm = p->ctas_per_sm;
-    out->grid = p->grid;
+    const bool all_stored = p->n_stored > 0 && p->n_stored == p->n_tables;
+    out->warps_per_cta = all_stored ? 4 : p->warps;
+    out->ctas_per_sm = all_stored ? p->ctas_stored : p->ctas_per_sm;
+    out->grid = all_stored ? p->grid_stored : p->grid;
     out->device_table_bytes = (int64_t)p->record_bytes * p->n_tables;
     out->paper_B_bytes = (int64_t)p->n_tables * 256 * kK * 8;
     out->paper_C_bytes = (int64_t)p->n_tables * kK * kK * 8;
@@ -631,6 +632,7 @@ int rljsde_plan_info(const rljsde_plan_t *p, rljsde_plan_info_t *out)
     out->n_stored_c_tables = p->n_stored;
     out->n_stored_c_blocks = p->n_stored_blocks;
     out->device_c_bytes = (int64_t)p->cstore_bytes;
+    out->n_launches = (p->n_stored > 0 && p->n_stored < p->n_tables) ? 2 : 1;
     return RLJSDE_OK;
 }
 

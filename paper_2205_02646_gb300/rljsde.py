@@ -48,7 +48,8 @@ class PlanInfo(ctypes.Structure):
                 ("device_table_bytes", ctypes.c_int64), ("paper_B_bytes", ctypes.c_int64),
                 ("paper_C_bytes", ctypes.c_int64), ("paper_D_bytes", ctypes.c_int64),
                 ("path", ctypes.c_int), ("n_apertures", ctypes.c_int), ("n_stored_c_tables", ctypes.c_int),
-                ("n_stored_c_blocks", ctypes.c_int), ("device_c_bytes", ctypes.c_int64)]
+                ("n_stored_c_blocks", ctypes.c_int), ("device_c_bytes", ctypes.c_int64),
+                ("n_launches", ctypes.c_int)]
 
 
 class Image(ctypes.Structure):

@@ -195,9 +195,13 @@ def test_plan_info_counts(rl):
     assert info["n_blocks"] == 64 * 64
 
 
-def test_batch_graph_and_autotune(rl):
+@pytest.mark.parametrize("c_supply", [1, 2])
+def test_batch_graph_and_autotune(rl, c_supply):
     """One persistent launch over uneven images, replayed from a CUDA graph,
-    equals the plain batch launch; the autotuner keeps results identical."""
+    equals the plain batch launch; the autotuner keeps results identical.
+    The Gram-column supply is fixed on both sides (the automatic choice
+    depends on how many blocks use each table set, which differs between the
+    batch plan and the single-image plans), once stored and once factored."""
     import torch
     sizes = synth.batch_sizes(6, 11, lo=(64, 64), hi=(160, 224))
     masks, ys = [], []
@@ -206,7 +210,7 @@ def test_batch_graph_and_autotune(rl):
         m = synth.recurrent_mask(h // 2, w // 2, 4, 78)
         masks.append(m)
         ys.append(synth.measure(f, m).astype(np.float32))
-    plan = rl.Plan(masks, rl.default_params(nu_max=20))
+    plan = rl.Plan(masks, rl.default_params(nu_max=20, c_supply=c_supply))
     lrs = [torch.from_numpy(y).cuda() for y in ys]
     hr_a = [torch.zeros((h, w), device="cuda") for h, w in sizes]
     hr_b = [torch.zeros((h, w), device="cuda") for h, w in sizes]
@@ -230,7 +234,7 @@ def test_batch_graph_and_autotune(rl):
     for m, y, hr in zip(masks, ys, hr_b):
         nbh, nbw = m.shape[0] // 2, m.shape[1] // 2
         blocks = np.array([0, nbw - 1, (nbh - 1) * nbw, nbh * nbw - 1, 5 * nbw + 5, (nbh // 2) * nbw + nbw // 2])
-        single = gpu_run(rl, y, m, nu_max=20)
+        single = gpu_run(rl, y, m, nu_max=20, c_supply=c_supply)
         g = hr.cpu().numpy()
         assert np.array_equal(single["hr"], g)
         ohr, tr = oracle_run(y, m, blocks=blocks, nu_max=20)
