@@ -107,15 +107,18 @@ typedef struct {
                              and stored FP32 (8 MiB per table set), one 8 KiB
                              column read per block and iteration; 2 = factored,
                              rebuilt every iteration from 16 KB of tables with
-                             no memory traffic; 0 = auto (default): stored for
-                             each table set at least 256 blocks use, the most
-                             used first, while the matrices fit in an eighth of
-                             the free device memory, factored for the others
-                             and for FP64 loops and paths 2 and 3.  1 needs the
-                             FP32 loop on path 1 (RLJSDE_ERR_UNSUPPORTED
-                             otherwise, also when auto would choose path 2 or
-                             3) and fails with RLJSDE_ERR_OUT_OF_MEMORY when the
-                             matrices do not fit.  A plan with both kinds of
+                             no memory traffic; 3 = stored for the table sets
+                             at least 256 blocks use, factored for the others
+                             (border table sets of a recurrent mask: less
+                             memory, one more kernel); 0 = auto (default):
+                             stored for every table set, the most used first,
+                             while the matrices fit in an eighth of the free
+                             device memory, factored for the rest and for FP64
+                             loops and paths 2 and 3.  1 and 3 need the FP32
+                             loop on path 1 (RLJSDE_ERR_UNSUPPORTED otherwise,
+                             also when auto would choose path 2 or 3) and fail
+                             with RLJSDE_ERR_OUT_OF_MEMORY when the matrices do
+                             not fit.  A plan with both kinds of
                              table sets runs two kernels per reconstruction;
                              the stored-C loop always runs 4 warps per CTA at
                              full occupancy (rljsde_set_launch and

@@ -252,8 +252,9 @@ int check_params(const rljsde_params *p)
         return RLJSDE_ERR_INVALID_ARG;
     if (p->pairs != 0 && p->pairs != 1) return RLJSDE_ERR_INVALID_ARG;
     if ((p->path == 2 || p->path == 3) && p->precision != 0) return RLJSDE_ERR_UNSUPPORTED;
-    if (p->c_supply < 0 || p->c_supply > 2) return RLJSDE_ERR_INVALID_ARG;
-    if (p->c_supply == 1 && (p->precision != 0 || p->path == 2 || p->path == 3)) return RLJSDE_ERR_UNSUPPORTED;
+    if (p->c_supply < 0 || p->c_supply > 3) return RLJSDE_ERR_INVALID_ARG;
+    if ((p->c_supply == 1 || p->c_supply == 3) && (p->precision != 0 || p->path == 2 || p->path == 3))
+        return RLJSDE_ERR_UNSUPPORTED;
     return RLJSDE_OK;
 }
 
@@ -406,7 +407,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         if (p->onthefly)
             for (auto &t : table_of) t = 0;
     } else {
-        if (prm->c_supply == 1) {      // the direct path has no Gram matrix to store
+        if (prm->c_supply == 1 || prm->c_supply == 3) {      // the direct path has no Gram matrix
             release(p);
             return RLJSDE_ERR_UNSUPPORTED;
         }
@@ -420,7 +421,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         }
     }
     p->n_blocks = ord;
-    if (prm->c_supply == 1 && p->onthefly) {
+    if ((prm->c_supply == 1 || prm->c_supply == 3) && p->onthefly) {
         release(p);
         return RLJSDE_ERR_UNSUPPORTED;
     }
@@ -440,13 +441,14 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     for (int g = 0; g < n_groups; ++g)
         for (int e = start[g]; e < start[g + 1]; e += kChunk) chunk_table[e / kChunk] = (uint32_t)g;
 
-    // Table sets whose Gram matrix is stored (c_supply): all of them (1), or
-    // (auto) those at least kStoredMinBlocks blocks use, the most used first,
-    // within an eighth of the free device memory.
+    // Table sets whose Gram matrix is stored (c_supply): all of them (1),
+    // those at least kStoredMinBlocks blocks use (3), or (auto) all, the most
+    // used first, within an eighth of the free device memory.
     if (!p->direct && !p->onthefly && prm->precision == 0 && prm->c_supply != 2) {
         p->cslot.assign(p->n_tables, -1);
-        if (prm->c_supply == 1) {
+        if (prm->c_supply != 0) {
             for (int t = 0; t < p->n_tables; ++t) {
+                if (prm->c_supply == 3 && count[t] < kStoredMinBlocks) continue;
                 p->cslot[t] = p->n_stored++;
                 p->n_stored_blocks += count[t];
             }
@@ -458,7 +460,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             for (int t = 0; t < p->n_tables; ++t) order[t] = t;
             std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return count[x] > count[y]; });
             for (int t : order) {
-                if (count[t] < kStoredMinBlocks || (size_t)(p->n_stored + 1) * kStoredCBytes > budget) break;
+                if ((size_t)(p->n_stored + 1) * kStoredCBytes > budget) break;
                 p->cslot[t] = p->n_stored++;
                 p->n_stored_blocks += count[t];
             }

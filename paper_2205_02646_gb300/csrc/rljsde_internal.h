@@ -113,9 +113,9 @@ static_assert(sizeof(Shortlist) == 136, "shortlist layout");
 // C_{k+32,l}.im), entry i * 32 + lane holding the two candidates that lane
 // of the FP32 loop updates in its register pair i.
 constexpr size_t kStoredCBytes = (size_t)kK * kK * 8;
-// c_supply auto stores the matrix of a table set that at least this many
-// blocks use: below that its 8 MiB saves too little per reconstruction
-// (border table sets of a recurrent mask are used by few blocks each).
+// c_supply 3 stores the matrix of a table set that at least this many blocks
+// use (border table sets of a recurrent mask are used by few blocks each);
+// the others run the factored loop in a second kernel.
 constexpr int kStoredMinBlocks = 256;
 
 }  // namespace rljsde

@@ -70,7 +70,8 @@ def test_argument_errors_before_gpu(rl):
     assert _create(rl, ok, layout=2) == 1
     assert _create(rl, ok, pairs=2) == 1
     # stored Gram matrices: FP32 loop on host table sets only
-    assert _create(rl, ok, c_supply=3) == 1
+    assert _create(rl, ok, c_supply=4) == 1
+    assert _create(rl, ok, c_supply=3, precision=1) == 8
     assert _create(rl, ok, c_supply=1, precision=1) == 8
     assert _create(rl, ok, c_supply=1, path=2) == 8
     assert _create(rl, ok, c_supply=1, path=3) == 8

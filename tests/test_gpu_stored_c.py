@@ -4,8 +4,9 @@ C_{., uv} of Eq. 14 from a matrix stored per local measurement matrix, built
 on the device in FP64 and stored FP32.  Checked against the FP64 oracle block
 by block (traces and coefficient increments included) on the 8x8-LR tile's
 144 local matrices, on the other sensor layouts and with the conjugate-pair
-update; against the factored supply at full size; and the automatic choice,
-which stores only the much-used table sets, block for block against both."""
+update; against the factored supply at full size; and the frugal choice,
+which stores only the much-used table sets and runs the others factored in a
+second kernel, block for block against both."""
 import numpy as np
 import pytest
 
@@ -86,10 +87,11 @@ def test_stored_c_agrees_with_factored_supply_at_full_size(rl):
     nb, nu = nbh * nbw, 100
     lr = torch.from_numpy(y).cuda()
     runs = {}
-    for supply in (0, 1, 2):
+    for supply in (0, 1, 2, 3):
         plan = rl.Plan(mask, rl.default_params(nu_max=nu, c_supply=supply))
         info = plan.info()
-        assert info["n_stored_c_tables"] == {0: 4, 1: info["n_tables"], 2: 0}[supply]
+        assert info["n_stored_c_tables"] == {0: 100, 1: 100, 2: 0, 3: 4}[supply]
+        assert info["n_launches"] == (2 if supply == 3 else 1)
         hr = torch.full((2 * lr_h, 2 * lr_w), float("nan"), device="cuda")
         sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
         dc = torch.zeros(nb * nu * 2, device="cuda")
@@ -98,12 +100,14 @@ def test_stored_c_agrees_with_factored_supply_at_full_size(rl):
         d = dc.view(nb, nu, 2).cpu().numpy()
         runs[supply] = (hr.cpu().numpy(), sel.view(nb, nu).cpu().numpy(), d[..., 0] + 1j * d[..., 1])
         del plan
-    # auto stores the 4 interior table sets (16,000 blocks each) and leaves
-    # the border ones (at most 128 blocks each) factored: every block's
-    # output equals that of one of the uniform supplies bit for bit
+    # auto stores all 100 table sets here, as 1 does; 3 stores the 4 interior
+    # ones (about 15,000 blocks each) and runs the border ones (at most 128
+    # blocks each) factored: every block's output equals that of one of the
+    # uniform supplies bit for bit
     hb = {s: runs[s][0].reshape(nbh, 4, nbw, 4) for s in runs}
-    eq1 = np.all(hb[0] == hb[1], axis=(1, 3))
-    eq2 = np.all(hb[0] == hb[2], axis=(1, 3))
+    assert np.array_equal(hb[0], hb[1])
+    eq1 = np.all(hb[3] == hb[1], axis=(1, 3))
+    eq2 = np.all(hb[3] == hb[2], axis=(1, 3))
     assert np.all(eq1 | eq2)
     assert (eq1 & ~eq2).sum() > nb // 2 and (eq2 & ~eq1).sum() > 0
     same = np.all(runs[1][1] == runs[2][1], axis=1)
