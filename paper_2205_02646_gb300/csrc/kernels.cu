@@ -159,6 +159,7 @@ struct Args {
 template <typename T, int MODE = 0> struct RecOf;
 template <int MODE> struct RecOf<float, MODE> { using type = RecordF32; };
 template <> struct RecOf<float, 1> { using type = RecordShortF32; };
+template <> struct RecOf<float, 17> { using type = RecordShortF32; };   // mode 1 with stored C
 template <int MODE> struct RecOf<double, MODE> { using type = Record<double>; };
 
 // Pair tables of the FP32 loop: for kap1 pair j, (cos, cos, sin, sin) of
@@ -935,6 +936,7 @@ __device__ __forceinline__ C2<float> h_of(const C2<float> *om, int k, int t)
 // an f32x2 register): re, im and -im.
 struct HalfState {
     int kc[4];
+    int coff[4], ce;                 // stored C: each candidate's float4 in a column, and which half of it
     float2 Rre[2], Rim[2], qd[2];    // slots (0, 1) and (2, 3) packed
     float2 hre[4][2], him[4][2], nhim[4][2];
 };
@@ -1026,6 +1028,14 @@ __device__ __forceinline__ void shortlist_setup(const Args &a, const RecordShort
 #pragma unroll
         for (int sl4 = 0; sl4 < 4; ++sl4) {
             st.kc[sl4] = kn[sl4];
+            {
+                // where the stored-C loop's lanes keep candidate k in a column:
+                // float4 (4 jj + 2 a + b) * 32 + 16 h + kap2, low or high half by e
+                const int k1 = kn[sl4] >> 5, k2f = kn[sl4] & 31;
+                st.coff[sl4] = (((k1 >> 1) & 3) * 4 + 2 * (k1 >> 4) + (k2f >> 4)) * 32 + 16 * ((k1 >> 3) & 1) +
+                               (k2f & 15);
+                st.ce |= (k1 & 1) << sl4;
+            }
             if (sl4 & 1) { st.Rre[sl4 >> 1].y = Rn[sl4].re; st.Rim[sl4 >> 1].y = Rn[sl4].im; }
             else { st.Rre[sl4 >> 1].x = Rn[sl4].re; st.Rim[sl4 >> 1].x = Rn[sl4].im; }
             C2<float> hk[4];
@@ -1048,15 +1058,22 @@ __device__ __forceinline__ int shortlist_iterations(const Args &a, const Shortli
 // The shortlist loop for up to two blocks (on[b]: block b is present), one
 // per half-warp.  All lanes take part in every shuffle and ballot; a half
 // whose block is absent or done only skips the update.
+// STORED: the column of C comes from the plan's stored Gram matrix cs (one
+// 16-byte load per candidate, gathered from the 8 KiB column) instead of
+// being rebuilt from the factored tables.
+template <bool STORED>
 __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF32 &rec, C2<float> *scratch,
                                                const C2<float> *om, const C2<float> *omc, const float *wt,
-                                               const WorkEntry (&we)[2], const bool (&on)[2], const int lane)
+                                               const WorkEntry (&we)[2], const bool (&on)[2], const int lane,
+                                               const float4 *cs)
 {
     const int hb = lane >> 4;
     HalfState st;
 #pragma unroll
+    st.ce = 0;
     for (int sl4 = 0; sl4 < 4; ++sl4) {
         st.kc[sl4] = 0;
+        st.coff[sl4] = 0;
         if (sl4 < 2) st.Rre[sl4] = st.Rim[sl4] = st.qd[sl4] = f2(0.f, 0.f);
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) st.hre[sl4][pr] = st.him[sl4][pr] = st.nhim[sl4][pr] = f2(0.f, 0.f);
@@ -1106,9 +1123,31 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
         const int wl = 16 * hb + (mine ? __ffs(mine) - 1 : 0);
         const float sre = st.kc[0] == bk ? st.Rre[0].x : st.kc[1] == bk ? st.Rre[0].y : st.kc[2] == bk ? st.Rre[1].x : st.Rre[1].y;
         const float sim = st.kc[0] == bk ? st.Rim[0].x : st.kc[1] == bk ? st.Rim[0].y : st.kc[2] == bk ? st.Rim[1].x : st.Rim[1].y;
+        float4 cv[4];
+        if (STORED && it < nu_h) {
+            // the candidates' entries of column bk, in flight during the bookkeeping
+            const float4 *col = cs + (size_t)(bk & (kK - 1)) * 512;
+#pragma unroll
+            for (int sl4 = 0; sl4 < 4; ++sl4) cv[sl4] = ldg_stream4(col + st.coff[sl4]);
+        }
         const float Rre = __shfl_sync(0xffffffffu, sre, wl);
         const float Rim = __shfl_sync(0xffffffffu, sim, wl);
-        if (it < nu_h) {
+        if (STORED && it < nu_h) {
+            const float invD = rec.invD[bk & (kK - 1)];
+            select_step<float>(a, om, invD, gamma, bk & (kK - 1), Rre, Rim, eta, gam, lane & 15, trow, it, u, v, g,
+                               fpix, unused_pw);
+            // Eq. 17 on the shortlist with the stored column, as the stored-C loop does
+            const C2<float> gd = {gamma * (Rre * invD), gamma * (Rim * invD)};   // as in select_step
+            const float2 ngr = f2(-gd.re, -gd.re), gi = f2(gd.im, gd.im), ngi = f2(-gd.im, -gd.im);
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                const float4 A = cv[2 * pr], B = cv[2 * pr + 1];
+                const bool ea = (st.ce >> (2 * pr)) & 1, eb = (st.ce >> (2 * pr + 1)) & 1;
+                const float2 Cre = f2(ea ? A.y : A.x, eb ? B.y : B.x), Cim = f2(ea ? A.w : A.z, eb ? B.w : B.z);
+                st.Rre[pr] = fma2(Cim, gi, fma2(Cre, ngr, st.Rre[pr]));
+                st.Rim[pr] = fma2(Cre, ngi, fma2(Cim, ngr, st.Rim[pr]));
+            }
+        } else if (!STORED && it < nu_h) {
             select_step<float>(a, om, rec.invD[bk & (kK - 1)], gamma, bk & (kK - 1), Rre, Rim, eta, gam, lane & 15,
                                trow, it, u, v, g, fpix, unused_pw);
             // Eq. 17 on the shortlist: R_k -= sum_t conj(h_t(k)) g_t G_t(uv - k), two
@@ -1183,6 +1222,7 @@ __host__ __device__ constexpr int lay_of(int mode)
 __host__ __device__ constexpr bool pairs_of(int mode) { return (mode & kModePairs) != 0; }
 __host__ __device__ constexpr bool stored_of(int mode) { return (mode & kModeStoredC) != 0; }
 __host__ __device__ constexpr bool plain_of(int mode) { return (mode & 7) == 0 || (mode & 7) == 3 || (mode & 7) == 4; }
+__host__ __device__ constexpr int learned_of(int mode) { return (mode & 7) == 1 || (mode & 7) == 2 ? (mode & 7) : 0; }
 
 template <typename T, int MODE> struct Loop;
 template <int MODE> struct Loop<float, MODE> {
@@ -1192,8 +1232,8 @@ template <int MODE> struct Loop<float, MODE> {
                                                const float *wt, const WorkEntry we, const int lane,
                                                const float4 *cs)
     {
-        if constexpr (stored_of(MODE)) {
-            // (the launch takes only chunks whose table set has a stored matrix)
+        // (a stored-C launch takes only chunks whose table set has a stored matrix)
+        if constexpr (plain_of(MODE) && stored_of(MODE)) {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
             greedy_loop_stored<lay_of(MODE), pairs_of(MODE)>(a, rec, cs, om, pt, we, lane, Y);
@@ -1201,19 +1241,20 @@ template <int MODE> struct Loop<float, MODE> {
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
             greedy_loop_f32<lay_of(MODE), pairs_of(MODE)>(a, rec, om, omc, pt, we, lane, Y);
-        } else if constexpr (MODE == 1) {
+        } else if constexpr (learned_of(MODE) == 1) {
             const Shortlist &sl = a.shortlists[we.ord];
             if (!(sl.missing <= a.max_missing)) return;
             if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, 1);
             const WorkEntry w2[2] = {we, we};
             const bool on[2] = {true, false};
-            shortlist_pair(a, rec, scratch, om, omc, wt, w2, on, lane);
+            shortlist_pair<stored_of(MODE)>(a, rec, scratch, om, omc, wt, w2, on, lane, cs);
         } else {
             const Shortlist &sl = a.shortlists[we.ord];
             if (sl.missing <= a.max_missing) return;
             C2<float> Y[8][4];
             initial_projection<float>(a, rec, scratch, omc, wt, we, lane, Y);
-            greedy_loop_f32<kLayThreeQuarter>(a, rec, om, omc, pt, we, lane, Y);
+            if constexpr (stored_of(MODE)) greedy_loop_stored<kLayThreeQuarter>(a, rec, cs, om, pt, we, lane, Y);
+            else greedy_loop_f32<kLayThreeQuarter>(a, rec, om, omc, pt, we, lane, Y);
         }
     }
 
@@ -1222,7 +1263,7 @@ template <int MODE> struct Loop<float, MODE> {
     static __device__ __forceinline__ void run_pair(const Args &a, const Rec &rec, C2<float> *scratch,
                                                     const C2<float> *om, const C2<float> *omc,
                                                     const PairTables &pt, const float *wt, const WorkEntry e0,
-                                                    const WorkEntry e1, const int lane)
+                                                    const WorkEntry e1, const int lane, const float4 *cs)
     {
         const bool r0 = e0.img >= 0 && a.shortlists[e0.ord].missing <= a.max_missing;
         const bool r1 = e1.img >= 0 && a.shortlists[e1.ord].missing <= a.max_missing;
@@ -1230,7 +1271,7 @@ template <int MODE> struct Loop<float, MODE> {
         if (a.n_restricted != nullptr && lane == 0) atomicAdd(a.n_restricted, (int)r0 + (int)r1);
         const WorkEntry w2[2] = {e0, e1};
         const bool on[2] = {r0, r1};
-        shortlist_pair(a, rec, scratch, om, omc, wt, w2, on, lane);
+        shortlist_pair<stored_of(MODE)>(a, rec, scratch, om, omc, wt, w2, on, lane, cs);
     }
 };
 template <int MODE> struct Loop<double, MODE> {
@@ -1246,7 +1287,7 @@ template <int MODE> struct Loop<double, MODE> {
     static __device__ __forceinline__ void run_pair(const Args &a, const Record<double> &rec, C2<double> *scratch,
                                                     const C2<double> *om, const C2<double> *omc,
                                                     const PairTables &pt, const double *wt, const WorkEntry e0,
-                                                    const WorkEntry e1, const int lane)
+                                                    const WorkEntry e1, const int lane, const float4 *)
     {
         if (e0.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e0, lane, nullptr);
         if (e1.img >= 0) run(a, rec, scratch, om, omc, pt, wt, e1, lane, nullptr);
@@ -1259,7 +1300,7 @@ template <int MODE> struct Loop<double, MODE> {
 template <int MODE>
 __device__ __forceinline__ bool chunk_has_work(const Args &a, const int c)
 {
-    if constexpr (MODE != 1 && MODE != 2) {
+    if constexpr (learned_of(MODE) == 0) {
         // a plan with stored and factored table sets runs them as two launches
         if (a.cfilter == 0) return true;
         const bool stored = a.cslot[a.chunk_table[c]] >= 0;
@@ -1270,7 +1311,7 @@ __device__ __forceinline__ bool chunk_has_work(const Args &a, const int c)
             const WorkEntry we = a.entries[(size_t)c * kChunk + threadIdx.x];
             if (we.img >= 0) {
                 const bool restricted = a.shortlists[we.ord].missing <= a.max_missing;
-                mine = MODE == 1 ? restricted : !restricted;
+                mine = learned_of(MODE) == 1 ? restricted : !restricted;
             }
         }
         return __syncthreads_or(mine) != 0;
@@ -1323,7 +1364,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
     __syncthreads();
 
     const uint32_t rb = (uint32_t)sizeof(Rec);
-    const unsigned char *records = MODE == 1 ? a.records_short : a.records;
+    const unsigned char *records = learned_of(MODE) == 1 ? a.records_short : a.records;
     // Per slot s: table held (held0/held1), a load in flight (bit s of
     // pending) and the mbarrier parity to wait for (bit s of parity).
     int held0 = -1, held1 = -1;
@@ -1349,18 +1390,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
             parity ^= 1u << s;
             pending &= ~(1u << s);
         }
+        const float4 *cs = nullptr;           // this chunk's stored Gram matrix, if any
+        if constexpr (stored_of(MODE)) {
+            const int cl = a.cslot[a.chunk_table[c]];
+            if (cl >= 0) cs = a.cstore + (size_t)cl * (kStoredCBytes / 16);
+        }
         if (!work) {
             // no block of this chunk in this mode
-        } else if constexpr (MODE == 1 && WARPS * 2 == kChunk) {
+        } else if constexpr (learned_of(MODE) == 1 && WARPS * 2 == kChunk) {
             const WorkEntry e0 = a.entries[(size_t)c * kChunk + warp];
             const WorkEntry e1 = a.entries[(size_t)c * kChunk + warp + WARPS];
-            Loop<T, MODE>::run_pair(a, *slot(s), scratch, om, omc, *pt, wt, e0, e1, lane);
+            Loop<T, MODE>::run_pair(a, *slot(s), scratch, om, omc, *pt, wt, e0, e1, lane, cs);
         } else {
-            const float4 *cs = nullptr;       // this chunk's stored Gram matrix, if any
-            if constexpr (stored_of(MODE)) {
-                const int cl = a.cslot[a.chunk_table[c]];
-                if (cl >= 0) cs = a.cstore + (size_t)cl * (kStoredCBytes / 16);
-            }
             for (int e = warp; e < kChunk; e += WARPS) {
                 const WorkEntry we = a.entries[(size_t)c * kChunk + e];
                 if (we.img >= 0) Loop<T, MODE>::run(a, *slot(s), scratch, om, omc, *pt, wt, we, lane, cs);
@@ -1719,7 +1760,8 @@ const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 8), RLJSDE_VARIANT(float, 4, 3, 11), RLJSDE_VARIANT(float, 4, 3, 12),
     RLJSDE_VARIANT(double, 4, 1, 8), RLJSDE_VARIANT(double, 4, 1, 11), RLJSDE_VARIANT(double, 4, 1, 12),
     RLJSDE_VARIANT(float, 4, 3, 16), RLJSDE_VARIANT(float, 4, 3, 19), RLJSDE_VARIANT(float, 4, 3, 20), RLJSDE_VARIANT(float, 4, 3, 24),
-    RLJSDE_VARIANT(float, 4, 3, 27), RLJSDE_VARIANT(float, 4, 3, 28),
+    RLJSDE_VARIANT(float, 4, 3, 27), RLJSDE_VARIANT(float, 4, 3, 28), RLJSDE_VARIANT(float, 4, 3, 17),
+    RLJSDE_VARIANT(float, 4, 3, 18),
 };
 #undef RLJSDE_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -1980,8 +2022,11 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
     a.use_nu_hat = use_nu_hat;
     a.n_restricted = n_restricted;
     // shortlist blocks first, then the full loop on the rest
-    int st = launch_mode(plan, a, 1, plan->learned_warps, plan->learned_minb, (cudaStream_t)stream);
-    if (st == RLJSDE_OK) st = launch_mode(plan, a, 2, 4, 0, (cudaStream_t)stream);
+    // with every table set's Gram matrix stored, both loops read its columns
+    const int sc = plan->n_stored > 0 && plan->n_stored == plan->n_tables ? kModeStoredC : 0;
+    const int lw = sc ? 4 : plan->learned_warps, lm = sc ? 3 : plan->learned_minb;
+    int st = launch_mode(plan, a, 1 | sc, lw, lm, (cudaStream_t)stream);
+    if (st == RLJSDE_OK) st = launch_mode(plan, a, 2 | sc, 4, 0, (cudaStream_t)stream);
     return st;
 }
 

@@ -120,8 +120,9 @@ def test_tensor_core_convolutions_match_fp64_features(rl):
             assert abs(got - fr[fi]) <= 0.02 * scale + 0.01 * abs(fr[fi]), (fi, bi, bj, got, fr[fi])
 
 
+@pytest.mark.parametrize("c_supply", [0, 2])        # Gram columns read from the stored C / rebuilt
 @pytest.mark.parametrize("seed", [1, 2])
-def test_restricted_loop_matches_oracle_with_q_zero_outside(rl, seed):
+def test_restricted_loop_matches_oracle_with_q_zero_outside(rl, seed, c_supply):
     import torch
     f, mask, y = _image(24, 24, seed)
     nbh, nbw = 12, 12
@@ -130,7 +131,8 @@ def test_restricted_loop_matches_oracle_with_q_zero_outside(rl, seed):
     rng = np.random.default_rng(seed)
     idx = np.stack([rng.choice(1024, 64, replace=False) for _ in range(nb)])
     buf = torch.from_numpy(rl.shortlist_from_indices(idx)).cuda()
-    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu, c_supply=c_supply))
+    assert (plan.info()["n_stored_c_tables"] == plan.info()["n_tables"]) == (c_supply == 0)
     lr = torch.from_numpy(y).cuda()
     hr = torch.zeros((48, 48), device="cuda")
     sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
@@ -157,14 +159,15 @@ def test_restricted_loop_matches_oracle_with_q_zero_outside(rl, seed):
     assert not res["fails"], res["fails"][:3]
 
 
-def test_shortlist_of_plain_selections_reproduces_plain_loop(rl):
+@pytest.mark.parametrize("c_supply", [0, 2])
+def test_shortlist_of_plain_selections_reproduces_plain_loop(rl, c_supply):
     """If the shortlist holds every candidate the full loop selects, the
     restricted argmax makes the same choices."""
     import torch
     f, mask, y = _image(32, 32, 4)
     nu = 40
     nb = 16 * 16
-    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu, c_supply=c_supply))
     lr = torch.from_numpy(y).cuda()
     hr = torch.zeros((64, 64), device="cuda")
     sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
@@ -214,8 +217,9 @@ def test_training_lowers_the_loss(rl):
     assert losses[-1] < 0.8 * losses[0], losses[::8]
 
 
+@pytest.mark.parametrize("c_supply", [0, 2])
 @pytest.mark.parametrize("tau", [-1.0, 0.1, 0.5, 0.97, 2.0])
-def test_mixed_fallback_matches_both_passes(rl, tau):
+def test_mixed_fallback_matches_both_passes(rl, tau, c_supply):
     """With the confidence gate between the extremes, every block is
     reconstructed either by the shortlist loop (left-out mass <= tau) or by
     the full loop (the rest), whatever the other blocks of its chunk take:
@@ -230,7 +234,7 @@ def test_mixed_fallback_matches_both_passes(rl, tau):
     idx = np.stack([rng.choice(1024, 64, replace=False) for _ in range(nb)])
     missing = rng.random(nb).astype(np.float32)
     buf = torch.from_numpy(rl.shortlist_from_indices(idx, missing=missing)).cuda()
-    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu, c_supply=c_supply))
     lr = torch.from_numpy(y).cuda()
     hr_p = torch.zeros((2 * 96, 2 * 128), device="cuda")
     plan.reconstruct(lr, hr_p)
@@ -250,7 +254,8 @@ def test_mixed_fallback_matches_both_passes(rl, tau):
     assert (d <= 1e-4).mean() >= 0.99 if d.size else True
 
 
-def test_restricted_loop_with_repeated_candidates(rl):
+@pytest.mark.parametrize("c_supply", [0, 2])
+def test_restricted_loop_with_repeated_candidates(rl, c_supply):
     """A shortlist that names some candidates twice searches the distinct
     candidates it names: the same as the oracle with q = 0 outside them."""
     import torch
@@ -265,7 +270,7 @@ def test_restricted_loop_with_repeated_candidates(rl):
         idx[b] = np.concatenate([distinct, rng.choice(distinct, 16, replace=True)])
         rng.shuffle(idx[b])
     buf = torch.from_numpy(rl.shortlist_from_indices(idx)).cuda()
-    plan = rl.Plan(mask, rl.default_params(nu_max=nu))
+    plan = rl.Plan(mask, rl.default_params(nu_max=nu, c_supply=c_supply))
     lr = torch.from_numpy(y).cuda()
     hr = torch.zeros((48, 48), device="cuda")
     sel = torch.zeros(nb * nu, dtype=torch.int16, device="cuda")
