@@ -159,7 +159,8 @@ int rljsde_plan_create_batch(rljsde_plan_t **out, int n_images, const uint8_t *c
  * Reconstruct one image: lr (device, lr_h x lr_w floats, pitch lr_pitch >= lr_w)
  * -> hr (device, 2lr_h x 2lr_w floats, pitch hr_pitch >= 2 lr_w).  Every HR
  * pixel is written.  Only for single-image plans.  Asynchronous on `stream`,
- * allocates nothing, one kernel launch.
+ * allocates nothing, one kernel launch (two when the plan stores the Gram
+ * matrices of some of its table sets only: rljsde_plan_info n_launches).
  */
 int rljsde_reconstruct(const rljsde_plan_t *plan, const float *lr, size_t lr_pitch,
                        float *hr, size_t hr_pitch, void *stream);
@@ -190,14 +191,16 @@ typedef struct {
 int rljsde_set_images(rljsde_plan_t *plan, const rljsde_image *images);
 
 /*
- * Reconstruct every image of a batch plan in ONE persistent kernel launch.
- * Reads the pointers stored by rljsde_set_images.  Asynchronous, allocates
- * nothing, launches exactly one kernel: safe to capture in a CUDA graph.
+ * Reconstruct every image of a batch plan in ONE persistent kernel launch
+ * (two as above).  Reads the pointers stored by rljsde_set_images.
+ * Asynchronous, allocates nothing, launches nothing else: safe to capture in
+ * a CUDA graph.
  */
 int rljsde_reconstruct_batch(const rljsde_plan_t *plan, void *stream);
 
-/* Launch shape of the persistent kernel: warps per CTA (4 or 8) and resident
- * CTAs per SM to launch (1..4; clamped to what fits).  0 restores defaults. */
+/* Launch shape of the persistent factored-loop kernel: warps per CTA (4 or
+ * 8) and resident CTAs per SM to launch (1..4; clamped to what fits).  0
+ * restores defaults.  The stored-C loop keeps its own shape. */
 int rljsde_set_launch(rljsde_plan_t *plan, int warps_per_cta, int ctas_per_sm);
 
 /*
