@@ -19,6 +19,7 @@
 //   output.
 // Training runs on 16x16 L-pixel patches (rows/cols [2bi - 8, 2bi + 8)), whose
 // centre features equal those of the whole-image pass.
+#include <cuda.h>                 // CUtensorMap (the encoder is fetched through the runtime)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -495,14 +496,30 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n,
 // matrices, the 8-element K groups of one 8-row group contiguous (leading
 // byte offset 128), 8-row groups 36 x 128 bytes apart (stride byte offset).
 namespace tc {
+// Implicit-GEMM 3x3 convolution (pad 1, stride 1 or 2) of 32 bfloat16
+// channels on the tensor cores.  A tile is 128 consecutive output positions
+// of one output row (MMA M).  The 3 input rows it reads (3 x 130 or 3 x 260
+// positions x 32 channels) come into shared memory by TMA (tiled tensor
+// copies; positions outside the image read as zeros), double-buffered so that
+// the next tile's rows load while this tile computes; the threads then lay
+// the 288 taps x channels of every position out as K-major core matrices
+// (the A operand) from shared memory, one thread issues 18 MMAs (K 16) into
+// 32 tensor-memory columns, and each warp reads its 32 rows back, adds the
+// bias, applies ReLU and stores bfloat16.
 constexpr int kM = 128;                              // output positions per tile (MMA M)
 constexpr int kKTot = 9 * kC;                        // 288
 constexpr uint32_t kLBO = 128;                       // next 8-element K group
 constexpr uint32_t kSBO = (kKTot / 8) * 128;         // next 8-row group: 4608
 constexpr uint32_t kABytes = (kM / 8) * kSBO;        // 73,728
 constexpr uint32_t kBBytes = (kC / 8) * kSBO;        // 18,432
-constexpr uint32_t kSmem = kABytes + kBBytes + 16;   // + mbarrier and tensor-memory address
+constexpr int kBoxCols = 130;                        // input positions per TMA box (one row)
+constexpr uint32_t kBoxBytes = kBoxCols * kC * 2;    // 8,320
+constexpr uint32_t kStripBytes = 3 * 2 * kBoxBytes;  // 3 rows of 2 boxes (stride 2): 49,920
+constexpr uint32_t kOffStrip = kABytes + kBBytes;    // 92,160
+constexpr uint32_t kOffBar = kOffStrip + 2 * kStripBytes;
+constexpr uint32_t kSmem = kOffBar + 32 + 128;       // 3 mbarriers, tensor-memory address; 128 B for alignment
 static_assert(kSmem <= 227 * 1024, "tile operands must fit in shared memory");
+static_assert(kOffStrip % 128 == 0 && kBoxBytes % 128 == 0 && kStripBytes % 128 == 0, "TMA destinations");
 // D FP32, A and B BF16, both K-major, N = 32, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
                             ((uint32_t)(kM >> 4) << 24);
@@ -547,33 +564,74 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return a | (b << 16);
 }
 
-// in: [hi][wi][32] bfloat16; out: [ho][wo][32] bfloat16 (relu(acc + b) rounded);
-// w: [32][32][9] (bfloat16-rounded), b: [32].
-__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in, const float *w, const float *bias,
-                                                         __nv_bfloat16 *out, int hi, int wi, int ho, int wo,
-                                                         int stride, int *status)
+// B of conv2 / conv3 once per weight change: w [32][32][9] (bfloat16-rounded
+// FP32) as bfloat16 core matrices (row = output channel, K group q = tap
+// q / 4, input channels 8 (q % 4) ..), kBBytes each.
+__global__ void pack_conv_kernel(const float *w, unsigned char *dst)
 {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *A = sm, *B = sm + kABytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kABytes + kBBytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kABytes + kBBytes + 8);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kC * (kKTot / 8)) return;
+    const int co = i / (kKTot / 8), q = i % (kKTot / 8);
+    const int t = q >> 2, ci0 = (q & 3) * 8;
+    const float *src = w + (co * kC + ci0) * 9 + t;          // w[co][ci][t]
+    uint4 v;
+    v.x = pack_bf16(src[0], src[9]); v.y = pack_bf16(src[18], src[27]);
+    v.z = pack_bf16(src[36], src[45]); v.w = pack_bf16(src[54], src[63]);
+    *reinterpret_cast<uint4 *>(dst + (co >> 3) * kSBO + q * kLBO + (co & 7) * 16) = v;
+}
 
-    // B: weights as bfloat16 in the core-matrix layout (row = output channel,
-    // K group q = tap q / 4, input channels 8 (q % 4) ..)
-    for (int i = tid; i < kC * (kKTot / 8); i += blockDim.x) {
-        const int co = i / (kKTot / 8), q = i % (kKTot / 8);
-        const int t = q >> 2, ci0 = (q & 3) * 8;
-        const float *src = w + (co * kC + ci0) * 9 + t;          // w[co][ci][t]
-        uint4 v;
-        v.x = pack_bf16(src[0], src[9]); v.y = pack_bf16(src[18], src[27]);
-        v.z = pack_bf16(src[36], src[45]); v.w = pack_bf16(src[54], src[63]);
-        *reinterpret_cast<uint4 *>(B + (co >> 3) * kSBO + q * kLBO + (co & 7) * 16) = v;
-    }
+// The 3 input rows of tile (oy, ox0) into the strip at `dst`: per row one
+// box of 130 positions (stride 1) or two (stride 2), starting one position
+// left of the first tap; completes on `bar` with the boxes' bytes.
+__device__ __forceinline__ void load_strip(const CUtensorMap *tm, uint32_t dst, uint32_t bar, int stride, int oy,
+                                           int ox0)
+{
+    const uint32_t row_bytes = (uint32_t)stride * kBoxBytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(3u * row_bytes)
+                 : "memory");
+    const int iy0 = stride * oy - 1, ix0 = stride * ox0 - 1;
+    for (int r = 0; r < 3; ++r)
+        for (int part = 0; part < stride; ++part)
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                         " [%0], [%1, {%2, %3, %4}], [%5];"
+                         ::"r"(dst + r * row_bytes + part * kBoxBytes), "l"(reinterpret_cast<uint64_t>(tm)),
+                         "r"(0), "r"(ix0 + part * kBoxCols), "r"(iy0 + r), "r"(bar)
+                         : "memory");
+}
+
+// in (through tmap): [hi][wi][32] bfloat16; out: [ho][wo][32] bfloat16
+// (relu(acc + b) rounded); bpack: pack_conv_kernel's B; b: [32].
+__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                         const unsigned char *bpack, const float *bias,
+                                                         __nv_bfloat16 *out, int ho, int wo, int stride, int *status)
+{
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    // TMA destinations want 128-byte alignment
+    unsigned char *sm = sm_raw + ((128u - (saddr(sm_raw) & 127u)) & 127u);
+    unsigned char *B = sm + kABytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kOffBar);     // strip full x 2, MMA done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kOffBar + 24);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t a_addr = saddr(sm), b_addr = saddr(B), strip_addr = saddr(sm + kOffStrip);
+    const uint32_t full_bar0 = saddr(&bars[0]), mma_bar = saddr(&bars[2]);   // strip k: full_bar0 + 8 k
+    const int tiles_per_row = (wo + kM - 1) / kM;
+    const long long n_tiles = (long long)ho * tiles_per_row;
+
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+        for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bars[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // the first two tiles' rows
+        for (int k = 0; k < 2; ++k) {
+            const long long tile = blockIdx.x + (long long)k * gridDim.x;
+            if (tile < n_tiles)
+                load_strip(&tmap, strip_addr + k * kStripBytes, full_bar0 + 8 * k, stride,
+                           (int)(tile / tiles_per_row), (int)(tile % tiles_per_row) * kM);
+        }
     }
+    // B: the packed weights, 18,432 bytes
+    for (int i = tid; i < (int)(kBBytes / 16); i += blockDim.x)
+        reinterpret_cast<uint4 *>(B)[i] = reinterpret_cast<const uint4 *>(bpack)[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
                      "r"(kTmemCols)
@@ -584,36 +642,55 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const uint32_t a_addr = saddr(A), b_addr = saddr(B), bar_addr = saddr(bar);
 
-    const long long total = (long long)ho * wo;
-    const long long n_tiles = (total + kM - 1) / kM;
-    uint32_t parity = 0;
-    bool failed = false;
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        // A: this thread's position, its 288 taps as bfloat16
-        const long long pos = tile * kM + tid;
-        const bool valid = pos < total;
-        const int oy = valid ? (int)(pos / wo) : 0, ox = valid ? (int)(pos % wo) : 0;
-        unsigned char *arow = A + (tid >> 3) * kSBO + (tid & 7) * 16;
+    // strip loads in flight (bit k), the same in every thread: every thread
+    // takes the same decisions from the tile indices
+    uint32_t pending = (blockIdx.x < n_tiles ? 1u : 0u) | (blockIdx.x + (long long)gridDim.x < n_tiles ? 2u : 0u);
+    uint32_t full_parity = 0, mma_parity = 0;        // bit k: phase of strip k
+    bool failed = false, mma_in_flight = false;
+    const uint32_t row_bytes = (uint32_t)stride * kBoxBytes;
+    int k = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, k ^= 1) {
+        const int oy = (int)(tile / tiles_per_row), ox0 = (int)(tile % tiles_per_row) * kM;
+        const int p = tid;                            // this thread's position in the tile
+        const bool valid = ox0 + p < wo;
+        // this tile's rows
+        const bool ok = wait_phase(full_bar0 + 8 * k, (full_parity >> k) & 1u);
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        full_parity ^= 1u << k;
+        pending &= ~(1u << k);
+        // A: the 9 taps x 32 channels of position p from the strip (tap
+        // (dy, dx) is strip row dy, position stride p + dx); the four 16-byte
+        // channel groups are visited in an order rotated by p so that the
+        // quarter-warp's reads fall in distinct bank groups
+        const uint32_t srow = strip_addr + k * kStripBytes + (uint32_t)(stride * p) * (kC * 2);
+        const uint32_t arow = a_addr + (p >> 3) * kSBO + (p & 7) * 16;
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-            const int y = stride * oy + t / 3 - 1, x = stride * ox + t % 3 - 1;
-            const bool inb = valid && y >= 0 && y < hi && x >= 0 && x < wi;
-            // the tap's 32 channels: 64 contiguous bytes, one core-matrix row per 8 channels
-            const uint4 *src = reinterpret_cast<const uint4 *>(in + (inb ? ((long long)y * wi + x) * kC : 0));
+            const uint32_t src = srow + (t / 3) * row_bytes + (t % 3) * (kC * 2);
 #pragma unroll
-            for (int cg = 0; cg < 4; ++cg) {
-                const uint4 u = inb ? src[cg] : make_uint4(0u, 0u, 0u, 0u);
-                *reinterpret_cast<uint4 *>(arow + (t * 4 + cg) * kLBO) = u;
+            for (int i = 0; i < 4; ++i) {
+                const int cg = (i + p) & 3;
+                uint4 u;
+                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w) : "r"(src + cg * 16));
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+                             ::"r"(arow + (uint32_t)(t * 4 + cg) * kLBO), "r"(u.x), "r"(u.y), "r"(u.z), "r"(u.w)
+                             : "memory");
             }
         }
         // generic-proxy writes -> tensor-core (async proxy) reads
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        __syncthreads();                              // A complete, strip k consumed
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const long long nxt = tile + 2ll * gridDim.x;  // the tile after next, into the strip just consumed
+        if (nxt < n_tiles) pending |= 1u << k;
+        mma_in_flight = true;
         if (tid == 0) {
+            if (nxt < n_tiles)
+                load_strip(&tmap, strip_addr + k * kStripBytes, full_bar0 + 8 * k, stride,
+                           (int)(nxt / tiles_per_row), (int)(nxt % tiles_per_row) * kM);
 #pragma unroll
             for (int j = 0; j < kKTot / 16; ++j) {
                 const uint64_t da = desc(a_addr + j * 2 * kLBO), db = desc(b_addr + j * 2 * kLBO);
@@ -623,12 +700,13 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in
                              : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(bar_addr)
+                         ::"r"(mma_bar)
                          : "memory");
         }
-        const bool ok = wait_phase(bar_addr, parity);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        parity ^= 1u;
+        const bool done = wait_phase(mma_bar, mma_parity);
+        if (__syncthreads_or(!done)) { failed = true; break; }
+        mma_parity ^= 1u;
+        mma_in_flight = false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // this warp's 32 accumulator rows (TMEM lanes 32 warp ..), 32 columns each
         uint32_t r[32];
@@ -638,7 +716,7 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in
                      : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (valid) {
-            uint4 *dst = reinterpret_cast<uint4 *>(out + pos * kC);
+            uint4 *dst = reinterpret_cast<uint4 *>(out + ((long long)oy * wo + ox0 + p) * kC);
 #pragma unroll
             for (int cg = 0; cg < 4; ++cg) {
                 float v[8];
@@ -651,11 +729,13 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __nv_bfloat16 *in
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        (void)lane;
     }
     if (failed) {
         if (tid == 0) atomicOr(status, 2);
-        wait_phase(bar_addr, parity);                 // let an MMA still in flight finish
+        // let copies and an MMA still in flight land before the shared memory goes away
+        for (int b = 0; b < 2; ++b)
+            if ((pending >> b) & 1u) wait_phase(full_bar0 + 8 * b, (full_parity >> b) & 1u);
+        if (mma_in_flight) wait_phase(mma_bar, mma_parity);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1258,6 +1338,7 @@ struct rljsde_net {
     float *master = nullptr, *rounded = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *w16 = nullptr;
     unsigned char *head_packed = nullptr;   // head weights for head_select_kernel (bfloat16, 599,040 B)
+    unsigned char *conv_packed = nullptr;   // conv2 and conv3 weights for conv_tc_kernel (2 x 18,432 B)
     int step = 0;
     int sm_count = 1;                    // SMs of the device the network lives on
     // training buffers, sized for `cap` samples
@@ -1302,18 +1383,50 @@ int grid_for(long long work, int threads)
     return (int)(g < 1 ? 1 : (g > 65535 * 16 ? 65535 * 16 : g));
 }
 
-// conv2 / conv3 of a whole image on the tensor cores (tc::conv_tc_kernel).
-int conv_tc(const __nv_bfloat16 *in, const float *w, const float *b, __nv_bfloat16 *out, int hi, int wi, int ho, int wo,
-            int stride,
-            int sm_count, int *status, cudaStream_t s)
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// against the driver library).
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled()
 {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// conv2 / conv3 of a whole image on the tensor cores (tc::conv_tc_kernel):
+// in [hi][wi][32] bfloat16 (256-byte aligned), bpack the packed weights.
+int conv_tc(const __nv_bfloat16 *in, const unsigned char *bpack, const float *b, __nv_bfloat16 *out, int hi, int wi,
+            int ho, int wo, int stride, int sm_count, int *status, cudaStream_t s)
+{
+    const EncodeTiled enc = encode_tiled();
+    if (!enc) return RLJSDE_ERR_CUDA;
+    // the input as a 3-D tensor (channel, column, row), boxes of 130 positions of one row
+    CUtensorMap tm;
+    const cuuint64_t dims[3] = {(cuuint64_t)kC, (cuuint64_t)wi, (cuuint64_t)hi};
+    const cuuint64_t strides[2] = {(cuuint64_t)kC * 2, (cuuint64_t)wi * kC * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kC, (cuuint32_t)tc::kBoxCols, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return RLJSDE_ERR_CUDA;
     if (cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem) !=
         cudaSuccess)
         return RLJSDE_ERR_CUDA;
-    const long long tiles = ((long long)ho * wo + tc::kM - 1) / tc::kM;
-    const long long cap = 2ll * (sm_count > 0 ? sm_count : 1);      // two 92 KB CTAs per SM
+    const long long tiles = (long long)ho * ((wo + tc::kM - 1) / tc::kM);
+    const long long cap = sm_count > 0 ? sm_count : 1;               // one 188 KB CTA per SM
     const int grid = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
-    tc::conv_tc_kernel<<<grid, 128, tc::kSmem, s>>>(in, w, b, out, hi, wi, ho, wo, stride, status);
+    tc::conv_tc_kernel<<<grid, 128, tc::kSmem, s>>>(tm, bpack, b, out, ho, wo, stride, status);
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
 
@@ -1321,6 +1434,9 @@ void refresh_bf16(rljsde_net *n, cudaStream_t s)
 {
     to_bf16_kernel<<<grid_for(kParams, 256), 256, 0, s>>>(n->master, n->w16, n->rounded, kParams);
     hd::pack_head_kernel<<<grid_for(1040 * kHeadIn, 256), 256, 0, s>>>(n->master + kWh, n->head_packed);
+    tc::pack_conv_kernel<<<grid_for(kC * (tc::kKTot / 8), 128), 128, 0, s>>>(n->rounded + kW2, n->conv_packed);
+    tc::pack_conv_kernel<<<grid_for(kC * (tc::kKTot / 8), 128), 128, 0, s>>>(n->rounded + kW3,
+                                                                             n->conv_packed + tc::kBBytes);
 }
 
 // Forward over n patches already in n->x with origins in n->origin; the
@@ -1370,8 +1486,9 @@ int propose_pass(const rljsde_plan_t *plan, const rljsde_net_t *net, const float
     conv1_image_kernel<<<gcap((long long)P, 128), 128, 0, s>>>(lr, (long long)lr_pitch, plan->d_masks, lr_h, lr_w,
                                                                r + kW1, b + kB1, a1);
     // conv2 (stride 2, onto the block grid) and conv3 on the tensor cores
-    int cst = conv_tc(a1, r + kW2, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, sms, plan->d_status, s);
-    if (cst == RLJSDE_OK) cst = conv_tc(a2, r + kW3, b + kB3, a3, nbh, nbw, nbh, nbw, 1, sms, plan->d_status, s);
+    int cst = conv_tc(a1, net->conv_packed, b + kB2, a2, lr_h, lr_w, nbh, nbw, 2, sms, plan->d_status, s);
+    if (cst == RLJSDE_OK)
+        cst = conv_tc(a2, net->conv_packed + tc::kBBytes, b + kB3, a3, nbh, nbw, nbh, nbw, 1, sms, plan->d_status, s);
     if (cst != RLJSDE_OK) return cst;
     if (cudaFuncSetAttribute(hd::head_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hd::kSmem) !=
         cudaSuccess)
@@ -1397,7 +1514,8 @@ int rljsde_net_create(rljsde_net_t **out, uint64_t seed)
     bool ok = cudaMalloc(&n->master, b) == cudaSuccess && cudaMalloc(&n->rounded, b) == cudaSuccess &&
               cudaMalloc(&n->grad, b) == cudaSuccess && cudaMalloc(&n->m, b) == cudaSuccess &&
               cudaMalloc(&n->v, b) == cudaSuccess && cudaMalloc(&n->w16, (size_t)kParams * 2) == cudaSuccess &&
-              cudaMalloc(&n->head_packed, hd::kPackedBytes) == cudaSuccess;
+              cudaMalloc(&n->head_packed, hd::kPackedBytes) == cudaSuccess &&
+              cudaMalloc(&n->conv_packed, 2 * tc::kBBytes) == cudaSuccess;
     if (!ok) { rljsde_net_destroy(n); return RLJSDE_ERR_OUT_OF_MEMORY; }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1443,6 +1561,7 @@ void rljsde_net_destroy(rljsde_net_t *n)
     free_train(n);
     cudaFree(n->master); cudaFree(n->rounded); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v); cudaFree(n->w16);
     cudaFree(n->head_packed);
+    cudaFree(n->conv_packed);
     delete n;
 }
 
