@@ -501,11 +501,12 @@ namespace tc {
 // of one output row (MMA M).  The 3 input rows it reads (3 x 130 or 3 x 260
 // positions x 32 channels) come into shared memory by TMA (tiled tensor
 // copies; positions outside the image read as zeros), double-buffered so that
-// the next tile's rows load while this tile computes; the threads then lay
-// the 288 taps x channels of every position out as K-major core matrices
+// the next tile's rows load while this tile computes; four producer warps
+// lay the 288 taps x channels of every position out as K-major core matrices
 // (the A operand) from shared memory, one thread issues 18 MMAs (K 16) into
-// 32 tensor-memory columns, and each warp reads its 32 rows back, adds the
-// bias, applies ReLU and stores bfloat16.
+// one of two 32-column accumulators, and four epilogue warps read the
+// previous tile's accumulator back, add the bias, apply ReLU and store
+// bfloat16 meanwhile.
 constexpr int kM = 128;                              // output positions per tile (MMA M)
 constexpr int kKTot = 9 * kC;                        // 288
 constexpr uint32_t kLBO = 128;                       // next 8-element K group
@@ -517,13 +518,13 @@ constexpr uint32_t kBoxBytes = kBoxCols * kC * 2;    // 8,320
 constexpr uint32_t kStripBytes = 3 * 2 * kBoxBytes;  // 3 rows of 2 boxes (stride 2): 49,920
 constexpr uint32_t kOffStrip = kABytes + kBBytes;    // 92,160
 constexpr uint32_t kOffBar = kOffStrip + 2 * kStripBytes;
-constexpr uint32_t kSmem = kOffBar + 32 + 128;       // 3 mbarriers, tensor-memory address; 128 B for alignment
+constexpr uint32_t kSmem = kOffBar + 64 + 128;       // 6 mbarriers, tensor-memory address; 128 B for alignment
 static_assert(kSmem <= 227 * 1024, "tile operands must fit in shared memory");
 static_assert(kOffStrip % 128 == 0 && kBoxBytes % 128 == 0 && kStripBytes % 128 == 0, "TMA destinations");
 // D FP32, A and B BF16, both K-major, N = 32, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
                             ((uint32_t)(kM >> 4) << 24);
-constexpr uint32_t kTmemCols = 32;
+constexpr uint32_t kTmemCols = 64;                   // two 32-column accumulators
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -599,9 +600,26 @@ __device__ __forceinline__ void load_strip(const CUtensorMap *tm, uint32_t dst, 
                          : "memory");
 }
 
+// Producer-group and epilogue-group agreement: a named barrier over the
+// group's 128 threads that also ORs a failure flag, so that every thread of
+// the group leaves its loop at the same tile.
+__device__ __forceinline__ bool group_or(const int id, const bool v)
+{
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n"
+                 " selp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "r"(id)
+                 : "memory");
+    return r != 0;
+}
+
 // in (through tmap): [hi][wi][32] bfloat16; out: [ho][wo][32] bfloat16
 // (relu(acc + b) rounded); bpack: pack_conv_kernel's B; b: [32].
-__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+// Warps 0-3 build A and issue the MMAs (thread 0 also the strip loads);
+// warps 4-7 read the accumulators back and store, one tile behind, from the
+// other of two 32-column accumulators.
+__global__ void __launch_bounds__(256, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                          const unsigned char *bpack, const float *bias,
                                                          __nv_bfloat16 *out, int ho, int wo, int stride, int *status)
 {
@@ -609,18 +627,20 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__
     // TMA destinations want 128-byte alignment
     unsigned char *sm = sm_raw + ((128u - (saddr(sm_raw) & 127u)) & 127u);
     unsigned char *B = sm + kABytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kOffBar);     // strip full x 2, MMA done
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kOffBar + 24);
+    // mbarriers: strip full x 2, accumulator full x 2 (MMA commit), accumulator empty x 2 (128 arrivals)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kOffBar + 48);
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t a_addr = saddr(sm), b_addr = saddr(B), strip_addr = saddr(sm + kOffStrip);
-    const uint32_t full_bar0 = saddr(&bars[0]), mma_bar = saddr(&bars[2]);   // strip k: full_bar0 + 8 k
+    const uint32_t full_bar0 = saddr(&bars[0]), accf_bar0 = saddr(&bars[2]), acce_bar0 = saddr(&bars[4]);
     const int tiles_per_row = (wo + kM - 1) / kM;
     const long long n_tiles = (long long)ho * tiles_per_row;
 
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bars[i])) : "memory");
+        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bars[i])) : "memory");
+        for (int i = 4; i < 6; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(saddr(&bars[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         // the first two tiles' rows
         for (int k = 0; k < 2; ++k) {
             const long long tile = blockIdx.x + (long long)k * gridDim.x;
@@ -638,104 +658,130 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // B, written by threads, read by the MMAs
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    bool failed = false;
 
-    // strip loads in flight (bit k), the same in every thread: every thread
-    // takes the same decisions from the tile indices
-    uint32_t pending = (blockIdx.x < n_tiles ? 1u : 0u) | (blockIdx.x + (long long)gridDim.x < n_tiles ? 2u : 0u);
-    uint32_t full_parity = 0, mma_parity = 0;        // bit k: phase of strip k
-    bool failed = false, mma_in_flight = false;
-    const uint32_t row_bytes = (uint32_t)stride * kBoxBytes;
-    int k = 0;
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, k ^= 1) {
-        const int oy = (int)(tile / tiles_per_row), ox0 = (int)(tile % tiles_per_row) * kM;
-        const int p = tid;                            // this thread's position in the tile
-        const bool valid = ox0 + p < wo;
-        // this tile's rows
-        const bool ok = wait_phase(full_bar0 + 8 * k, (full_parity >> k) & 1u);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        full_parity ^= 1u << k;
-        pending &= ~(1u << k);
-        // A: the 9 taps x 32 channels of position p from the strip (tap
-        // (dy, dx) is strip row dy, position stride p + dx); the four 16-byte
-        // channel groups are visited in an order rotated by p so that the
-        // quarter-warp's reads fall in distinct bank groups
-        const uint32_t srow = strip_addr + k * kStripBytes + (uint32_t)(stride * p) * (kC * 2);
-        const uint32_t arow = a_addr + (p >> 3) * kSBO + (p & 7) * 16;
+    if (warp < 4) {
+        // ---- producers: A from the strip, the MMAs, the strip loads
+        uint32_t pending = (blockIdx.x < n_tiles ? 1u : 0u) |
+                           (blockIdx.x + (long long)gridDim.x < n_tiles ? 2u : 0u);   // strip loads in flight
+        uint32_t full_parity = 0, accf_parity = 0, acce_parity = 0;
+        bool mma_in_flight = false;                   // the last tile's MMAs may still read A
+        int n = 0;                                    // tiles done by this CTA
+        const uint32_t row_bytes = (uint32_t)stride * kBoxBytes;
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++n) {
+            const int k = n & 1, b = n & 1;           // strip and accumulator of this tile
+            const int p = tid;
+            // this tile's rows, and A free (the previous tile's MMAs done)
+            bool ok = wait_phase(full_bar0 + 8 * k, (full_parity >> k) & 1u);
+            if (ok && n > 0) {
+                ok = wait_phase(accf_bar0 + 8 * (b ^ 1), (accf_parity >> (b ^ 1)) & 1u);
+                if (ok) { accf_parity ^= 1u << (b ^ 1); mma_in_flight = false; }
+            }
+            if (group_or(1, !ok)) { failed = true; break; }
+            full_parity ^= 1u << k;
+            pending &= ~(1u << k);
+            const uint32_t srow = strip_addr + k * kStripBytes + (uint32_t)(stride * p) * (kC * 2);
+            const uint32_t arow = a_addr + (p >> 3) * kSBO + (p & 7) * 16;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const uint32_t src = srow + (t / 3) * row_bytes + (t % 3) * (kC * 2);
+            for (int t = 0; t < 9; ++t) {
+                const uint32_t src = srow + (t / 3) * row_bytes + (t % 3) * (kC * 2);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int cg = (i + p) & 3;
-                uint4 u;
-                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                             : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w) : "r"(src + cg * 16));
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
-                             ::"r"(arow + (uint32_t)(t * 4 + cg) * kLBO), "r"(u.x), "r"(u.y), "r"(u.z), "r"(u.w)
+                for (int i = 0; i < 4; ++i) {
+                    const int cg = (i + p) & 3;      // rotated: the quarter-warp's reads in distinct bank groups
+                    uint4 u;
+                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                                 : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w) : "r"(src + cg * 16));
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+                                 ::"r"(arow + (uint32_t)(t * 4 + cg) * kLBO), "r"(u.x), "r"(u.y), "r"(u.z),
+                                 "r"(u.w)
+                                 : "memory");
+                }
+            }
+            // the accumulator of this tile free (its epilogue two tiles back done)
+            ok = true;
+            if (n >= 2) {
+                ok = wait_phase(acce_bar0 + 8 * b, (acce_parity >> b) & 1u);
+                if (ok) acce_parity ^= 1u << b;
+            }
+            // generic-proxy writes -> tensor-core (async proxy) reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (group_or(1, !ok)) { failed = true; break; }   // also: A complete, strip k consumed
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const long long nxt = tile + 2ll * gridDim.x;    // into the strip just consumed
+            if (nxt < n_tiles) pending |= 1u << k;
+            mma_in_flight = true;
+            if (tid == 0) {
+                if (nxt < n_tiles)
+                    load_strip(&tmap, strip_addr + k * kStripBytes, full_bar0 + 8 * k, stride,
+                               (int)(nxt / tiles_per_row), (int)(nxt % tiles_per_row) * kM);
+                const uint32_t d = tmem + (uint32_t)b * 32u;
+#pragma unroll
+                for (int j = 0; j < kKTot / 16; ++j) {
+                    const uint64_t da = desc(a_addr + j * 2 * kLBO), db = desc(b_addr + j * 2 * kLBO);
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                 ::"r"(d), "l"(da), "l"(db), "r"(kIdesc), "r"(j)
+                                 : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(accf_bar0 + 8 * b)
                              : "memory");
             }
         }
-        // generic-proxy writes -> tensor-core (async proxy) reads
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();                              // A complete, strip k consumed
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const long long nxt = tile + 2ll * gridDim.x;  // the tile after next, into the strip just consumed
-        if (nxt < n_tiles) pending |= 1u << k;
-        mma_in_flight = true;
-        if (tid == 0) {
-            if (nxt < n_tiles)
-                load_strip(&tmap, strip_addr + k * kStripBytes, full_bar0 + 8 * k, stride,
-                           (int)(nxt / tiles_per_row), (int)(nxt % tiles_per_row) * kM);
-#pragma unroll
-            for (int j = 0; j < kKTot / 16; ++j) {
-                const uint64_t da = desc(a_addr + j * 2 * kLBO), db = desc(b_addr + j * 2 * kLBO);
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                             ::"r"(tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(j)
-                             : "memory");
+        if (failed) {
+            if (tid == 0) atomicOr(status, 2);
+            // let copies and MMAs still in flight land before the shared memory goes away
+            for (int k = 0; k < 2; ++k)
+                if ((pending >> k) & 1u) wait_phase(full_bar0 + 8 * k, (full_parity >> k) & 1u);
+            if (mma_in_flight) {                      // the previous tile's MMAs, into the other accumulator
+                const int b = (n & 1) ^ 1;
+                wait_phase(accf_bar0 + 8 * b, (accf_parity >> b) & 1u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(mma_bar)
+        }
+    } else {
+        // ---- epilogue: accumulator rows 32 (warp - 4) .. of each tile, one tile behind
+        const int q = warp - 4, row = q * 32 + (tid & 31);
+        float bv[kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) bv[c] = bias[c];
+        uint32_t accf_parity = 0;
+        int n = 0;
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++n) {
+            const int b = n & 1;
+            const bool ok = wait_phase(accf_bar0 + 8 * b, (accf_parity >> b) & 1u);
+            if (group_or(2, !ok)) { failed = true; break; }
+            accf_parity ^= 1u << b;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t r[32];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                         : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 32u)
                          : "memory");
-        }
-        const bool done = wait_phase(mma_bar, mma_parity);
-        if (__syncthreads_or(!done)) { failed = true; break; }
-        mma_parity ^= 1u;
-        mma_in_flight = false;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // this warp's 32 accumulator rows (TMEM lanes 32 warp ..), 32 columns each
-        uint32_t r[32];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                     : "r"(tmem + ((uint32_t)(warp * 32) << 16))
-                     : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (valid) {
-            uint4 *dst = reinterpret_cast<uint4 *>(out + ((long long)oy * wo + ox0 + p) * kC);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar0 + 8 * b) : "memory");
+            const int oy = (int)(tile / tiles_per_row), ox = (int)(tile % tiles_per_row) * kM + row;
+            if (ox < wo) {
+                uint4 *dst = reinterpret_cast<uint4 *>(out + ((long long)oy * wo + ox) * kC);
 #pragma unroll
-            for (int cg = 0; cg < 4; ++cg) {
-                float v[8];
+                for (int cg = 0; cg < 4; ++cg) {
+                    float v[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = fmaxf(__uint_as_float(r[cg * 8 + e]) + bias[cg * 8 + e], 0.f);
-                uint4 u;
-                u.x = pack_bf16(v[0], v[1]); u.y = pack_bf16(v[2], v[3]);
-                u.z = pack_bf16(v[4], v[5]); u.w = pack_bf16(v[6], v[7]);
-                dst[cg] = u;
+                    for (int e = 0; e < 8; ++e) v[e] = fmaxf(__uint_as_float(r[cg * 8 + e]) + bv[cg * 8 + e], 0.f);
+                    uint4 u;
+                    u.x = pack_bf16(v[0], v[1]); u.y = pack_bf16(v[2], v[3]);
+                    u.z = pack_bf16(v[4], v[5]); u.w = pack_bf16(v[6], v[7]);
+                    dst[cg] = u;
+                }
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    }
-    if (failed) {
-        if (tid == 0) atomicOr(status, 2);
-        // let copies and an MMA still in flight land before the shared memory goes away
-        for (int b = 0; b < 2; ++b)
-            if ((pending >> b) & 1u) wait_phase(full_bar0 + 8 * b, (full_parity >> b) & 1u);
-        if (mma_in_flight) wait_phase(mma_bar, mma_parity);
+        if (failed && (tid & 127) == 0) atomicOr(status, 2);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1426,7 +1472,7 @@ int conv_tc(const __nv_bfloat16 *in, const unsigned char *bpack, const float *b,
     const long long tiles = (long long)ho * ((wo + tc::kM - 1) / tc::kM);
     const long long cap = sm_count > 0 ? sm_count : 1;               // one 188 KB CTA per SM
     const int grid = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
-    tc::conv_tc_kernel<<<grid, 128, tc::kSmem, s>>>(tm, bpack, b, out, ho, wo, stride, status);
+    tc::conv_tc_kernel<<<grid, 256, tc::kSmem, s>>>(tm, bpack, b, out, ho, wo, stride, status);
     return cudaGetLastError() == cudaSuccess ? RLJSDE_OK : RLJSDE_ERR_CUDA;
 }
 
