@@ -114,11 +114,14 @@ typedef struct {
                              stored for every table set, the most used first,
                              while the matrices fit in an eighth of the free
                              device memory, factored for the rest and for FP64
-                             loops and paths 2 and 3.  1 and 3 need the FP32
-                             loop on path 1 (RLJSDE_ERR_UNSUPPORTED otherwise,
-                             also when auto would choose path 2 or 3) and fail
-                             with RLJSDE_ERR_OUT_OF_MEMORY when the matrices do
-                             not fit.  A plan with both kinds of
+                             loops, paths 2 and 3 and frequency weights with a
+                             zero (the stored loop's state is sqrt(q / D) R,
+                             which cannot hold R where q is 0).  1 and 3 need
+                             the FP32 loop on path 1 and q > 0 wherever it
+                             counts (RLJSDE_ERR_UNSUPPORTED otherwise, also
+                             when auto would choose path 2 or 3) and fail with
+                             RLJSDE_ERR_OUT_OF_MEMORY when the matrices do not
+                             fit.  A plan with both kinds of
                              table sets runs two kernels per reconstruction;
                              the stored-C loop always runs 4 warps per CTA at
                              full occupancy (rljsde_set_launch and

@@ -128,7 +128,7 @@ struct Args {
     const unsigned char *records;
     uint32_t record_bytes;
     const unsigned char *records_short;    // RecordShortF32 per table (shortlist loop)
-    const float4 *cstore;                  // stored Gram matrices (c_supply), kStoredCBytes each
+    const float4 *cstore;                  // stored Gram matrices (c_supply), kStoredTableBytes each
     const int *cslot;                      // per table set: its stored matrix, or -1 (factored)
     int cfilter;                           // chunks this launch takes: 0 all, 1 those whose table set
                                            // has a stored matrix, 2 the others
@@ -744,17 +744,26 @@ __device__ __forceinline__ void greedy_loop_f32(const Args &a, const RecordF32 &
 
 // ----------------------------------------------- stored-C (paper) loop --
 // The iteration of Eqs. 11-17 in the paper's recurrent form (Table I): the
-// projected residual R itself is the loop state, and Eq. 17 subtracts
-// gamma delta times the column C_{., uv} of the Gram matrix (Eq. 14) stored
-// for the block's local measurement matrix: 8 KiB read per iteration, one
-// float4 per lane and register pair, 512 contiguous bytes per warp load.
-// R^0 comes from the same factored initial projection as the other loops,
-// and the scores, argmax and bookkeeping are the factored loop's.
+// projected residual is the loop state, scaled per candidate as R'_k = s_k
+// R_k with s_k = sqrt(q_k / D_k) so that the score of Eq. 11 is |R'_k|^2,
+// and Eq. 17 subtracts gamma delta times the column of the stored Gram
+// matrix (Eq. 14, rows scaled the same way) of the block's local
+// measurement matrix: 8 KiB read per iteration, one float4 per lane and
+// register pair, 512 contiguous bytes per warp load; delta = R'_uv / (s_uv
+// D_uv) (Eq. 16) with the stored 1 / (s_uv D_uv).  R^0 comes from the same
+// factored initial projection as the other loops, and the argmax and the
+// bookkeeping are the factored loop's.
 __device__ __forceinline__ float4 ldg_stream4(const float4 *p)
 {
     float4 v;
     asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ldg_stream1(const float *p)
+{
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 
@@ -788,13 +797,14 @@ __device__ __forceinline__ void keep_slot(const float s, const int i, float &bs,
     if (s > bs) { bs = s; bi = i; }
 }
 
-__device__ __forceinline__ void score_pair_slot(const RecordF32 &rec, const CP (&R)[4], const int h, const int jj,
-                                                const int k2, float &bs0, int &bi0, float &bs1, int &bi1)
+// The state is R'_k = s_k R_k with s_k = sqrt(q_k / D_k), so the score of
+// Eq. 11 is |R'_k|^2.
+__device__ __forceinline__ float2 norm2(const CP r) { return fma2(r.im, r.im, mul2(r.re, r.re)); }
+
+__device__ __forceinline__ void score_pair_slot(const CP (&R)[4], const int jj, float &bs0, int &bi0, float &bs1,
+                                                int &bi1)
 {
-    const float4 q0 = lds4(rec.qDP[4 * h + jj][0][k2]);
-    const float4 q1 = lds4(rec.qDP[4 * h + jj][1][k2]);
-    const float2 s00 = energy(f2(q0.x, q0.y), R[0]), s01 = energy(f2(q0.z, q0.w), R[1]);
-    const float2 s10 = energy(f2(q1.x, q1.y), R[2]), s11 = energy(f2(q1.z, q1.w), R[3]);
+    const float2 s00 = norm2(R[0]), s01 = norm2(R[1]), s10 = norm2(R[2]), s11 = norm2(R[3]);
     keep_slot(s00.x, 4 * jj + 0, bs0, bi0);
     keep_slot(s01.x, 4 * jj + 1, bs0, bi0);
     keep_slot(s00.y, 4 * jj + 2, bs0, bi0);
@@ -869,6 +879,18 @@ __device__ __forceinline__ void greedy_loop_stored(const Args &a, const RecordF3
             Yj[t] = {f2(Y0[2 * jj][t].re, Y0[2 * jj + 1][t].re), f2(Y0[2 * jj][t].im, Y0[2 * jj + 1][t].im)};
         state_to_R<LAY>(a, Yj, h, jj, k2, e1c, e1s, e1n, pt, R[jj]);
     }
+    {
+        // R' = s R, the row scales stored after the columns in the same lane order
+        const float4 *sc = cs + kStoredScaleOff + lane;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float4 w = ldg_stream4(sc + 32 * i);
+            CP &r = R[i >> 2][i & 3];
+            r.re = mul2(r.re, f2(w.x, w.y));
+            r.im = mul2(r.im, f2(w.z, w.w));
+        }
+    }
+    const float *invd = reinterpret_cast<const float *>(cs + kStoredInvDOff);   // 1 / (s_l D_l)
     const float gamma = (float)a.gamma;
     const int eta = kOff + ((lane >> 2) & 3), gam = kOff + (lane & 3);
     float fpix = 0.f, pw = 0.f;
@@ -880,7 +902,7 @@ __device__ __forceinline__ void greedy_loop_stored(const Args &a, const RecordF3
         float bs0 = -1.f, bs1 = -1.f;
         int bi0 = 0, bi1 = 0;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) score_pair_slot(rec, R[jj], h, jj, k2, bs0, bi0, bs1, bi1);
+        for (int jj = 0; jj < 4; ++jj) score_pair_slot(R[jj], jj, bs0, bi0, bs1, bi1);
         if (bs1 > bs0) { bs0 = bs1; bi0 = bi1 + 16; }
         float bs = bs0;
         // slot -> k: a = slot >> 4, jj = (slot >> 2) & 3, e = (slot >> 1) & 1, b = slot & 1
@@ -889,13 +911,13 @@ __device__ __forceinline__ void greedy_loop_stored(const Args &a, const RecordF3
         const bool more = it + 1 < a.nu_max;
         float4 col[16];
         if (more) load_column(cs, bk, lane, col);      // in flight during the bookkeeping
+        const float invD = ldg_stream1(invd + bk);
         const int wl = (bk & 15) + ((bk >> 5) & 8) * 2;
         const int slot = ((bk >> 9) << 4) | (((bk >> 6) & 3) << 2) | (((bk >> 5) & 1) << 1) | ((bk >> 4) & 1);
         float mre, mim;
         r_at_slot(R, slot, mre, mim);
         const float Rre = __shfl_sync(0xffffffffu, mre, wl);
         const float Rim = __shfl_sync(0xffffffffu, mim, wl);
-        const float invD = rec.invD[bk];
         select_step<float, LAY, PAIRS>(a, om, invD, gamma, bk, Rre, Rim, eta, gam, lane, trow, it, u, v, g, fpix,
                                        pw);
         if (more) {
@@ -1069,8 +1091,8 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
 {
     const int hb = lane >> 4;
     HalfState st;
-#pragma unroll
     st.ce = 0;
+#pragma unroll
     for (int sl4 = 0; sl4 < 4; ++sl4) {
         st.kc[sl4] = 0;
         st.coff[sl4] = 0;
@@ -1086,6 +1108,21 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
             shortlist_setup(a, rec, scratch, om, omc, wt, we[b], sl, lane, b, st);
             nu[b] = shortlist_iterations(a, sl);
         }
+    const float *invd = nullptr;
+    if constexpr (STORED) {
+        // the stored columns' scaled state R'_k = s_k R_k, its score |R'_k|^2
+        // (q / D folded into s), and 1 / (s_uv D_uv) for delta
+        const float4 *sc = cs + kStoredScaleOff;
+#pragma unroll
+        for (int sl4 = 0; sl4 < 4; ++sl4) {
+            const float4 w = ldg_stream4(sc + st.coff[sl4]);
+            const float sk = ((st.ce >> sl4) & 1) ? w.y : w.x;
+            if (sl4 & 1) { st.Rre[sl4 >> 1].y *= sk; st.Rim[sl4 >> 1].y *= sk; }
+            else { st.Rre[sl4 >> 1].x *= sk; st.Rim[sl4 >> 1].x *= sk; }
+        }
+        st.qd[0] = st.qd[1] = f2(1.f, 1.f);
+        invd = reinterpret_cast<const float *>(cs + kStoredInvDOff);
+    }
     const int nu_h = hb == 0 ? nu[0] : nu[1];
     const int numax = nu[0] > nu[1] ? nu[0] : nu[1];
     const WorkEntry me = hb == 0 ? we[0] : we[1];
@@ -1100,8 +1137,12 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
         // largest by warp reductions over each half's inputs (non-negative,
         // so the bits order like the values), then the smallest index among
         // the candidates holding it
-        const float2 sc01 = mul2(st.qd[0], fma2(st.Rim[0], st.Rim[0], mul2(st.Rre[0], st.Rre[0])));
-        const float2 sc23 = mul2(st.qd[1], fma2(st.Rim[1], st.Rim[1], mul2(st.Rre[1], st.Rre[1])));
+        float2 sc01 = fma2(st.Rim[0], st.Rim[0], mul2(st.Rre[0], st.Rre[0]));
+        float2 sc23 = fma2(st.Rim[1], st.Rim[1], mul2(st.Rre[1], st.Rre[1]));
+        if constexpr (!STORED) {
+            sc01 = mul2(st.qd[0], sc01);
+            sc23 = mul2(st.qd[1], sc23);
+        }
         const unsigned sb[4] = {__float_as_uint(sc01.x), __float_as_uint(sc01.y), __float_as_uint(sc23.x),
                                 __float_as_uint(sc23.y)};
         int bk;
@@ -1133,7 +1174,7 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
         const float Rre = __shfl_sync(0xffffffffu, sre, wl);
         const float Rim = __shfl_sync(0xffffffffu, sim, wl);
         if (STORED && it < nu_h) {
-            const float invD = rec.invD[bk & (kK - 1)];
+            const float invD = ldg_stream1(invd + (bk & (kK - 1)));
             select_step<float>(a, om, invD, gamma, bk & (kK - 1), Rre, Rim, eta, gam, lane & 15, trow, it, u, v, g,
                                fpix, unused_pw);
             // Eq. 17 on the shortlist with the stored column, as the stored-C loop does
@@ -1393,7 +1434,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) recurrent_kernel(const Args 
         const float4 *cs = nullptr;           // this chunk's stored Gram matrix, if any
         if constexpr (stored_of(MODE)) {
             const int cl = a.cslot[a.chunk_table[c]];
-            if (cl >= 0) cs = a.cstore + (size_t)cl * (kStoredCBytes / 16);
+            if (cl >= 0) cs = a.cstore + (size_t)cl * (kStoredTableBytes / 16);
         }
         if (!work) {
             // no block of this chunk in this mode
@@ -1845,11 +1886,12 @@ int launch_mode(const rljsde_plan *p, const Args &a, int mode, int warps, int mi
 }
 
 // Stored Gram matrix (c_supply) of Eq. 14 in the factored form of the
-// tables, C_{k,l} = sum_t conj(h_t(k)) h_t(l) G_t((l - k) mod 16), evaluated
-// in FP64 from the FP64 G_t and rounded to FP32 once, in the stored-C loop's
-// read order (float4 i * 32 + lane of column l: the candidates of lane's
-// register pair i).  One CTA per (column, stored table set), one thread per
-// float4.
+// tables, C_{k,l} = sum_t conj(h_t(k)) h_t(l) G_t((l - k) mod 16), each row
+// scaled by s_k = sqrt(q_k / D_k) (the stored-C loop's state is s R),
+// evaluated in FP64 from the FP64 tables and rounded to FP32 once, in the
+// loop's read order (float4 i * 32 + lane of column l: the candidates of
+// lane's register pair i).  One CTA per (column, stored table set), one
+// thread per float4.
 __device__ __forceinline__ C2<double> h64(const double2 *om, const uint32_t slot_ap, const int t, const int k1,
                                           const int k2)
 {
@@ -1865,22 +1907,29 @@ __device__ __forceinline__ C2<double> h64(const double2 *om, const uint32_t slot
     return z;
 }
 
+// The candidate k of float4 i * 32 + lane of a stored column (low half; the
+// high half holds k + 32).
+__device__ __forceinline__ int stored_k(const int i, const int lane)
+{
+    const int jj = i >> 2, qa = (i >> 1) & 1, qb = i & 1;
+    return (8 * (lane >> 4) + 2 * jj + 16 * qa) * kW + (lane & 15) + 16 * qb;
+}
+
 __global__ void __launch_bounds__(512) build_c_kernel(const double *g64, const Consts *consts,
                                                       const uint32_t slot_ap, float4 *out)
 {
     __shared__ double2 G[4][256];
     __shared__ double2 om[32];
     const int l = blockIdx.x, tab = blockIdx.y;
-    const double *src = g64 + (size_t)tab * 2048;
+    const double *src = g64 + (size_t)tab * kStoredBuildDoubles;
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) G[i >> 8][i & 255] = make_double2(src[2 * i], src[2 * i + 1]);
     if (threadIdx.x < 32) om[threadIdx.x] = make_double2(consts->om64[2 * threadIdx.x], consts->om64[2 * threadIdx.x + 1]);
     __syncthreads();
     const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int jj = i >> 2, qa = (i >> 1) & 1, qb = i & 1;
-    const int l1 = l >> 5, l2 = l & 31, k2 = (lane & 15) + 16 * qb;
+    const int l1 = l >> 5, l2 = l & 31;
     float re[2], im[2];
     for (int e = 0; e < 2; ++e) {
-        const int k1 = 8 * (lane >> 4) + 2 * jj + e + 16 * qa;
+        const int k = stored_k(i, lane) + kW * e, k1 = k >> 5, k2 = k & 31;
         const int d = ((l1 - k1) & 15) * 16 + ((l2 - k2) & 15);
         double cre = 0.0, cim = 0.0;
         for (int t = 0; t < 4; ++t) {
@@ -1890,10 +1939,29 @@ __global__ void __launch_bounds__(512) build_c_kernel(const double *g64, const C
             cre += z.re * gt.x - z.im * gt.y;
             cim += z.re * gt.y + z.im * gt.x;
         }
-        re[e] = (float)cre;
-        im[e] = (float)cim;
+        const double sk = sqrt(src[2048 + k]);
+        re[e] = (float)(sk * cre);
+        im[e] = (float)(sk * cim);
     }
-    out[((size_t)tab * kK + l) * 512 + threadIdx.x] = make_float4(re[0], re[1], im[0], im[1]);
+    out[(size_t)tab * (kStoredTableBytes / 16) + (size_t)l * 512 + threadIdx.x] =
+        make_float4(re[0], re[1], im[0], im[1]);
+}
+
+// The row scales s_k in the lane order and 1 / (s_l D_l) of each stored
+// table set; one CTA of 512 threads per table set.
+__global__ void __launch_bounds__(512) build_c_scales_kernel(const double *g64, float4 *out)
+{
+    const int tab = blockIdx.x;
+    const double *src = g64 + (size_t)tab * kStoredBuildDoubles;
+    float4 *base = out + (size_t)tab * (kStoredTableBytes / 16);
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31, k = stored_k(i, lane);
+    const float s0 = (float)sqrt(src[2048 + k]), s1 = (float)sqrt(src[2048 + k + kW]);
+    base[kStoredScaleOff + threadIdx.x] = make_float4(s0, s1, s0, s1);
+    float *invd = reinterpret_cast<float *>(base + kStoredInvDOff);
+    for (int l = threadIdx.x; l < kK; l += blockDim.x) {
+        const double sl = sqrt(src[2048 + l]), invD = src[2048 + kK + l];
+        invd[l] = sl > 0.0 ? (float)(invD / sl) : 0.f;
+    }
 }
 
 }  // namespace
@@ -1903,6 +1971,7 @@ int build_stored_c(rljsde_plan *p, const double *d_g64)
     if (!p->d_cstore || p->n_stored < 1 || p->n_stored > 65535) return RLJSDE_ERR_INVALID_ARG;
     build_c_kernel<<<dim3(kK, p->n_stored), 512>>>(d_g64, p->d_consts, p->slot_ap,
                                                   static_cast<float4 *>(p->d_cstore));
+    build_c_scales_kernel<<<p->n_stored, 512>>>(d_g64, static_cast<float4 *>(p->d_cstore));
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return RLJSDE_ERR_CUDA;
     return RLJSDE_OK;
 }

@@ -175,12 +175,17 @@ void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t
 {
     static thread_local Tables T;
     build_tables(key, w, r32, slot_ap, T);
-    if (g64)     // FP64 G_t for the stored Gram matrix: [t][d] as (re, im)
+    if (g64) {   // FP64 tables for the stored Gram matrix: G_t [t][d] as (re, im), q/D, 1/D
         for (int t = 0; t < 4; ++t)
             for (int d = 0; d < 256; ++d) {
                 g64[(t * 256 + d) * 2] = T.Gre[t][d];
                 g64[(t * 256 + d) * 2 + 1] = T.Gim[t][d];
             }
+        for (int k = 0; k < kK; ++k) {
+            g64[2048 + k] = pair_hidden(pairs, k) ? 0.0 : inv_or_zero(q[k], T.D[k]);
+            g64[2048 + kK + k] = inv_or_zero(1.0, T.D[k]);
+        }
+    }
     for (int d = 0; d < 256; ++d) {
         float *a = sh->G01[d], *b = sh->G23[d];
         a[0] = (float)T.Gre[0][d]; a[1] = (float)T.Gre[1][d]; a[2] = (float)T.Gim[0][d]; a[3] = (float)T.Gim[1][d];
@@ -348,6 +353,16 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     p->slot_ap = slot_ap;
     p->n_apertures = n_ap;
     frequency_weight(*prm, p->q);
+    // The stored-C loop folds q_k / D_k into its state (R'_k = sqrt(q_k / D_k)
+    // R_k), which loses R_k where q_k = 0 although the argmax may still pick
+    // k (every score 0): such a q keeps the factored loop.
+    bool foldable = true;
+    for (int k = 0; k < kK; ++k)
+        if (!pair_hidden(prm->pairs != 0, k) && !(p->q[k] > 0.0)) foldable = false;
+    if (!foldable && (prm->c_supply == 1 || prm->c_supply == 3)) {
+        release(p);
+        return RLJSDE_ERR_UNSUPPORTED;
+    }
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
         release(p);
@@ -444,7 +459,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
     // Table sets whose Gram matrix is stored (c_supply): all of them (1),
     // those at least kStoredMinBlocks blocks use (3), or (auto) all, the most
     // used first, within an eighth of the free device memory.
-    if (!p->direct && !p->onthefly && prm->precision == 0 && prm->c_supply != 2) {
+    if (!p->direct && !p->onthefly && prm->precision == 0 && prm->c_supply != 2 && foldable) {
         p->cslot.assign(p->n_tables, -1);
         if (prm->c_supply != 0) {
             for (int t = 0; t < p->n_tables; ++t) {
@@ -460,7 +475,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
             for (int t = 0; t < p->n_tables; ++t) order[t] = t;
             std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return count[x] > count[y]; });
             for (int t : order) {
-                if ((size_t)(p->n_stored + 1) * kStoredCBytes > budget) break;
+                if ((size_t)(p->n_stored + 1) * kStoredTableBytes > budget) break;
                 p->cslot[t] = p->n_stored++;
                 p->n_stored_blocks += count[t];
             }
@@ -502,7 +517,7 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
         try {
             host.resize(p->record_bytes * (size_t)p->n_tables);
             if (!prm->precision) host_short.resize(sizeof(RecordShortF32) * (size_t)p->n_tables);
-            if (p->n_stored) g64.resize((size_t)p->n_stored * 2048);
+            if (p->n_stored) g64.resize((size_t)p->n_stored * kStoredBuildDoubles);
         } catch (...) {
             st = RLJSDE_ERR_OUT_OF_MEMORY;
         }
@@ -517,15 +532,16 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
                     build_record32(key, w64, r32, slot_ap, prm->pairs != 0, p->q,
                                    (RecordF32 *)(host.data() + p->record_bytes * t),
                                    (RecordShortF32 *)(host_short.data() + sizeof(RecordShortF32) * t),
-                                   p->n_stored && p->cslot[t] >= 0 ? g64.data() + (size_t)2048 * p->cslot[t]
-                                                                   : nullptr);
+                                   p->n_stored && p->cslot[t] >= 0
+                                       ? g64.data() + (size_t)kStoredBuildDoubles * p->cslot[t]
+                                       : nullptr);
             }
             st = upload(&p->d_records, host.data(), host.size());
             if (!st && !prm->precision) st = upload(&p->d_records_short, host_short.data(), host_short.size());
             if (!st && p->n_stored) {
                 // the Gram matrices (Eq. 14) of the stored table sets, built on the device
                 double *d_g64 = nullptr;
-                p->cstore_bytes = kStoredCBytes * (size_t)p->n_stored;
+                p->cstore_bytes = kStoredTableBytes * (size_t)p->n_stored;
                 if (cudaMalloc(&p->d_cstore, p->cstore_bytes) != cudaSuccess) {
                     p->d_cstore = nullptr;
                     cudaGetLastError();

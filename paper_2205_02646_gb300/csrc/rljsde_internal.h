@@ -108,11 +108,20 @@ struct Shortlist {
 };
 static_assert(sizeof(Shortlist) == 136, "shortlist layout");
 
-// Stored Gram matrix of one table set (c_supply): 1024 columns of 8 KiB,
-// each as 16 x 32 float4 = (C_{k,l}.re, C_{k+32,l}.re, C_{k,l}.im,
-// C_{k+32,l}.im), entry i * 32 + lane holding the two candidates that lane
-// of the FP32 loop updates in its register pair i.
-constexpr size_t kStoredCBytes = (size_t)kK * kK * 8;
+// Stored Gram matrix of one table set (c_supply), the stored-C loop's
+// state being R'_k = s_k R_k with s_k = sqrt(q_k / D_k), so that the score
+// of Eq. 11 is |R'_k|^2:
+//   C'_{k,l} = s_k C_{k,l}: 1024 columns of 8 KiB, each as 16 x 32 float4
+//     (C'_{k,l}.re, C'_{k+32,l}.re, C'_{k,l}.im, C'_{k+32,l}.im), entry
+//     i * 32 + lane holding the two candidates that lane of the FP32 loop
+//     updates in its register pair i;
+//   then s_k in the same lane order, as float4 (s_k, s_k+32, s_k, s_k+32);
+//   then 1 / (s_l D_l) by linear l (0 where s_l D_l is 0), so that
+//     delta = R_uv / D_uv = R'_uv / (s_uv D_uv) (Eq. 16).
+constexpr size_t kStoredColsBytes = (size_t)kK * kK * 8;
+constexpr size_t kStoredTableBytes = kStoredColsBytes + 8192 + 4096;
+constexpr size_t kStoredScaleOff = kStoredColsBytes / 16;          // in float4
+constexpr size_t kStoredInvDOff = kStoredColsBytes / 16 + 512;     // in float4
 // c_supply 3 stores the matrix of a table set that at least this many blocks
 // use (border table sets of a recurrent mask are used by few blocks each);
 // the others run the factored loop in a second kernel.
@@ -148,7 +157,7 @@ struct rljsde_plan {
     int n_stored_blocks = 0;          // blocks that use them
     std::vector<int> cslot;           // per table set: its stored matrix, or -1 (factored)
     int *d_cslot = nullptr;
-    void *d_cstore = nullptr;         // n_stored x kStoredCBytes, in the stored-C loop's read order
+    void *d_cstore = nullptr;         // n_stored x kStoredTableBytes, in the stored-C loop's read order
     size_t cstore_bytes = 0;
     rljsde::WorkEntry *d_entries = nullptr;
     uint32_t *d_chunk_table = nullptr;
@@ -166,9 +175,10 @@ struct rljsde_plan {
 namespace rljsde {
 // Implemented in kernels.cu.
 int choose_launch(rljsde_plan *plan, int warps, int ctas_per_sm);
-// Fill plan->d_cstore from the FP64 G_t of the stored table sets (device,
-// in stored order, per table 4 x 256 x (re, im) doubles, t-major);
-// synchronous.
+// Fill plan->d_cstore from FP64 tables of the stored table sets (device, in
+// stored order, kStoredBuildDoubles per table: G_t as 4 x 256 x (re, im),
+// t-major, then q_k / D_k and 1 / D_k by linear k); synchronous.
+constexpr int kStoredBuildDoubles = 2048 + 2 * kK;
 int build_stored_c(rljsde_plan *plan, const double *d_g64);
 const char *last_cuda_error();
 }  // namespace rljsde

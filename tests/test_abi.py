@@ -72,6 +72,8 @@ def test_argument_errors_before_gpu(rl):
     # stored Gram matrices: FP32 loop on host table sets only
     assert _create(rl, ok, c_supply=4) == 1
     assert _create(rl, ok, c_supply=3, precision=1) == 8
+    qz = np.ones(1024); qz[5] = 0.0
+    assert _create(rl, ok, c_supply=1, q_table=qz) == 8            # q = 0 somewhere: factored loop only
     assert _create(rl, ok, c_supply=1, precision=1) == 8
     assert _create(rl, ok, c_supply=1, path=2) == 8
     assert _create(rl, ok, c_supply=1, path=3) == 8

@@ -85,14 +85,17 @@ def test_whole_image_shortlists_match_patch_logits(rl):
         assert abs(nu_frac[bi * nbw + bj] - zb[1024]) < 0.05 * (1 + abs(zb[1024]))
 
 
-def test_tensor_core_convolutions_match_fp64_features(rl):
+@pytest.mark.parametrize("shape", [(40, 56), (36, 560)])
+def test_tensor_core_convolutions_match_fp64_features(rl, shape):
     """conv2 and conv3 of the whole-image pass run on the tensor cores
-    (tcgen05, bfloat16 taps, FP32 accumulation in tensor memory).  A head
-    whose iteration row selects one feature turns each block's iteration
-    output into that feature, which must equal the FP64 reference's up to
-    bfloat16 rounding of the activations."""
+    (tcgen05, bfloat16 taps, FP32 accumulation in tensor memory; input rows
+    staged by TMA, 128 output positions of a row per tile).  A head whose
+    iteration row selects one feature turns each block's iteration output
+    into that feature, which must equal the FP64 reference's up to bfloat16
+    rounding of the activations.  The second shape has block rows of 280
+    positions: two full tiles and a ragged one, checked at the tile seams."""
     import torch
-    f, mask, y = _image(h=40, w=56, seed=8)
+    f, mask, y = _image(h=shape[0], w=shape[1], seed=8)
     net = rl.Net(seed=11)
     base = cnn_ref.unflatten(net.get_params())
     plan = rl.Plan(mask, rl.default_params(nu_max=10))
@@ -101,6 +104,8 @@ def test_tensor_core_convolutions_match_fp64_features(rl):
     rng = np.random.default_rng(4)
     blocks = [(0, 0), (0, nbw - 1), (nbh - 1, 0), (nbh - 1, nbw - 1), (1, 2)] + \
         [tuple(b) for b in rng.integers(0, [nbh, nbw], (20, 2))]
+    if nbw > 128:
+        blocks += [(0, 127), (0, 128), (nbh - 1, 255), (nbh - 1, 256), (nbh // 2, nbw - 2), (3, 129)]
     ref = {}
     for bi, bj in blocks:
         x, origin = cnn_ref.patch(y, mask, bi, bj)

@@ -17,7 +17,7 @@ from test_gpu_parity import TIE, TOL, check, gpu_run, oracle_run, rl  # noqa: F4
 
 pytestmark = pytest.mark.gpu
 
-MIB8 = 1024 * 1024 * 8
+TABLE_C_BYTES = 1024 * 1024 * 8 + 8192 + 4096   # scaled columns, row scales, 1 / (s D)
 
 
 def _every_block(g, hr, tr, nbw, max_tie_frac=0.03):
@@ -34,7 +34,7 @@ def test_stored_c_64x64_every_block(rl, index):
     g = gpu_run(rl, y, mask, c_supply=1)
     info = g["plan"].info()
     assert info["n_stored_c_tables"] == info["n_tables"]
-    assert info["device_c_bytes"] == info["n_tables"] * MIB8
+    assert info["device_c_bytes"] == info["n_tables"] * TABLE_C_BYTES
     hr, tr = oracle_run(y, mask)
     res = _every_block(g, hr, tr, mask.shape[1] // 2)
     print("stored C 64x64 #%d: matched %d / %d, near-ties %d, max err %.3g"
@@ -131,7 +131,8 @@ def test_stored_c_agrees_with_factored_supply_at_full_size(rl):
 def test_stored_c_refused_where_there_is_no_table_set(rl):
     """Stored C needs host table sets: a random (non-recurrent) mask, whose
     auto path builds tables in the kernel, and 15 apertures, which only the
-    direct path holds, are refused; so is the FP64 loop."""
+    direct path holds, are refused; so are the FP64 loop and a frequency
+    weight with a zero."""
     rnd = synth.random_mask(256, 256, 3)
     with pytest.raises(rl.RljsdeError) as e:
         rl.Plan(rnd, rl.default_params(c_supply=1))
@@ -143,4 +144,12 @@ def test_stored_c_refused_where_there_is_no_table_set(rl):
     f, mask, y = synth.workload("rljsde_64x64")
     with pytest.raises(rl.RljsdeError) as e:
         rl.Plan(mask, rl.default_params(c_supply=1, precision=1))
+    assert e.value.status == 8
+    # a frequency weight of 0 (the stored loop's state sqrt(q / D) R loses R
+    # there): auto keeps the factored loop, stored is refused
+    qz = np.ones(1024)
+    qz[33] = 0.0
+    assert rl.Plan(mask, rl.default_params(q_table=qz)).info()["n_stored_c_tables"] == 0
+    with pytest.raises(rl.RljsdeError) as e:
+        rl.Plan(mask, rl.default_params(q_table=qz, c_supply=1))
     assert e.value.status == 8
