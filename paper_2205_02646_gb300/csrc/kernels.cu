@@ -1108,20 +1108,16 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
             shortlist_setup(a, rec, scratch, om, omc, wt, we[b], sl, lane, b, st);
             nu[b] = shortlist_iterations(a, sl);
         }
-    const float *invd = nullptr;
     if constexpr (STORED) {
-        // the stored columns' scaled state R'_k = s_k R_k, its score |R'_k|^2
-        // (q / D folded into s), and 1 / (s_uv D_uv) for delta
-        const float4 *sc = cs + kStoredScaleOff;
+        // the stored columns' scaled state R'_k = s_k R_k, s_k = sqrt(q_k / D_k)
+        // from the record's q / D, whose score is |R'_k|^2
 #pragma unroll
-        for (int sl4 = 0; sl4 < 4; ++sl4) {
-            const float4 w = ldg_stream4(sc + st.coff[sl4]);
-            const float sk = ((st.ce >> sl4) & 1) ? w.y : w.x;
-            if (sl4 & 1) { st.Rre[sl4 >> 1].y *= sk; st.Rim[sl4 >> 1].y *= sk; }
-            else { st.Rre[sl4 >> 1].x *= sk; st.Rim[sl4 >> 1].x *= sk; }
+        for (int pr = 0; pr < 2; ++pr) {
+            const float2 sk = f2(sqrtf(st.qd[pr].x), sqrtf(st.qd[pr].y));
+            st.Rre[pr] = mul2(st.Rre[pr], sk);
+            st.Rim[pr] = mul2(st.Rim[pr], sk);
+            st.qd[pr] = f2(1.f, 1.f);
         }
-        st.qd[0] = st.qd[1] = f2(1.f, 1.f);
-        invd = reinterpret_cast<const float *>(cs + kStoredInvDOff);
     }
     const int nu_h = hb == 0 ? nu[0] : nu[1];
     const int numax = nu[0] > nu[1] ? nu[0] : nu[1];
@@ -1174,7 +1170,9 @@ __device__ __forceinline__ void shortlist_pair(const Args &a, const RecordShortF
         const float Rre = __shfl_sync(0xffffffffu, sre, wl);
         const float Rim = __shfl_sync(0xffffffffu, sim, wl);
         if (STORED && it < nu_h) {
-            const float invD = ldg_stream1(invd + (bk & (kK - 1)));
+            // delta = R'_uv / (s_uv D_uv): a plan storing every table set's
+            // Gram matrix keeps 1 / (s D) in the record's invD
+            const float invD = rec.invD[bk & (kK - 1)];
             select_step<float>(a, om, invD, gamma, bk & (kK - 1), Rre, Rim, eta, gam, lane & 15, trow, it, u, v, g,
                                fpix, unused_pw);
             // Eq. 17 on the shortlist with the stored column, as the stored-C loop does

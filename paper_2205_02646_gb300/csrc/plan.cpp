@@ -171,7 +171,8 @@ void build_record64(const uint8_t *key, const double *w, const Cd *r32, uint32_t
 }
 
 void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t slot_ap, bool pairs,
-                    const std::vector<double> &q, RecordF32 *rec, RecordShortF32 *sh, double *g64)
+                    const std::vector<double> &q, RecordF32 *rec, RecordShortF32 *sh, double *g64,
+                    bool scaled_invd)
 {
     static thread_local Tables T;
     build_tables(key, w, r32, slot_ap, T);
@@ -193,7 +194,11 @@ void build_record32(const uint8_t *key, const double *w, const Cd *r32, uint32_t
     }
     for (int k = 0; k < kK; ++k) {
         sh->qD[k] = (float)inv_or_zero(q[k], T.D[k]);
-        sh->invD[k] = (float)inv_or_zero(1.0, T.D[k]);
+        // the stored shortlist loop keeps R'_k = sqrt(q_k / D_k) R_k and needs
+        // 1 / (sqrt(q_uv / D_uv) D_uv) for delta
+        const double qd = inv_or_zero(q[k], T.D[k]);
+        sh->invD[k] = (float)(scaled_invd ? (qd > 0.0 ? inv_or_zero(1.0, T.D[k]) / std::sqrt(qd) : 0.0)
+                                          : inv_or_zero(1.0, T.D[k]));
     }
     std::memcpy(sh->types, key, 256);
     for (int d1 = 0; d1 < 16; ++d1)
@@ -534,7 +539,8 @@ int create(rljsde_plan **out, int n_images, const uint8_t *const *masks, const i
                                    (RecordShortF32 *)(host_short.data() + sizeof(RecordShortF32) * t),
                                    p->n_stored && p->cslot[t] >= 0
                                        ? g64.data() + (size_t)kStoredBuildDoubles * p->cslot[t]
-                                       : nullptr);
+                                       : nullptr,
+                                   p->n_stored > 0 && p->n_stored == p->n_tables);
             }
             st = upload(&p->d_records, host.data(), host.size());
             if (!st && !prm->precision) st = upload(&p->d_records_short, host_short.data(), host_short.size());

@@ -87,7 +87,9 @@ static_assert(sizeof(RecordF32) % 16 == 0, "record size must allow bulk copies")
 // FP32 tables of the shortlist loop, which reads the four G_t at one
 // (d1, d2) per candidate: G01[d] = (G_0(d), G_1(d)), G23[d] = (G_2(d), G_3(d))
 // as (re, re, im, im) so that each pair of types fills one f32x2 register
-// pair, d = d1 * 16 + d2; qD and invD by linear k.
+// pair, d = d1 * 16 + d2; qD and invD by linear k.  When every table set of
+// the plan stores its Gram matrix, invD holds 1 / (s_k D_k), s_k =
+// sqrt(q_k / D_k), the stored shortlist loop's delta factor.
 struct RecordShortF32 {
     float G01[256][4];
     float G23[256][4];
