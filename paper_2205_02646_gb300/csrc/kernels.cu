@@ -9,10 +9,16 @@
 //      from which R_k = sum_t conj(h_t(k)) Y_t(k mod 16);
 //   3. nu_max iterations of: scores q_k |R_k|^2 / D_k and their argmax
 //      (Eq. 11), delta = R_uv / D_uv (Eq. 16), c_uv += gamma delta (Eq. 15),
-//      and the projected-residual update of Eq. 17, carried out on Y:
-//          Y_t(kap) -= gamma delta h_t(uv) G_t((uv - kap) mod 16),
-//      which is Eq. 17 with C factored as C_{k,l} = sum_t conj(h_t(k)) h_t(l)
-//      G_t(l - k);
+//      and the projected-residual update of Eq. 17, R -= gamma delta C_{., uv},
+//      with the column of C (Eq. 14) either
+//        - read from the Gram matrix the plan stores for the block's local
+//          mask (the paper's recurrent form, Table I; the default), the state
+//          kept as sqrt(q_k / D_k) R_k so that the score is its squared
+//          modulus (greedy_loop_stored), or
+//        - rebuilt from the factored tables, the update carried out on Y:
+//            Y_t(kap) -= gamma delta h_t(uv) G_t((uv - kap) mod 16),
+//          which is Eq. 17 with C factored as C_{k,l} = sum_t conj(h_t(k))
+//          h_t(l) G_t(l - k) (greedy_loop_f32, and the FP64 loop);
 //   4. Eq. 18 on the central block, accumulated as each coefficient changes.
 // A persistent CTA walks chunks of 8 blocks that share one table set; the
 // table set of the next chunk of the same slot parity is brought into shared
