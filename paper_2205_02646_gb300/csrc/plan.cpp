@@ -644,7 +644,7 @@ int rljsde_plan_info(const rljsde_plan_t *p, rljsde_plan_info_t *out)
     out->n_interior_tables = p->n_interior;
     out->n_work_entries = p->n_entries;
     const bool all_stored = p->n_stored > 0 && p->n_stored == p->n_tables;
-    out->warps_per_cta = all_stored ? 4 : p->warps;
+    out->warps_per_cta = all_stored ? p->warps_stored : p->warps;
     out->ctas_per_sm = all_stored ? p->ctas_stored : p->ctas_per_sm;
     out->grid = all_stored ? p->grid_stored : p->grid;
     out->device_table_bytes = (int64_t)p->record_bytes * p->n_tables;

@@ -148,7 +148,7 @@ struct rljsde_plan {
     int n_apertures = 0;              // distinct non-empty apertures in the masks
     int device = 0, sm_count = 0;
     int warps = 4, ctas_per_sm = 0, grid = 0, variant = 0;   // factored loop (and FP64, learned)
-    int variant_stored = 0, grid_stored = 0, ctas_stored = 0;  // stored-C loop, if n_stored > 0
+    int variant_stored = 0, grid_stored = 0, ctas_stored = 0, warps_stored = 0;   // stored-C loop, if n_stored > 0
     int learned_warps = 4;            // warps per CTA of the shortlist-loop kernel (4: two blocks per warp)
     int learned_minb = 3;             // its register budget: resident CTAs per SM
     // device memory, all owned by the plan
