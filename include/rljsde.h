@@ -123,9 +123,9 @@ typedef struct {
                              RLJSDE_ERR_OUT_OF_MEMORY when the matrices do not
                              fit.  A plan with both kinds of
                              table sets runs two kernels per reconstruction;
-                             the stored-C loop always runs one CTA of 8 warps
-                             per SM (rljsde_set_launch and rljsde_autotune
-                             shape the factored loop).  The
+                             the stored-C loop runs one CTA of 8 warps per SM
+                             (4 warps x 3 CTAs below nu_max 20; rljsde_set_launch
+                             and rljsde_autotune shape the factored loop).  The
                              learned proposal's loops always use the factored
                              form                                              */
 } rljsde_params;

@@ -1805,11 +1805,16 @@ const Variant kVariants[] = {
     RLJSDE_VARIANT(float, 4, 3, 8), RLJSDE_VARIANT(float, 4, 3, 11), RLJSDE_VARIANT(float, 4, 3, 12),
     RLJSDE_VARIANT(double, 4, 1, 8), RLJSDE_VARIANT(double, 4, 1, 11), RLJSDE_VARIANT(double, 4, 1, 12),
     // the stored-C loop: one CTA of 8 warps per SM with the full register file
-    // (254 registers, no spills) ran 4 % faster than 4 warps x 3 CTAs (168,
-    // spilling) and 2 % faster than 4 warps x 2 CTAs
-    RLJSDE_VARIANT(float, 8, 1, 16), RLJSDE_VARIANT(float, 8, 1, 19), RLJSDE_VARIANT(float, 8, 1, 20),
+    // (254 registers, no spills) iterates 4 % faster than 4 warps x 3 CTAs
+    // (168, spilling) and 2 % faster than 4 warps x 2 CTAs, but its initial
+    // projection is 7 % slower: 4 x 3 for short loops (nu_max < 20)
+    RLJSDE_VARIANT(float, 8, 1, 16), RLJSDE_VARIANT(float, 4, 3, 16), RLJSDE_VARIANT(float, 8, 1, 19),
+    RLJSDE_VARIANT(float, 8, 1, 20),
     RLJSDE_VARIANT(float, 8, 1, 24), RLJSDE_VARIANT(float, 8, 1, 27), RLJSDE_VARIANT(float, 8, 1, 28),
-    RLJSDE_VARIANT(float, 4, 3, 17), RLJSDE_VARIANT(float, 8, 1, 18),
+    // the learned path's full loop on the blocks the gate sends back: few per
+    // chunk, so more CTAs of fewer warps (with a tenth of the blocks sent
+    // back the learned path ran at 551 MP/s with 4 x 3, 415 with 8 x 1)
+    RLJSDE_VARIANT(float, 4, 3, 17), RLJSDE_VARIANT(float, 4, 3, 18),
 };
 #undef RLJSDE_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -2017,10 +2022,14 @@ int choose_launch(rljsde_plan *p, int warps, int ctas_per_sm)
     const int fp64 = p->params.precision == 1;
     const int mode = (p->kind == 1 ? 3 : p->kind == 3 ? 4 : 0) | (p->params.pairs ? kModePairs : 0);
     if (p->n_stored > 0 && !fp64) {
-        // the stored-C loop: its one instantiation (8 warps, one CTA per SM)
+        // the stored-C loop: 8 warps in one CTA per SM, or 4 warps x 3 CTAs for
+        // short loops where that instantiation exists
+        const int want_warps = p->params.nu_max >= 20 ? 8 : 4;
         p->variant_stored = -1;
         for (int i = 0; i < kNumVariants; ++i)
-            if (!kVariants[i].fp64 && kVariants[i].mode == (mode | kModeStoredC)) p->variant_stored = i;
+            if (!kVariants[i].fp64 && kVariants[i].mode == (mode | kModeStoredC) &&
+                (p->variant_stored < 0 || kVariants[i].warps == want_warps))
+                p->variant_stored = i;
         if (p->variant_stored < 0) return RLJSDE_ERR_UNSUPPORTED;
         const int occ = occupancy(kVariants[p->variant_stored]);
         if (occ < 0) return RLJSDE_ERR_CUDA;
@@ -2103,7 +2112,7 @@ int rljsde_reconstruct_learned(const rljsde_plan_t *plan, const float *lr, size_
     const int sc = plan->n_stored > 0 && plan->n_stored == plan->n_tables ? kModeStoredC : 0;
     const int lw = sc ? 4 : plan->learned_warps, lm = sc ? 3 : plan->learned_minb;
     int st = launch_mode(plan, a, 1 | sc, lw, lm, (cudaStream_t)stream);
-    if (st == RLJSDE_OK) st = launch_mode(plan, a, 2 | sc, sc ? 8 : 4, 0, (cudaStream_t)stream);
+    if (st == RLJSDE_OK) st = launch_mode(plan, a, 2 | sc, 4, 0, (cudaStream_t)stream);
     return st;
 }
 
