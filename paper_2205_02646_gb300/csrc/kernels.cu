@@ -793,32 +793,38 @@ __device__ __forceinline__ void load_column(const float4 *cs, const int l, const
     for (int i = 0; i < 16; ++i) col[i] = ldg_stream4(p + 32 * i);
 }
 
-// The argmax of the stored-C loop tracks (score, slot) per lane, slot =
-// 16 a + 4 jj + 2 e + b in increasing index order, and reads the winner's R
-// from its registers afterwards by a switch on the warp-uniform slot: two
-// operations per candidate fewer than carrying R along (1.5x faster loop,
-// identical results).  Ties keep the lower slot, hence the lower index.
-__device__ __forceinline__ void keep_slot(const float s, const int i, float &bs, int &bi)
-{
-    if (s > bs) { bs = s; bi = i; }
-}
-
 // The state is R'_k = s_k R_k with s_k = sqrt(q_k / D_k), so the score of
 // Eq. 11 is |R'_k|^2.
 __device__ __forceinline__ float2 norm2(const CP r) { return fma2(r.im, r.im, mul2(r.re, r.re)); }
 
-__device__ __forceinline__ void score_pair_slot(const CP (&R)[4], const int jj, float &bs0, int &bi0, float &bs1,
-                                                int &bi1)
+// Argmax of the stored-C loop.  Slots 4 g .. 4 g + 3 (g = 4 a + jj) are
+// four consecutive candidates of the lane in index order, held in R[jj][2a]
+// (.x, .y: e = 0, 1 with b = 0) and R[jj][2a + 1] (b = 1).  The scan visits
+// the groups in increasing g and keeps the largest score (two three-input
+// max operations per group, sm_100 and later), the first group reaching it
+// and three of that group's scores; the slot inside the group is the first
+// whose score equals the maximum (the fourth if none of the three does).
+// The same choice as comparing every candidate in index order, with 7
+// operations per group instead of 12 and a dependency chain through the
+// running maximum of two operations per group instead of eight.
+__device__ __forceinline__ float max3f(const float a, const float b, const float c)
 {
-    const float2 s00 = norm2(R[0]), s01 = norm2(R[1]), s10 = norm2(R[2]), s11 = norm2(R[3]);
-    keep_slot(s00.x, 4 * jj + 0, bs0, bi0);
-    keep_slot(s01.x, 4 * jj + 1, bs0, bi0);
-    keep_slot(s00.y, 4 * jj + 2, bs0, bi0);
-    keep_slot(s01.y, 4 * jj + 3, bs0, bi0);
-    keep_slot(s10.x, 4 * jj + 0, bs1, bi1);
-    keep_slot(s11.x, 4 * jj + 1, bs1, bi1);
-    keep_slot(s10.y, 4 * jj + 2, bs1, bi1);
-    keep_slot(s11.y, 4 * jj + 3, bs1, bi1);
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ void scan_group(const CP (&Rj)[4], const int a, const int g, float &bs, int &bg,
+                                           float &t0, float &t1, float &t2)
+{
+    const float2 s0 = norm2(Rj[2 * a]), s1 = norm2(Rj[2 * a + 1]);
+    const float m = max3f(max3f(bs, s0.x, s1.x), s0.y, s1.y);
+    const bool p = m > bs;
+    bg = p ? g : bg;
+    t0 = p ? s0.x : t0;
+    t1 = p ? s1.x : t1;
+    t2 = p ? s0.y : t2;
+    bs = m;
 }
 
 // R of this lane's candidate in a slot (the same slot in every lane).
@@ -905,14 +911,17 @@ __device__ __forceinline__ void greedy_loop_stored(const Args &a, const RecordF3
     const long long trow = (long long)we.ord * a.nu_max;
 
     for (int it = 0; it < a.nu_max; ++it) {
-        float bs0 = -1.f, bs1 = -1.f;
-        int bi0 = 0, bi1 = 0;
+        // scores are >= 0: starting from 0, a lane whose scores are all 0
+        // keeps group 0, slot 0, as a scan from -1 would
+        float bs = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
+        int bg = 0;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) score_pair_slot(R[jj], jj, bs0, bi0, bs1, bi1);
-        if (bs1 > bs0) { bs0 = bs1; bi0 = bi1 + 16; }
-        float bs = bs0;
-        // slot -> k: a = slot >> 4, jj = (slot >> 2) & 3, e = (slot >> 1) & 1, b = slot & 1
-        int bk = (8 * h + 2 * ((bi0 >> 2) & 3) + ((bi0 >> 1) & 1) + 16 * (bi0 >> 4)) * kW + k2 + 16 * (bi0 & 1);
+        for (int aa = 0; aa < 2; ++aa)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) scan_group(R[jj], aa, 4 * aa + jj, bs, bg, t0, t1, t2);
+        const int el = t0 == bs ? 0 : t1 == bs ? 1 : t2 == bs ? 2 : 3;
+        // slot 4 bg + el = 16 a + 4 jj + 2 e + b -> k
+        int bk = (8 * h + 2 * (bg & 3) + (el >> 1) + 16 * (bg >> 2)) * kW + k2 + 16 * (el & 1);
         warp_argmax(bs, bk);
         const bool more = it + 1 < a.nu_max;
         float4 col[16];
